@@ -1,0 +1,42 @@
+"""The oracle's pins must be sensitive: each plausible mistake below, planted in
+a scratch copy of the oracle (on the CPU), has to make the pin suite fail."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "tie_E_before_F": ("(hv == fv ? 2 : 3)", "(hv == ev ? 3 : 2)"),
+    "E_extends_on_tie": ("((e_ext > e_open) << 2)", "((e_ext >= e_open) << 2)"),
+    "F_extends_on_tie": ("((f_ext > f_open) << 3)", "((f_ext >= f_open) << 3)"),
+    "extend_charged_open": ("e_ext = E[at - 1] - e;", "e_ext = E[at - 1] - o;"),
+    "transposed_matrix": ("M[c[i - 1] * K + s[j - 1]]", "M[s[j - 1] * K + c[i - 1]]"),
+    "last_best_cell": ("if (hv > best) { best = hv;", "if (hv >= best && hv > 0) { best = hv;"),
+    "prefix_wrong_slot": ("ins[0] += (uint16_t)(j1 - i1);", "ins[1] += (uint16_t)(j1 - i1);"),
+    "suffix_short_by_one": ("for (int32_t t = 1; t <= k; t++) occ[i2 + t] = 1;",
+                            "for (int32_t t = 1; t < k; t++) occ[i2 + t] = 1;"),
+    "gap_cost_halved": ("+ 2 * g * r;", "+ g * r;"),
+    "distance_drops_term": ("sum += (int64_t)self[i] + self[ri] - 2",
+                            "sum += (int64_t)self[i] - 2"),
+    "F_dropped_from_H": ("max2(max2(0, dv), max2(ev, fv));", "max2(max2(0, dv), ev);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    for d in ("oracle", "seqgen", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    src = tmp_path / "oracle" / "msa_oracle.c"
+    text = src.read_text()
+    assert text.count(old) == 1, "mutation site moved: " + name
+    src.write_text(text.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=tmp_path,
+                       stdout=subprocess.PIPE, stderr=subprocess.STDOUT, timeout=600)
+    assert r.returncode == 1, r.stdout.decode()[-2000:]
