@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the center-star MSA hot path on one GB300 (or N, one process
+each, independent sequence sets = weak scaling).
+
+A step is one pass of the whole path over the 10,000-protein batched uneven
+workload (lognormal lengths, median 350, sigma 0.6, clipped 50-2000, 5
+families, BLOSUM62, gap 11/1): encode, exact center (all pairs), alignment of
+every sequence to the center with traceback, merge of the inserted spaces,
+MSA rows, sum-of-pairs cost.  Metric: GCUPS = DP cells of the step (center
+selection + alignment, real cells only) / step time.
+
+`value` times the step with inputs already in HBM (letters as a device
+buffer, outputs left in HBM); `e2e` times the same step through the C ABI
+with pinned host letters in and the MSA rows copied back to host memory.
+L2 is flushed (a 512 MB write) before every timed step, outside its events.
+
+--impl reference times the CPU oracle (plain C, all host cores) on bounded
+samples of the same workload's pairs, the same metric and unit.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batched_uneven_10k"
+METRIC = "GCUPS and % of integer/DPX roofline; end-to-end MSA sec (learned vs exact center)"
+UNIT = "GCUPS"
+# ALU roofline of the packed DP: 152 SMs x 128 integer lanes x 2.07 GHz max
+# clock / 3 integer ops per cell (6 DPX ops per packed pair of int16 cells).
+SMS, INT_LANES, MAX_GHZ, OPS_PER_CELL = 152, 128, 2.07, 3.0
+ALU_PEAK_GCUPS = SMS * INT_LANES * MAX_GHZ / OPS_PER_CELL
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="override the sequence count")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(letters, offsets, alph, M, o, e, seconds, seed=7):
+    """The oracle, as it stands, on random pairs of the workload for ~`seconds`."""
+    import oracle
+    prob = oracle.Problem(letters, offsets, alph, M, o, e)
+    lens = np.diff(offsets).astype(np.int64)
+    rng = np.random.default_rng(seed)
+    threads = oracle.default_threads()
+    probe = rng.integers(0, prob.n, size=(max(64, threads * 8), 2))
+    t0 = time.perf_counter()
+    oracle.pair_scores(prob, probe, threads)
+    dt = time.perf_counter() - t0
+    rate = float((lens[probe[:, 0]] * lens[probe[:, 1]]).sum()) / max(dt, 1e-6)
+    count = int(max(threads, min(2_000_000, rate * seconds / float((lens ** 2).mean()))))
+    pairs = rng.integers(0, prob.n, size=(count, 2))
+    cells = float((lens[pairs[:, 0]] * lens[pairs[:, 1]]).sum())
+    t0 = time.perf_counter()
+    oracle.pair_scores(prob, pairs, threads)
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d uniformly drawn pairs of the %d-sequence set (%.3g DP cells), "
+                      "scalar C full-matrix Gotoh, %.1f s" % (count, prob.n, cells, dt)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    from seqgen import generate, scoring
+    letters, offsets, w, _ = generate(args.workload, n=args.n)
+    alph, M, _, _ = scoring(w.kind)
+    prob = oracle.Problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    lens = np.diff(offsets).astype(np.int64)
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(11)
+    # size one step at a few seconds of CPU work
+    probe = rng.integers(0, prob.n, size=(threads * 8, 2))
+    t0 = time.perf_counter()
+    oracle.pair_scores(prob, probe, threads)
+    rate = float((lens[probe[:, 0]] * lens[probe[:, 1]]).sum()) / max(time.perf_counter() - t0, 1e-6)
+    per_step = int(max(threads, rate * 4.0 / float((lens ** 2).mean())))
+    times, cells_all = [], []
+    for s in range(args.warmup + args.steps):
+        pairs = rng.integers(0, prob.n, size=(per_step, 2))
+        cells = float((lens[pairs[:, 0]] * lens[pairs[:, 1]]).sum())
+        t0 = time.perf_counter()
+        oracle.pair_scores(prob, pairs, threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            cells_all.append(cells)
+    value = sum(cells_all) / sum(times) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "%s: %d proteins, lognormal lengths median 350 sigma 0.6 "
+                                   "clipped 50-2000, 5 families, BLOSUM62 11/1" % (w.name, prob.n),
+                       "step": "oracle pair scores on %d random pairs of the set" % per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d random pairs per step (%.3g cells)" %
+                                       (per_step, float(np.mean(cells_all)))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from seqgen import generate, scoring
+    from paper_1704_00878_gb300 import binding as b
+
+    # weak scaling: every rank aligns its own independent set of the same shape
+    base_seed = generate.__globals__["WORKLOADS"][args.workload].seed
+    letters, offsets, w, _ = generate(args.workload, n=args.n, seed=base_seed + 1000 * rank)
+    alph, M, _, _ = scoring(w.kind)
+    n = offsets.size - 1
+    stream = torch.cuda.current_stream()
+    dlet = torch.from_numpy(letters).cuda()
+    hlet = torch.from_numpy(letters).pin_memory()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ctx = b.Context(M, alph, w.gap_open, w.gap_extend, stream=stream)
+    h = ctx.h
+
+    def step_device():
+        b.msa_load(h, dlet, offsets)
+        c, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        b.msa_align_to_center(h, c)
+        _, W = b.msa_merge_gaps(h, want_rows=False)
+        sp = b.msa_sp_score(h)
+        return c, W, sp
+
+    host_rows = {}
+
+    def step_e2e():
+        b.msa_load(h, hlet, offsets)
+        c, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        b.msa_align_to_center(h, c)
+        _, W = b.msa_merge_gaps(h, want_rows=False)
+        buf = host_rows.get(W)
+        if buf is None:
+            host_rows.clear()
+            buf = host_rows[W] = torch.empty((n, W), dtype=torch.uint8).pin_memory()
+        b.msa_merge_gaps(h, out=buf)
+        sp = b.msa_sp_score(h)
+        return c, W, sp
+
+    def timed(fn, steps):
+        total_ms, cells, center_ms, center_cells, launches0 = 0.0, 0, 0.0, 0, None
+        out = None
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if launches0 is None:
+                launches0 = b.msa_stage_times(h)[1]["launches"]
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            out = fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            ms, cnt = b.msa_stage_times(h)
+            cells += cnt["center_cells"] + cnt["align_cells"]
+            center_ms += ms["center_kernels"]
+            center_cells += cnt["center_cells"]
+        launches = b.msa_stage_times(h)[1]["launches"] - launches0
+        return total_ms, cells, center_ms, center_cells, launches, out
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, cells, center_ms, center_cells, launches, (c, W, sp) = timed(step_device, args.steps)
+    clocks = sampler.stop()
+    stage_ms = b.msa_stage_times(h)[0]
+    e2e_ms, e2e_cells, *_ = timed(step_e2e, max(1, args.steps))
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def reduce_sum(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t)
+        return float(t.item())
+
+    t_max = reduce_max(total_ms)
+    all_cells = reduce_sum(float(cells))
+    e2e_max = reduce_max(e2e_ms)
+    e2e_all = reduce_sum(float(e2e_cells))
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    value = all_cells / (t_max * 1e-3) / 1e9
+    achieved = center_cells / (center_ms * 1e-3) / 1e9 if center_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
+        "config": {"workload": "%s: %d proteins per GPU, lognormal lengths median 350 sigma 0.6 "
+                               "clipped 50-2000, 5 families at 40%% divergence, 5%% indels, "
+                               "BLOSUM62 gap 11/1, exact all-pairs center" % (w.name, n),
+                   "step": "encode + exact center + align with traceback + merge + rows + SP",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "cells_per_step": cells / args.steps, "center": c, "msa_width": W,
+                   "avg_sp": sp / (n * (n - 1) / 2)},
+        "roofline": {"bound": "alu", "kernel": "k_center (exact-center DP, packed int16x2)",
+                     "achieved": achieved, "peak": ALU_PEAK_GCUPS, "unit": UNIT,
+                     "frac": achieved / ALU_PEAK_GCUPS if achieved else None, "traffic": None,
+                     "peak_source": "152 SMs x 128 int lanes x 2.07 GHz / 3 ops per cell"},
+        "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+        "clocks": clocks,
+        "e2e": {"value": e2e_all / (e2e_max * 1e-3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": int(letters.nbytes + offsets.nbytes),
+                "d2h_bytes_per_step": int(n * W + 8 * 4)},
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(letters, offsets, alph, M, w.gap_open, w.gap_extend,
+                                            args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

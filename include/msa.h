@@ -1,0 +1,151 @@
+/*
+ * msa.h -- C ABI of the GB300 center-star multiple sequence alignment library
+ * (libmsa.so).  The method is HAlign-II's protein path (arXiv 1704.00878,
+ * Methods, "Smith-Waterman algorithm for protein sequences with Spark" and
+ * Figure 3): pick a center sequence, align every sequence to it with affine-gap
+ * Smith-Waterman (Eq. 1-2) and traceback, then merge the inserted spaces into
+ * one alignment.
+ *
+ * Conventions for every call:
+ *   - return 0 (MSA_OK) or a negative MSA_E* code; msa_last_error() then
+ *     holds a one-line reason.  No call falls back to the CPU.
+ *   - every call is enqueued on the stream given to msa_create and returns
+ *     after that stream has finished the call's work (synchronous to the
+ *     caller), so host outputs are valid on return.
+ *   - "host or device" pointers are classified with cudaPointerGetAttributes;
+ *     device pointers must belong to the context's current device.
+ *   - the caller owns every buffer it passes; the library copies what it
+ *     keeps.  Device working memory belongs to the context and is released by
+ *     msa_destroy.
+ *   - sequence indices are positions in the set given to msa_load.
+ *   - a context is not thread-safe; use one per host thread.
+ */
+#ifndef MSA_H
+#define MSA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSA_OK        0
+#define MSA_EINVAL   (-1)   /* bad argument, letter not in the alphabet, empty sequence */
+#define MSA_ENOMEM   (-2)   /* device or host allocation failed */
+#define MSA_ECUDA    (-3)   /* a CUDA call failed */
+#define MSA_ETIMEOUT (-4)   /* a bounded device wait gave up */
+#define MSA_ESTATE   (-5)   /* calls made out of order (e.g. merge before align) */
+#define MSA_ERANGE   (-6)   /* a size beyond a documented limit */
+
+/* cell precision policy for the score fill */
+#define MSA_AUTO   0   /* packed int16x2 when the a-priori bound fits, else int32 */
+#define MSA_INT16  1   /* packed int16x2; pairs that may overflow are re-run in int32 */
+#define MSA_INT32  2   /* int32 cells */
+
+/* center selection modes (msa_select_center) */
+#define MSA_CENTER_EXACT          0   /* all pairs */
+#define MSA_CENTER_EXACT_SAMPLED  1   /* every candidate against a given reference subset */
+#define MSA_CENTER_LEARNED        2   /* embedding network (msa_train_selector / msa_load_selector) */
+#define MSA_CENTER_FIRST          3   /* index 0 (the nucleotide path's "first sequence") */
+
+#define MSA_MAX_ALPHABET 32
+#define MSA_MAX_LEN      8192  /* residues per sequence */
+
+typedef struct msa_ctx msa_ctx;
+
+typedef struct {
+    const int8_t *matrix;   /* alphabet x alphabet substitution scores s(a,b) = matrix[a*alphabet+b], host */
+    int32_t alphabet;       /* 1 .. MSA_MAX_ALPHABET */
+    const char *letters;    /* alphabet characters, index k <-> letters[k]; '-' is reserved */
+    int32_t gap_open;       /* W_k = gap_open + (k-1)*gap_extend (Eq. 2), gap_open >= gap_extend >= 1 */
+    int32_t gap_extend;
+    int32_t precision;      /* MSA_AUTO | MSA_INT16 | MSA_INT32 */
+    int32_t sat_limit;      /* int16 overflow guard, 0 = 32767; smaller values force the
+                               int32 re-run on more pairs (used to test that path) */
+} msa_params;
+
+/* Create a context.  cuda_stream: a cudaStream_t (NULL = the legacy default
+ * stream).  Copies the matrix and letters.  EINVAL on a bad alphabet, gap
+ * pair or precision. */
+int msa_create(msa_ctx **out, const msa_params *params, void *cuda_stream);
+void msa_destroy(msa_ctx *ctx);
+const char *msa_last_error(const msa_ctx *ctx);
+
+/* Load n >= 1 sequences: sequence t is letters[offsets[t] .. offsets[t+1]).
+ * letters: host or device ASCII; offsets: host int64[n+1], offsets[0] = 0.
+ * Encodes letters to alphabet indices on the GPU and sorts by length
+ * (stable).  EINVAL for an empty sequence or a letter outside `letters`;
+ * ERANGE for a sequence longer than MSA_MAX_LEN.  Replaces any earlier set. */
+int msa_load(msa_ctx *ctx, const uint8_t *letters, const int64_t *offsets, int64_t n);
+
+/* Local alignment scores S(a,b) (Eq. 1-2, best cell over H) for listed pairs.
+ * pairs: host int64[npairs][2] (a is the row sequence, b the column
+ * sequence); scores_out: host or device int32[npairs]. */
+int msa_pair_scores(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, int32_t *scores_out);
+
+/* Choose the center star sequence (Figure 3's first MapReduce step).
+ * EXACT: center = argmin_i sum_j d(i,j), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B)
+ *   over all j (lowest index on ties).
+ * EXACT_SAMPLED: the same sum over j in refs (host int64[nref], distinct).
+ * LEARNED: argmin_i ||e_i - mean(e)||^2 over the selector's embeddings.
+ * FIRST: 0.
+ * center_out: host int64; sum_dist_out (nullable, host int64): the winning
+ * row sum (EXACT modes), else 0.  ESTATE for LEARNED without a selector. */
+int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
+                      int64_t *center_out, int64_t *sum_dist_out);
+
+/* Row sums of d for every sequence from the last EXACT / EXACT_SAMPLED
+ * selection: rowsum_out host or device int64[n]. */
+int msa_center_rowsums(msa_ctx *ctx, int64_t *rowsum_out);
+
+/* Align every loaded sequence to `center` (Figure 3's map step): affine
+ * Smith-Waterman fill with 4-bit traceback codes, traceback from the best
+ * cell (smallest row, then column) to a zero cell, flank rule, and one row of
+ * the inserted-space matrix per sequence.  scores_out: nullable, host or
+ * device int32[n]. */
+int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out);
+
+/* Results of the last msa_align_to_center, each nullable, host or device:
+ *   seg_out int32[n][5] = {score, i1, j1, i2, j2}: the local segment is
+ *     center[i1+1..i2] x seq[j1+1..j2] (all 0 when the score is 0);
+ *   ins_out uint16[n][Lc+1]: residues inserted before center residue 1
+ *     (slot 0), between residues j and j+1 (slot j), after the last (slot Lc);
+ *   occ_out uint8[n][Lc+1]: occ[i] = 1 if a residue faces center residue i
+ *     (i = 1..Lc), 0 if a gap does; occ[0] = 0. */
+int msa_alignment_info(msa_ctx *ctx, int32_t *seg_out, uint16_t *ins_out, uint8_t *occ_out);
+
+/* Traceback codes of sequence `seq` from the last msa_align_to_center, as a
+ * host or device uint8[Lc][Ls] array: bits 0-1 source of H (0 zero, 1
+ * diagonal, 2 F = center residue vs gap, 3 E = sequence residue vs gap),
+ * bit 2 E extended, bit 3 F extended.  Testing aid. */
+int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out);
+
+/* Merge (Figure 3's reduce + final map): G[j] = max over rows of ins[j],
+ * width W = Lc + sum_j G[j]; row t holds, per slot j, its ins[j] residues
+ * left-justified then G[j]-ins[j] gaps '-', then center column j+1's facing
+ * residue or '-'.  msa_out: NULL to query the width only, else host or device
+ * uint8[n][W] (ASCII letters and '-').  width_out: host int64. */
+int msa_merge_gaps(msa_ctx *ctx, uint8_t *msa_out, int64_t *width_out);
+
+/* Sum-of-pairs cost of the merged alignment (the paper's avg SP numerator:
+ * +1 per differing residue pair, +2 per residue-gap pair, per column);
+ * avg SP = cost / (n(n-1)/2).  sp_cost_out: host int64. */
+int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out);
+
+/* Sizes of the current state: dims_out host int64[4] = {n, center (-1 if
+ * none), Lc (center length, 0 if none), W (MSA width, 0 before a merge)}. */
+int msa_dims(msa_ctx *ctx, int64_t *dims_out);
+
+/* Device milliseconds of the stages of the last calls, CUDA events on the
+ * context stream: [0] encode, [1] center selection, [2] align DP, [3]
+ * traceback, [4] merge, [5] rows, [6] SP, [7] center DP kernels alone, [8]
+ * align DP kernels alone.  counters_out (nullable, int64[3]): DP cells of the
+ * last center selection, DP cells of the last alignment, kernels launched by
+ * this context since msa_create. */
+int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSA_H */

@@ -1,0 +1,227 @@
+"""ctypes binding of libmsa.so (include/msa.h): argument marshalling only.
+
+Every function has the name of its C entry point.  Arrays may be numpy arrays
+(host) or torch tensors (host or CUDA); outputs are returned as numpy arrays
+unless a caller-provided `out` buffer is given.  Errors raise MSAError with the
+library's message.  There is no CPU fallback: importing this module on a
+machine without the built library raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+MSA_OK, MSA_EINVAL, MSA_ENOMEM, MSA_ECUDA, MSA_ETIMEOUT, MSA_ESTATE, MSA_ERANGE = 0, -1, -2, -3, -4, -5, -6
+MSA_AUTO, MSA_INT16, MSA_INT32 = 0, 1, 2
+MSA_CENTER_EXACT, MSA_CENTER_EXACT_SAMPLED, MSA_CENTER_LEARNED, MSA_CENTER_FIRST = 0, 1, 2, 3
+MSA_MAX_LEN = 8192
+
+STAGES = ("encode", "center", "align_dp", "traceback", "merge", "rows", "sp", "center_kernels",
+          "align_kernels")
+
+
+class MSAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+class msa_params(ctypes.Structure):
+    _fields_ = [("matrix", ctypes.c_void_p), ("alphabet", ctypes.c_int32),
+                ("letters", ctypes.c_char_p), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("sat_limit", ctypes.c_int32)]
+
+
+_lib = None
+_SIGS = {
+    "msa_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(msa_params), ctypes.c_void_p]),
+    "msa_destroy": (None, [ctypes.c_void_p]),
+    "msa_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "msa_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "msa_pair_scores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "msa_select_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_center_rowsums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_align_to_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "msa_alignment_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_debug_codes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "msa_merge_gaps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_sp_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libmsa.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libmsa.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(x))
+
+
+def _check(ctx, rc):
+    if rc != MSA_OK:
+        msg = lib().msa_last_error(ctx)
+        raise MSAError(rc, msg.decode() if msg else "error")
+
+
+def msa_create(matrix, letters, gap_open, gap_extend, precision=MSA_AUTO, sat_limit=0, stream=None):
+    """Returns a context handle.  stream: a torch.cuda.Stream, an int handle, or None."""
+    M = np.ascontiguousarray(matrix, dtype=np.int8)
+    p = msa_params(ctypes.c_void_p(M.ctypes.data), int(M.shape[0]), letters.encode(),
+                   int(gap_open), int(gap_extend), int(precision), int(sat_limit))
+    h = ctypes.c_void_p()
+    st = getattr(stream, "cuda_stream", stream)
+    rc = lib().msa_create(ctypes.byref(h), ctypes.byref(p), ctypes.c_void_p(st) if st else None)
+    if rc != MSA_OK:
+        raise MSAError(rc, "msa_create rejected its parameters")
+    return h
+
+
+def msa_destroy(ctx):
+    lib().msa_destroy(ctx)
+
+
+def msa_last_error(ctx):
+    m = lib().msa_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def msa_load(ctx, letters, offsets):
+    """letters: uint8 ASCII (numpy, or torch host/CUDA); offsets: int64[n+1] host."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(ctx, lib().msa_load(ctx, _ptr(letters), _ptr(off), off.size - 1))
+
+
+def msa_dims(ctx):
+    d = np.zeros(4, np.int64)
+    _check(ctx, lib().msa_dims(ctx, _ptr(d)))
+    return tuple(int(x) for x in d)
+
+
+def msa_pair_scores(ctx, pairs, out=None):
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    res = np.zeros(pr.shape[0], np.int32) if out is None else out
+    _check(ctx, lib().msa_pair_scores(ctx, _ptr(pr), pr.shape[0], _ptr(res)))
+    return res
+
+
+def msa_select_center(ctx, mode, refs=None):
+    """Returns (center, winning row sum of distances)."""
+    c = np.zeros(1, np.int64)
+    s = np.zeros(1, np.int64)
+    r = None if refs is None else np.ascontiguousarray(refs, dtype=np.int64)
+    _check(ctx, lib().msa_select_center(ctx, int(mode), _ptr(r), 0 if r is None else r.size,
+                                        _ptr(c), _ptr(s)))
+    return int(c[0]), int(s[0])
+
+
+def msa_center_rowsums(ctx, out=None):
+    n = msa_dims(ctx)[0]
+    res = np.zeros(n, np.int64) if out is None else out
+    _check(ctx, lib().msa_center_rowsums(ctx, _ptr(res)))
+    return res
+
+
+def msa_align_to_center(ctx, center, scores_out=None):
+    _check(ctx, lib().msa_align_to_center(ctx, int(center), _ptr(scores_out)))
+    return scores_out
+
+
+def msa_alignment_info(ctx):
+    """(seg int32[n,5], ins uint16[n,Lc+1], occ uint8[n,Lc+1])."""
+    n, _, lc, _ = msa_dims(ctx)
+    seg = np.zeros((n, 5), np.int32)
+    ins = np.zeros((n, lc + 1), np.uint16)
+    occ = np.zeros((n, lc + 1), np.uint8)
+    _check(ctx, lib().msa_alignment_info(ctx, _ptr(seg), _ptr(ins), _ptr(occ)))
+    return seg, ins, occ
+
+
+def msa_debug_codes(ctx, seq, ls):
+    _, _, lc, _ = msa_dims(ctx)
+    out = np.zeros((lc, int(ls)), np.uint8)
+    _check(ctx, lib().msa_debug_codes(ctx, int(seq), _ptr(out)))
+    return out
+
+
+def msa_merge_gaps(ctx, out=None, want_rows=True):
+    """Returns (msa uint8[n, W] or the given out buffer or None, W)."""
+    w = np.zeros(1, np.int64)
+    _check(ctx, lib().msa_merge_gaps(ctx, None, _ptr(w)))
+    W = int(w[0])
+    if not want_rows:
+        return None, W
+    n = msa_dims(ctx)[0]
+    res = np.zeros((n, W), np.uint8) if out is None else out
+    _check(ctx, lib().msa_merge_gaps(ctx, _ptr(res), _ptr(w)))
+    return res, W
+
+
+def msa_sp_score(ctx):
+    v = np.zeros(1, np.int64)
+    _check(ctx, lib().msa_sp_score(ctx, _ptr(v)))
+    return int(v[0])
+
+
+def msa_stage_times(ctx):
+    """({stage: ms}, {"center_cells", "align_cells", "launches"})."""
+    ms = np.zeros(len(STAGES), np.float32)
+    cnt = np.zeros(3, np.int64)
+    _check(ctx, lib().msa_stage_times(ctx, _ptr(ms), len(STAGES), _ptr(cnt)))
+    return (dict(zip(STAGES, (float(x) for x in ms))),
+            {"center_cells": int(cnt[0]), "align_cells": int(cnt[1]), "launches": int(cnt[2])})
+
+
+class Context:
+    """Owns one msa_ctx; `with Context(...) as h:` destroys it on exit."""
+
+    def __init__(self, matrix, letters, gap_open, gap_extend, **kw):
+        self.h = msa_create(matrix, letters, gap_open, gap_extend, **kw)
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def close(self):
+        if self.h:
+            msa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

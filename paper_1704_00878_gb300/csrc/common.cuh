@@ -1,0 +1,90 @@
+// common.cuh -- definitions shared by the CUDA translation units of libmsa.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "msa.h"
+
+#define MSA_FULL_MASK 0xffffffffu
+
+// Score given to padding rows (query positions past the end) and to the
+// padding residue code (subject positions past the end).  Any negative value
+// keeps every padded cell strictly below the best real cell: each padded H is
+// a real or padded neighbour minus a positive amount, or zero.
+#define MSA_PAD_SCORE (-100)
+
+// Residues of every loaded sequence sit at 16-byte aligned offsets followed by
+// at least MSA_SEQ_TAIL bytes of the padding code, so 16-byte loads that start
+// inside a sequence stay inside its allocation.
+#define MSA_SEQ_TAIL 16
+
+// Profile rows are padded to a multiple of this many bytes so that every
+// residue row of the profile starts on the same shared-memory bank.
+#define MSA_PROF_ALIGN 128
+
+// ---------------------------------------------------------------- DPX cells
+// One DP cell value is either an int32 or two int16 lanes packed in 32 bits
+// (lane 0 = first subject, lane 1 = second subject).  All arithmetic goes
+// through the Blackwell/Hopper DPX integer instructions.
+template <bool PACK> struct Cell;
+
+template <> struct Cell<false> {
+  static __host__ __device__ __forceinline__ int splat(int x) { return x; }
+  // max(a + b, c)
+  static __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
+  // max(a + b, c, 0)
+  static __device__ __forceinline__ int addmax_relu(int a, int b, int c) { return __viaddmax_s32_relu(a, b, c); }
+  static __device__ __forceinline__ int vmax(int a, int b) { return max(a, b); }
+  static __device__ __forceinline__ int vmax3(int a, int b, int c) { return __vimax3_s32(a, b, c); }
+  // a + b (both lanes when packed)
+  static __device__ __forceinline__ int add(int a, int b) { return a + b; }
+  // sign-extended score of byte `sel` of (wa) -- one PRMT
+  template <int B>
+  static __device__ __forceinline__ int score(uint32_t wa, uint32_t /*wb*/) {
+    int d;
+    constexpr uint32_t sel = B | ((B | 8) << 4) | ((B | 8) << 8) | ((B | 8) << 12);
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(wa), "r"(0u), "n"(sel));
+    return d;
+  }
+  static __device__ __forceinline__ int lane0(int v) { return v; }
+  static __device__ __forceinline__ int lane1(int v) { return v; }
+};
+
+template <> struct Cell<true> {
+  static __host__ __device__ __forceinline__ int splat(int x) {
+    return (int)(((uint32_t)x & 0xffffu) | ((uint32_t)x << 16));
+  }
+  static __device__ __forceinline__ int addmax(int a, int b, int c) {
+    return (int)__viaddmax_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
+  }
+  static __device__ __forceinline__ int addmax_relu(int a, int b, int c) {
+    return (int)__viaddmax_s16x2_relu((unsigned)a, (unsigned)b, (unsigned)c);
+  }
+  static __device__ __forceinline__ int vmax(int a, int b) { return (int)__vmaxs2((unsigned)a, (unsigned)b); }
+  static __device__ __forceinline__ int vmax3(int a, int b, int c) {
+    return (int)__vimax3_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
+  }
+  static __device__ __forceinline__ int add(int a, int b) { return (int)__vadd2((unsigned)a, (unsigned)b); }
+  // lane 0 <- sign-extended byte B of wa, lane 1 <- sign-extended byte B of wb
+  template <int B>
+  static __device__ __forceinline__ int score(uint32_t wa, uint32_t wb) {
+    int d;
+    constexpr uint32_t sel = B | ((B | 8) << 4) | ((B + 4) << 8) | (((B + 4) | 8) << 12);
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(wa), "r"(wb), "n"(sel));
+    return d;
+  }
+  static __device__ __forceinline__ int lane0(int v) { return (int)(int16_t)(v & 0xffff); }
+  static __device__ __forceinline__ int lane1(int v) { return (int)(int16_t)((uint32_t)v >> 16); }
+};
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int w) {
+  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+}
+
+// Device-side error word bits (ctx->d_err).
+#define MSA_DERR_LETTER   1u   // a letter outside the alphabet
+#define MSA_DERR_TRACE    2u   // inconsistent traceback codes
+#define MSA_DERR_OVERFLOW 4u   // overflow list full
+
+static inline int round_up_int(int x, int m) { return (x + m - 1) / m * m; }
+static inline int64_t round_up_i64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -1,0 +1,882 @@
+// msa_api.cu -- the C ABI (include/msa.h) and its host-side planner:
+// length sorting, work-item classes for the center kernels, batching of the
+// traceback codes, and the stage timers.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "msa.h"
+#include "msa_kernels.cuh"
+#include "sw_kernels.cuh"
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+enum Stage { ST_ENCODE = 0, ST_CENTER, ST_ALIGN, ST_TRACE, ST_MERGE, ST_ROWS, ST_SP, ST_CENTER_K, ST_ALIGN_K, ST_N };
+
+}  // namespace
+
+struct msa_ctx {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  int K = 0, o = 0, e = 0, precision = MSA_AUTO, sat_limit = 32767, smax = 0;
+  std::vector<int8_t> hM;
+  std::string letters;
+  uint8_t hlut[256];
+  std::string err;
+
+  // scoring tables on the device
+  int8_t *dM = nullptr;
+  char *dLetters = nullptr;
+  uint8_t *dLut = nullptr, *dSymLut = nullptr;
+
+  // the loaded set (sorted by length, ascending, stable)
+  int n = 0, maxlen = 0;
+  std::vector<int32_t> len_sorted, perm, inv;
+  std::vector<int64_t> pstart;
+  DevBuf res, d_pstart, d_len, d_perm, d_inv, d_srcoff, staging;
+
+  // center selection
+  DevBuf pairsum, self, rowsum, prefix, qlist, ovf, ovf_scores, ovf_dst, part_val, part_idx,
+      pairs, pair_dst, pair_out;
+  bool have_rowsum = false;
+
+  // alignment
+  int64_t center = -1;
+  int Lc = 0;
+  DevBuf ins, occ, seg, score, codes, code_off, best;
+  bool aligned = false;
+
+  // merge
+  DevBuf G, off, msa, counts;
+  int64_t W = 0;
+  bool merged = false;
+
+  // small device scalars: [0] counter, [1] err + ovf_count, [2..] totals
+  unsigned long long *dcounter = nullptr;
+  unsigned *derr = nullptr;     // derr[0] error bits, derr[1] overflow count
+  long long *dsmall = nullptr;  // [0] total, [1] argmin val, [2] argmin idx, [3] width, [4] sp
+  DevBuf scratch;
+
+  cudaEvent_t ev[2 * ST_N] = {};
+  float stage_ms[ST_N] = {};
+  int64_t cells[2] = {0, 0};
+  int64_t launches = 0;
+  size_t codes_budget = (size_t)4 << 30;
+};
+
+namespace {
+
+int fail(msa_ctx *c, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? MSA_ENOMEM : MSA_ECUDA,          \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+  } while (0)
+
+#define TRY(expr)              \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != MSA_OK) return r_; \
+  } while (0)
+
+int ensure(msa_ctx *ctx, DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return MSA_OK;
+  if (b.p) {
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  bytes = (bytes + 255) / 256 * 256;
+  CK(cudaMalloc(&b.p, bytes));
+  b.cap = bytes;
+  return MSA_OK;
+}
+
+template <class T> T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int set_device(msa_ctx *ctx) {
+  CK(cudaSetDevice(ctx->dev));
+  return MSA_OK;
+}
+
+void stage_begin(msa_ctx *ctx, int s) { cudaEventRecord(ctx->ev[2 * s], ctx->st); }
+void stage_end(msa_ctx *ctx, int s) { cudaEventRecord(ctx->ev[2 * s + 1], ctx->st); }
+void stage_collect(msa_ctx *ctx, int s) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, ctx->ev[2 * s], ctx->ev[2 * s + 1]) == cudaSuccess)
+    ctx->stage_ms[s] = ms;
+  else
+    cudaGetLastError();
+}
+
+int check_derr(msa_ctx *ctx) {
+  unsigned h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, ctx->derr, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (h[0] & MSA_DERR_LETTER) return fail(ctx, MSA_EINVAL, "letter outside the alphabet");
+  if (h[0] & MSA_DERR_TRACE) return fail(ctx, MSA_ECUDA, "inconsistent traceback codes");
+  if (h[0] & MSA_DERR_OVERFLOW) return fail(ctx, MSA_ENOMEM, "int16 overflow list full");
+  return MSA_OK;
+}
+
+SeqSet seqset(msa_ctx *ctx) {
+  return SeqSet{P<uint8_t>(ctx->res), P<int64_t>(ctx->d_pstart), P<int32_t>(ctx->d_len), ctx->n};
+}
+Scoring scoring(msa_ctx *ctx) { return Scoring{ctx->dM, ctx->K, ctx->o, ctx->e}; }
+
+// ------------------------------------------------------------ pair scores
+// Scores of (a, b) pairs given in sorted indices, int32 cells.  dst[x] is the
+// output slot of pair x.  Pairs are grouped by the query's pass height and
+// ordered by subject length so the groups of a warp stay in step.
+int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector<int32_t> &dst_in,
+              int32_t *d_out) {
+  const int np = (int)pairs_in.size();
+  if (np == 0) return MSA_OK;
+  std::vector<int32_t> order(np);
+  std::iota(order.begin(), order.end(), 0);
+  const int short_rows = pairs_rows(8);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const int ax = ctx->len_sorted[pairs_in[x].x] > short_rows;
+    const int ay = ctx->len_sorted[pairs_in[y].x] > short_rows;
+    if (ax != ay) return ax < ay;
+    const int lx = ctx->len_sorted[pairs_in[x].y], ly = ctx->len_sorted[pairs_in[y].y];
+    return lx < ly;
+  });
+  std::vector<int2> pr(np);
+  std::vector<int32_t> dst(np);
+  int n_short = 0;
+  for (int x = 0; x < np; ++x) {
+    pr[x] = pairs_in[order[x]];
+    dst[x] = dst_in[order[x]];
+    if (ctx->len_sorted[pr[x].x] <= short_rows) ++n_short;
+  }
+  TRY(ensure(ctx, ctx->pairs, sizeof(int2) * np));
+  TRY(ensure(ctx, ctx->pair_dst, sizeof(int32_t) * np));
+  CK(cudaMemcpyAsync(ctx->pairs.p, pr.data(), sizeof(int2) * np, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->pair_dst.p, dst.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice,
+                     ctx->st));
+  const SeqSet ss = seqset(ctx);
+  const Scoring sc = scoring(ctx);
+  for (int part = 0; part < 2; ++part) {
+    const int G = part == 0 ? 8 : 32;
+    const int b = part == 0 ? 0 : n_short, e = part == 0 ? n_short : np;
+    if (e <= b) continue;
+    const int grid = pairs_grid(G);
+    const size_t scr = (size_t)grid * (256 / G) * 2 * ctx->maxlen * sizeof(int2);
+    TRY(ensure(ctx, ctx->scratch, scr));
+    CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+    PairJob job;
+    job.pairs = P<int2>(ctx->pairs) + b;
+    job.dst = P<int32_t>(ctx->pair_dst) + b;
+    job.out = d_out;
+    job.npairs = e - b;
+    job.counter = ctx->dcounter;
+    job.scratch = P<int2>(ctx->scratch);
+    job.scratch_cols = ctx->maxlen;
+    CK((++ctx->launches, launch_pairs)(G, ss, sc, job, grid, ctx->st));
+  }
+  return MSA_OK;
+}
+
+// ------------------------------------------------------------ center planning
+// Pass height choice for one query: the packed kernel variant whose rows x
+// (columns + ramp) cost is smallest, with a small charge per extra pass.
+int choose_shape(int Lq, int Ls_est) {
+  int best = 0;
+  double best_cost = 1e300;
+  for (int s = 0; s < kNumCenterShapes; ++s) {
+    const int G = kCenterShapes[s].G, R = kCenterShapes[s].R;
+    const int rows = G * R;
+    const int np = (Lq + rows - 1) / rows;
+    const double cost = (double)np * rows * (Ls_est + G - 1 + 24) * (R == 8 ? 1.08 : 1.0);
+    if (cost < best_cost) { best_cost = cost; best = s; }
+  }
+  return best;
+}
+
+struct ClassRange {
+  int shape, qb, qe, npass;
+};
+
+// Split an ascending list of query lengths into contiguous runs with the same
+// kernel variant.
+std::vector<ClassRange> plan_classes(const std::vector<int> &qlen, bool packed, int Ls_est_mode,
+                                     double Ls_mean) {
+  std::vector<ClassRange> out;
+  const int nq = (int)qlen.size();
+  int x = 0;
+  while (x < nq) {
+    const int Lq = qlen[x];
+    const int shape = packed ? choose_shape(Lq, Ls_est_mode ? (int)Ls_mean : Lq) : 8;
+    int y = x + 1;
+    while (y < nq) {
+      const int s2 = packed ? choose_shape(qlen[y], Ls_est_mode ? (int)Ls_mean : qlen[y]) : 8;
+      if (s2 != shape) break;
+      ++y;
+    }
+    const int rows = kCenterShapes[shape].G * kCenterShapes[shape].R;
+    const int np = (qlen[y - 1] + rows - 1) / rows;
+    out.push_back({shape, x, y, np});
+    x = y;
+  }
+  return out;
+}
+
+bool use_packed(msa_ctx *ctx, int Lq) {
+  if (ctx->precision == MSA_INT32) return false;
+  if (ctx->precision == MSA_INT16) return true;
+  // a-priori bound on any local score involving a sequence of length Lq
+  const long long bound = (long long)Lq * ctx->smax;
+  return bound <= (long long)ctx->sat_limit - ctx->smax;
+}
+
+int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
+  // qsorted: ascending sorted indices of the queries (mode 1); mode 0 uses all.
+  const int n = ctx->n;
+  const SeqSet ss = seqset(ctx);
+  const Scoring sc = scoring(ctx);
+  std::vector<int> qlen;
+  if (mode == 0) qlen.assign(ctx->len_sorted.begin(), ctx->len_sorted.end());
+  else for (int q : qsorted) qlen.push_back(ctx->len_sorted[q]);
+  double mean = 0;
+  for (int k = 0; k < n; ++k) mean += ctx->len_sorted[k];
+  mean /= n;
+  std::vector<int64_t> suffix(n + 1, 0);
+  for (int k = n - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + ctx->len_sorted[k];
+
+  if (mode == 1) {
+    TRY(ensure(ctx, ctx->qlist, sizeof(int32_t) * qsorted.size()));
+    CK(cudaMemcpyAsync(ctx->qlist.p, qsorted.data(), sizeof(int32_t) * qsorted.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+  }
+  // split the (ascending) query list into a packed run and an int32 run: a
+  // local score is at most min(Lq, Ls) * smax <= Lq * smax, so the query
+  // length alone decides whether int16 lanes are safe
+  std::vector<std::pair<int, int>> runs;  // [b, e) with packing flag
+  std::vector<bool> packed_of;
+  {
+    int x = 0;
+    const int nq = (int)qlen.size();
+    while (x < nq) {
+      const bool pk = use_packed(ctx, qlen[x]);
+      int y = x + 1;
+      while (y < nq && use_packed(ctx, qlen[y]) == pk) ++y;
+      runs.push_back({x, y});
+      packed_of.push_back(pk);
+      x = y;
+    }
+  }
+  int64_t cells = 0;
+  float center_ms = 0.f;
+  for (size_t ri = 0; ri < runs.size(); ++ri) {
+    const bool pk = packed_of[ri];
+    std::vector<int> sub(qlen.begin() + runs[ri].first, qlen.begin() + runs[ri].second);
+    std::vector<ClassRange> cls = plan_classes(sub, pk, mode, mean);
+    for (ClassRange cr : cls) {
+      cr.qb += runs[ri].first;
+      cr.qe += runs[ri].first;
+      const int G = kCenterShapes[cr.shape].G, R = kCenterShapes[cr.shape].R;
+      const int spi = (kCenterThreads / G) * (pk ? 2 : 1);
+      std::vector<int64_t> prefix(cr.qe - cr.qb + 1, 0);
+      for (int x = cr.qb; x < cr.qe; ++x) {
+        const int nsub = mode == 0 ? n - x : n;
+        prefix[x - cr.qb + 1] = prefix[x - cr.qb] + (nsub + spi - 1) / spi;
+      }
+      if (mode == 0)  // real cells: q against subjects [q, n)
+        for (int x = cr.qb; x < cr.qe; ++x) cells += (int64_t)ctx->len_sorted[x] * suffix[x];
+      TRY(ensure(ctx, ctx->prefix, sizeof(int64_t) * prefix.size()));
+      CK(cudaMemcpyAsync(ctx->prefix.p, prefix.data(), sizeof(int64_t) * prefix.size(),
+                         cudaMemcpyHostToDevice, ctx->st));
+      const int smem = center_smem_bytes(ctx->K, cr.npass * G * R);
+      const int grid = center_grid(cr.shape, pk, smem);
+      if (cr.npass > 1) {
+        const size_t scr = (size_t)grid * (kCenterThreads / G) * 2 * ctx->maxlen * sizeof(int2);
+        TRY(ensure(ctx, ctx->scratch, scr));
+      }
+      CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+      CenterJob job;
+      job.mode = mode;
+      job.qlist = P<int32_t>(ctx->qlist);
+      job.qb = cr.qb;
+      job.qe = cr.qe;
+      job.prefix = P<int64_t>(ctx->prefix);
+      job.n_items = prefix.back();
+      job.npass = cr.npass;
+      job.counter = ctx->dcounter;
+      job.pairsum = P<unsigned long long>(ctx->pairsum);
+      job.self = P<int32_t>(ctx->self);
+      job.sat_thresh = ctx->sat_limit - ctx->smax;
+      job.ovf = P<int2>(ctx->ovf);
+      job.ovf_count = ctx->derr + 1;
+      job.ovf_cap = (int)(ctx->ovf.cap / sizeof(int2));
+      job.err = ctx->derr;
+      job.scratch = P<int2>(ctx->scratch);
+      job.scratch_cols = ctx->maxlen;
+      stage_begin(ctx, ST_CENTER_K);
+      CK((++ctx->launches, launch_center)(cr.shape, pk, ss, sc, job, grid, ctx->st));
+      stage_end(ctx, ST_CENTER_K);
+      // the prefix buffer is reused by the next class: wait for this one
+      CK(cudaStreamSynchronize(ctx->st));
+      stage_collect(ctx, ST_CENTER_K);
+      center_ms += ctx->stage_ms[ST_CENTER_K];
+    }
+  }
+  if (mode == 1) {
+    double sumL = 0;
+    for (int k = 0; k < n; ++k) sumL += ctx->len_sorted[k];
+    for (int q : qsorted) cells += (int64_t)((double)ctx->len_sorted[q] * sumL);
+  }
+  ctx->cells[0] = cells;
+  ctx->stage_ms[ST_CENTER_K] = center_ms;
+
+  // pairs whose packed lanes may have overflowed: recompute in int32
+  unsigned h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, ctx->derr, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (h[0] & MSA_DERR_OVERFLOW) return fail(ctx, MSA_ENOMEM, "int16 overflow list full");
+  if (h[1] > 0) {
+    const int cnt = (int)h[1];
+    std::vector<int2> ov(cnt);
+    CK(cudaMemcpyAsync(ov.data(), ctx->ovf.p, sizeof(int2) * cnt, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<int32_t> dst(cnt);
+    std::iota(dst.begin(), dst.end(), 0);
+    TRY(ensure(ctx, ctx->ovf_scores, sizeof(int32_t) * cnt));
+    TRY(run_pairs(ctx, ov, dst, P<int32_t>(ctx->ovf_scores)));
+    CK((++ctx->launches, launch_apply_overflow)(mode == 0 ? 0 : 1, P<int2>(ctx->ovf), P<int32_t>(ctx->ovf_scores), cnt,
+                             P<unsigned long long>(ctx->pairsum), P<int32_t>(ctx->self), ctx->st));
+  }
+  return MSA_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+int msa_create(msa_ctx **out, const msa_params *p, void *cuda_stream) {
+  msa_ctx *ctx = nullptr;
+  if (!out || !p) return MSA_EINVAL;
+  *out = nullptr;
+  if (p->alphabet < 1 || p->alphabet > MSA_MAX_ALPHABET || !p->matrix || !p->letters)
+    return MSA_EINVAL;
+  if (p->gap_extend < 1 || p->gap_open < p->gap_extend || p->gap_open > 1000) return MSA_EINVAL;
+  if (p->precision < MSA_AUTO || p->precision > MSA_INT32) return MSA_EINVAL;
+  if ((int)strlen(p->letters) != p->alphabet) return MSA_EINVAL;
+  for (int a = 0; a < p->alphabet; ++a) {
+    if (p->letters[a] == '-') return MSA_EINVAL;
+    for (int b = 0; b < p->alphabet; ++b) {
+      if (p->matrix[a * p->alphabet + b] != p->matrix[b * p->alphabet + a]) return MSA_EINVAL;
+    }
+    for (int b = 0; b < a; ++b)
+      if (p->letters[a] == p->letters[b]) return MSA_EINVAL;
+  }
+  ctx = new (std::nothrow) msa_ctx;
+  if (!ctx) return MSA_ENOMEM;
+  ctx->K = p->alphabet;
+  ctx->o = p->gap_open;
+  ctx->e = p->gap_extend;
+  ctx->precision = p->precision;
+  ctx->sat_limit = p->sat_limit > 0 ? std::min(p->sat_limit, 32767) : 32767;
+  ctx->hM.assign(p->matrix, p->matrix + ctx->K * ctx->K);
+  ctx->letters.assign(p->letters, p->letters + ctx->K);
+  ctx->smax = 0;
+  for (int8_t v : ctx->hM) ctx->smax = std::max<int>(ctx->smax, v);
+  memset(ctx->hlut, 255, sizeof ctx->hlut);
+  for (int a = 0; a < ctx->K; ++a) ctx->hlut[(uint8_t)ctx->letters[a]] = (uint8_t)a;
+  ctx->st = (cudaStream_t)cuda_stream;
+
+  auto init = [&]() -> int {
+    CK(cudaGetDevice(&ctx->dev));
+    CK(cudaMalloc(&ctx->dM, MSA_MAX_ALPHABET * MSA_MAX_ALPHABET));
+    CK(cudaMemcpy(ctx->dM, ctx->hM.data(), ctx->hM.size(), cudaMemcpyHostToDevice));
+    char lt[MSA_MAX_ALPHABET + 1] = {0};
+    memcpy(lt, ctx->letters.data(), ctx->K);
+    lt[ctx->K] = '-';
+    CK(cudaMalloc(&ctx->dLetters, sizeof lt));
+    CK(cudaMemcpy(ctx->dLetters, lt, sizeof lt, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->dLut, 256));
+    CK(cudaMemcpy(ctx->dLut, ctx->hlut, 256, cudaMemcpyHostToDevice));
+    // SP symbols: letters 0..K-1, any other byte K, the gap '-' last (K+1)
+    uint8_t sym[256];
+    memset(sym, ctx->K, sizeof sym);
+    for (int a = 0; a < ctx->K; ++a) sym[(uint8_t)ctx->letters[a]] = (uint8_t)a;
+    sym[(uint8_t)'-'] = (uint8_t)(ctx->K + 1);
+    CK(cudaMalloc(&ctx->dSymLut, 256));
+    CK(cudaMemcpy(ctx->dSymLut, sym, 256, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->dcounter, sizeof(unsigned long long)));
+    CK(cudaMalloc(&ctx->derr, 2 * sizeof(unsigned)));
+    CK(cudaMemset(ctx->derr, 0, 2 * sizeof(unsigned)));
+    CK(cudaMalloc(&ctx->dsmall, 8 * sizeof(long long)));
+    for (auto &ev : ctx->ev) CK(cudaEventCreate(&ev));
+    TRY(ensure(ctx, ctx->ovf, sizeof(int2) * (1 << 20)));
+    return MSA_OK;
+  };
+  int rc = init();
+  if (rc != MSA_OK) {
+    msa_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return MSA_OK;
+}
+
+void msa_destroy(msa_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  DevBuf *bufs[] = {&ctx->res, &ctx->d_pstart, &ctx->d_len, &ctx->d_perm, &ctx->d_inv,
+                    &ctx->d_srcoff, &ctx->staging, &ctx->pairsum, &ctx->self, &ctx->rowsum,
+                    &ctx->prefix, &ctx->qlist, &ctx->ovf, &ctx->ovf_scores, &ctx->ovf_dst,
+                    &ctx->part_val, &ctx->part_idx, &ctx->pairs, &ctx->pair_dst,
+                    &ctx->pair_out, &ctx->ins, &ctx->occ, &ctx->seg, &ctx->score,
+                    &ctx->codes, &ctx->code_off, &ctx->best, &ctx->G, &ctx->off, &ctx->msa,
+                    &ctx->counts, &ctx->scratch};
+  for (DevBuf *b : bufs)
+    if (b->p) cudaFree(b->p);
+  cudaFree(ctx->dM);
+  cudaFree(ctx->dLetters);
+  cudaFree(ctx->dLut);
+  cudaFree(ctx->dSymLut);
+  cudaFree(ctx->dcounter);
+  cudaFree(ctx->derr);
+  cudaFree(ctx->dsmall);
+  for (auto &ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+const char *msa_last_error(const msa_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int msa_load(msa_ctx *ctx, const uint8_t *letters, const int64_t *offsets, int64_t n) {
+  if (!ctx) return MSA_EINVAL;
+  if (!letters || !offsets || n < 1) return fail(ctx, MSA_EINVAL, "empty input");
+  if (n > (int64_t)INT32_MAX / 2) return fail(ctx, MSA_ERANGE, "too many sequences");
+  if (offsets[0] != 0) return fail(ctx, MSA_EINVAL, "offsets[0] must be 0");
+  TRY(set_device(ctx));
+  std::vector<int32_t> lens(n);
+  int maxlen = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t L = offsets[t + 1] - offsets[t];
+    if (L <= 0) return fail(ctx, MSA_EINVAL, "sequence %lld is empty", (long long)t);
+    if (L > MSA_MAX_LEN) return fail(ctx, MSA_ERANGE, "sequence %lld longer than %d", (long long)t, MSA_MAX_LEN);
+    lens[t] = (int32_t)L;
+    maxlen = std::max(maxlen, (int)L);
+  }
+  ctx->aligned = ctx->merged = ctx->have_rowsum = false;
+  ctx->n = (int)n;
+  ctx->maxlen = maxlen;
+  ctx->perm.resize(n);
+  std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
+  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
+                   [&](int32_t a, int32_t b) { return lens[a] < lens[b]; });
+  ctx->inv.resize(n);
+  ctx->len_sorted.resize(n);
+  ctx->pstart.resize(n);
+  int64_t pos = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    ctx->inv[ctx->perm[k]] = (int32_t)k;
+    ctx->len_sorted[k] = lens[ctx->perm[k]];
+    ctx->pstart[k] = pos;
+    pos += round_up_i64(ctx->len_sorted[k], 16) + MSA_SEQ_TAIL;
+  }
+  const int64_t total = offsets[n];
+  TRY(ensure(ctx, ctx->res, pos));
+  TRY(ensure(ctx, ctx->d_pstart, sizeof(int64_t) * n));
+  TRY(ensure(ctx, ctx->d_len, sizeof(int32_t) * n));
+  TRY(ensure(ctx, ctx->d_perm, sizeof(int32_t) * n));
+  TRY(ensure(ctx, ctx->d_inv, sizeof(int32_t) * n));
+  TRY(ensure(ctx, ctx->d_srcoff, sizeof(int64_t) * (n + 1)));
+  TRY(ensure(ctx, ctx->pairsum, sizeof(unsigned long long) * n));
+  TRY(ensure(ctx, ctx->self, sizeof(int32_t) * n));
+  TRY(ensure(ctx, ctx->rowsum, sizeof(long long) * n));
+  TRY(ensure(ctx, ctx->part_val, sizeof(long long) * 1024));
+  TRY(ensure(ctx, ctx->part_idx, sizeof(long long) * 1024));
+  stage_begin(ctx, ST_ENCODE);
+  const uint8_t *src = letters;
+  if (!is_device_ptr(letters)) {
+    TRY(ensure(ctx, ctx->staging, total));
+    CK(cudaMemcpyAsync(ctx->staging.p, letters, total, cudaMemcpyHostToDevice, ctx->st));
+    src = P<uint8_t>(ctx->staging);
+  }
+  CK(cudaMemcpyAsync(ctx->d_pstart.p, ctx->pstart.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_len.p, ctx->len_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_perm.p, ctx->perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_inv.p, ctx->inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_srcoff.p, offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+  CK((++ctx->launches, launch_encode)(src, P<int64_t>(ctx->d_srcoff), P<int32_t>(ctx->d_perm), P<int64_t>(ctx->d_pstart),
+                   P<int32_t>(ctx->d_len), ctx->n, ctx->dLut, ctx->K, P<uint8_t>(ctx->res), ctx->derr,
+                   ctx->st));
+  stage_end(ctx, ST_ENCODE);
+  int rc = check_derr(ctx);
+  stage_collect(ctx, ST_ENCODE);
+  if (rc != MSA_OK) {
+    ctx->n = 0;
+    return rc;
+  }
+  return MSA_OK;
+}
+
+int msa_pair_scores(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, int32_t *scores_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  if (npairs < 0 || (npairs > 0 && (!pairs || !scores_out))) return fail(ctx, MSA_EINVAL, "bad pair list");
+  if (npairs == 0) return MSA_OK;
+  if (npairs > INT32_MAX / 2) return fail(ctx, MSA_ERANGE, "too many pairs");
+  TRY(set_device(ctx));
+  std::vector<int2> pr(npairs);
+  std::vector<int32_t> dst(npairs);
+  for (int64_t x = 0; x < npairs; ++x) {
+    const int64_t a = pairs[2 * x], b = pairs[2 * x + 1];
+    if (a < 0 || b < 0 || a >= ctx->n || b >= ctx->n) return fail(ctx, MSA_EINVAL, "pair index out of range");
+    pr[x] = make_int2(ctx->inv[a], ctx->inv[b]);
+    dst[x] = (int32_t)x;
+  }
+  TRY(ensure(ctx, ctx->pair_out, sizeof(int32_t) * npairs));
+  TRY(run_pairs(ctx, pr, dst, P<int32_t>(ctx->pair_out)));
+  CK(cudaMemcpyAsync(scores_out, ctx->pair_out.p, sizeof(int32_t) * npairs, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
+}
+
+int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
+                      int64_t *center_out, int64_t *sum_dist_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (!center_out) return fail(ctx, MSA_EINVAL, "center_out is NULL");
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  TRY(set_device(ctx));
+  if (sum_dist_out) *sum_dist_out = 0;
+  if (mode == MSA_CENTER_FIRST) {
+    *center_out = 0;
+    return MSA_OK;
+  }
+  if (mode == MSA_CENTER_LEARNED) return fail(ctx, MSA_ESTATE, "no trained selector loaded");
+  if (mode != MSA_CENTER_EXACT && mode != MSA_CENTER_EXACT_SAMPLED)
+    return fail(ctx, MSA_EINVAL, "unknown center mode %d", mode);
+  const int n = ctx->n;
+  std::vector<int32_t> qs;
+  if (mode == MSA_CENTER_EXACT_SAMPLED) {
+    if (!refs || nref < 1 || nref > n) return fail(ctx, MSA_EINVAL, "bad reference list");
+    std::vector<char> seen(n, 0);
+    for (int64_t r = 0; r < nref; ++r) {
+      if (refs[r] < 0 || refs[r] >= n) return fail(ctx, MSA_EINVAL, "reference index out of range");
+      if (seen[refs[r]]) return fail(ctx, MSA_EINVAL, "duplicate reference index");
+      seen[refs[r]] = 1;
+      qs.push_back(ctx->inv[refs[r]]);
+    }
+    std::sort(qs.begin(), qs.end());
+  }
+  stage_begin(ctx, ST_CENTER);
+  CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
+  CK(cudaMemsetAsync(ctx->self.p, 0, sizeof(int32_t) * n, ctx->st));
+  CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+  TRY(run_center(ctx, mode == MSA_CENTER_EXACT ? 0 : 1, qs));
+  if (mode == MSA_CENTER_EXACT_SAMPLED) {
+    // self scores of every sequence
+    std::vector<int2> sp(n);
+    std::vector<int32_t> dst(n);
+    for (int k = 0; k < n; ++k) { sp[k] = make_int2(k, k); dst[k] = k; }
+    TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
+    double sumsq = 0;
+    for (int k = 0; k < n; ++k) sumsq += (double)ctx->len_sorted[k] * ctx->len_sorted[k];
+    ctx->cells[0] += (int64_t)sumsq;
+  }
+  CK((++ctx->launches, launch_center_finalize)(mode == MSA_CENTER_EXACT ? 0 : 1, n, (int)qs.size(), P<int32_t>(ctx->d_perm),
+                            P<int32_t>(ctx->self), P<unsigned long long>(ctx->pairsum),
+                            P<int32_t>(ctx->qlist), ctx->dsmall, P<long long>(ctx->rowsum),
+                            ctx->dsmall + 1, ctx->dsmall + 2, P<long long>(ctx->part_val),
+                            P<long long>(ctx->part_idx), ctx->st));
+  stage_end(ctx, ST_CENTER);
+  long long h[3];
+  CK(cudaMemcpyAsync(h, ctx->dsmall, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  TRY(check_derr(ctx));
+  stage_collect(ctx, ST_CENTER);
+  *center_out = h[2];
+  if (sum_dist_out) *sum_dist_out = h[1];
+  ctx->have_rowsum = true;
+  return MSA_OK;
+}
+
+int msa_center_rowsums(msa_ctx *ctx, int64_t *rowsum_out) {
+  if (!ctx || !rowsum_out) return MSA_EINVAL;
+  if (!ctx->have_rowsum) return fail(ctx, MSA_ESTATE, "no exact center selection yet");
+  TRY(set_device(ctx));
+  CK(cudaMemcpyAsync(rowsum_out, ctx->rowsum.p, sizeof(int64_t) * ctx->n, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
+}
+
+int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  if (center < 0 || center >= ctx->n) return fail(ctx, MSA_EINVAL, "center index out of range");
+  TRY(set_device(ctx));
+  const int n = ctx->n;
+  const int kc = ctx->inv[center];
+  const int Lc = ctx->len_sorted[kc];
+  ctx->aligned = ctx->merged = false;
+  ctx->center = center;
+  ctx->Lc = Lc;
+  const int R = kCodesR, G = kCodesG;
+  const int nblk = (Lc + R - 1) / R;
+  const int npass = (Lc + G * R - 1) / (G * R);
+  const size_t row = (size_t)Lc + 1;
+  TRY(ensure(ctx, ctx->ins, sizeof(uint16_t) * row * n));
+  TRY(ensure(ctx, ctx->occ, row * n));
+  TRY(ensure(ctx, ctx->seg, sizeof(int32_t) * 5 * n));
+  TRY(ensure(ctx, ctx->score, sizeof(int32_t) * n));
+  CK(cudaMemsetAsync(ctx->ins.p, 0, sizeof(uint16_t) * row * n, ctx->st));
+  CK(cudaMemsetAsync(ctx->occ.p, 0, row * n, ctx->st));
+  CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+
+  // batches of subjects (sorted order) whose codes fit the budget
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  size_t budget = std::min(ctx->codes_budget, free_b / 2);
+  size_t max_one = (size_t)nblk * ctx->maxlen * 8;
+  if (budget < max_one) budget = max_one;
+  std::vector<std::pair<int, int>> batches;
+  std::vector<int64_t> offs(n);
+  size_t biggest = 0;
+  {
+    int b = 0;
+    size_t acc = 0;
+    for (int k = 0; k < n; ++k) {
+      const size_t sz = (size_t)nblk * ctx->len_sorted[k] * 8;
+      if (acc + sz > budget && k > b) {
+        batches.push_back({b, k});
+        biggest = std::max(biggest, acc);
+        b = k;
+        acc = 0;
+      }
+      offs[k] = (int64_t)acc;
+      acc += sz;
+    }
+    batches.push_back({b, n});
+    biggest = std::max(biggest, acc);
+  }
+  TRY(ensure(ctx, ctx->codes, biggest));
+  TRY(ensure(ctx, ctx->code_off, sizeof(int64_t) * n));
+  TRY(ensure(ctx, ctx->best, sizeof(int32_t) * 3 * n));
+  CK(cudaMemcpyAsync(ctx->code_off.p, offs.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  const SeqSet ss = seqset(ctx);
+  const Scoring sc = scoring(ctx);
+  const int smem = codes_smem_bytes(ctx->K, npass * G * R);
+  const int grid = codes_grid(smem);
+  if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * 8 * 2 * ctx->maxlen * sizeof(int2)));
+  float ms_dp = 0.f, ms_tb = 0.f;
+  int64_t cells = 0;
+  for (int k = 0; k < n; ++k) cells += (int64_t)Lc * ctx->len_sorted[k];
+  for (auto [sb, se] : batches) {
+    stage_begin(ctx, ST_ALIGN);
+    CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+    CodesJob job;
+    job.center = kc;
+    job.sb = sb;
+    job.se = se;
+    job.code_off = P<int64_t>(ctx->code_off) + sb;
+    job.codes = P<uint8_t>(ctx->codes);
+    job.best = P<int32_t>(ctx->best) + 3 * (size_t)sb;
+    job.npass = npass;
+    job.counter = ctx->dcounter;
+    job.scratch = P<int2>(ctx->scratch);
+    job.scratch_cols = ctx->maxlen;
+    // offsets inside the batch are relative to the batch start
+    CK((++ctx->launches, launch_codes)(ss, sc, job, grid, ctx->st));
+    stage_end(ctx, ST_ALIGN);
+    stage_begin(ctx, ST_TRACE);
+    CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
+                        P<int32_t>(ctx->best) + 3 * (size_t)sb, sb, se, P<int32_t>(ctx->d_len),
+                        P<int32_t>(ctx->d_perm), Lc, P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ),
+                        P<int32_t>(ctx->seg), P<int32_t>(ctx->score), ctx->derr, ctx->st));
+    stage_end(ctx, ST_TRACE);
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_ALIGN);
+    stage_collect(ctx, ST_TRACE);
+    ms_dp += ctx->stage_ms[ST_ALIGN];
+    ms_tb += ctx->stage_ms[ST_TRACE];
+  }
+  ctx->stage_ms[ST_ALIGN] = ms_dp;
+  ctx->stage_ms[ST_ALIGN_K] = ms_dp;
+  ctx->stage_ms[ST_TRACE] = ms_tb;
+  ctx->cells[1] = cells;
+  TRY(check_derr(ctx));
+  if (scores_out) {
+    CK(cudaMemcpyAsync(scores_out, ctx->score.p, sizeof(int32_t) * n, cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  ctx->aligned = true;
+  return MSA_OK;
+}
+
+int msa_alignment_info(msa_ctx *ctx, int32_t *seg_out, uint16_t *ins_out, uint8_t *occ_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (!ctx->aligned) return fail(ctx, MSA_ESTATE, "no alignment yet");
+  TRY(set_device(ctx));
+  const size_t n = ctx->n, row = (size_t)ctx->Lc + 1;
+  if (seg_out) CK(cudaMemcpyAsync(seg_out, ctx->seg.p, sizeof(int32_t) * 5 * n, cudaMemcpyDefault, ctx->st));
+  if (ins_out) CK(cudaMemcpyAsync(ins_out, ctx->ins.p, sizeof(uint16_t) * row * n, cudaMemcpyDefault, ctx->st));
+  if (occ_out) CK(cudaMemcpyAsync(occ_out, ctx->occ.p, row * n, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
+}
+
+int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
+  if (!ctx || !codes_out) return MSA_EINVAL;
+  if (!ctx->aligned) return fail(ctx, MSA_ESTATE, "no alignment yet");
+  if (seq < 0 || seq >= ctx->n) return fail(ctx, MSA_EINVAL, "sequence index out of range");
+  TRY(set_device(ctx));
+  // recompute the codes of this one subject into a private buffer
+  const int ks = ctx->inv[seq], kc = ctx->inv[ctx->center];
+  const int Lc = ctx->Lc, Ls = ctx->len_sorted[ks];
+  const int R = kCodesR, G = kCodesG, nblk = (Lc + R - 1) / R, npass = (Lc + G * R - 1) / (G * R);
+  const size_t bytes = (size_t)nblk * Ls * 8;
+  DevBuf cb, ob, bb, ib, oc, sg, sc_;
+  auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb, &ib, &oc, &sg, &sc_}) if (b->p) cudaFree(b->p); };
+  int rc = [&]() -> int {
+    TRY(ensure(ctx, cb, bytes));
+    TRY(ensure(ctx, ob, sizeof(int64_t)));
+    TRY(ensure(ctx, bb, sizeof(int32_t) * 3));
+    CK(cudaMemsetAsync(ob.p, 0, sizeof(int64_t), ctx->st));
+    CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+    const int smem = codes_smem_bytes(ctx->K, npass * G * R);
+    const int grid = 1;
+    if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(smem) * 8 * 2 * ctx->maxlen * sizeof(int2)));
+    CodesJob job;
+    job.center = kc;
+    job.sb = ks;
+    job.se = ks + 1;
+    job.code_off = P<int64_t>(ob);
+    job.codes = P<uint8_t>(cb);
+    job.best = P<int32_t>(bb);
+    job.npass = npass;
+    job.counter = ctx->dcounter;
+    job.scratch = P<int2>(ctx->scratch);
+    job.scratch_cols = ctx->maxlen;
+    CK((++ctx->launches, launch_codes)(seqset(ctx), scoring(ctx), job, grid, ctx->st));
+    std::vector<uint8_t> packed(bytes), out((size_t)Lc * Ls);
+    CK(cudaMemcpyAsync(packed.data(), cb.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int i = 0; i < Lc; ++i)
+      for (int j = 0; j < Ls; ++j) {
+        const size_t at = ((size_t)(i >> 4) * Ls + j) * 8 + ((i & 15) >> 1);
+        out[(size_t)i * Ls + j] = (packed[at] >> ((i & 1) * 4)) & 15;
+      }
+    CK(cudaMemcpyAsync(codes_out, out.data(), out.size(), cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MSA_OK;
+  }();
+  cleanup();
+  return rc;
+}
+
+int msa_merge_gaps(msa_ctx *ctx, uint8_t *msa_out, int64_t *width_out) {
+  if (!ctx || !width_out) return MSA_EINVAL;
+  if (!ctx->aligned) return fail(ctx, MSA_ESTATE, "align to a center first");
+  TRY(set_device(ctx));
+  const int n = ctx->n, Lc = ctx->Lc;
+  if (!ctx->merged) {
+    TRY(ensure(ctx, ctx->G, sizeof(int32_t) * (Lc + 1)));
+    TRY(ensure(ctx, ctx->off, sizeof(int32_t) * (Lc + 1)));
+    stage_begin(ctx, ST_MERGE);
+    CK(cudaMemsetAsync(ctx->G.p, 0, sizeof(int32_t) * (Lc + 1), ctx->st));
+    CK((++ctx->launches, launch_colmax)(P<uint16_t>(ctx->ins), n, Lc, P<int32_t>(ctx->G), ctx->st));
+    CK((++ctx->launches, launch_scan)(P<int32_t>(ctx->G), Lc, P<int32_t>(ctx->off), (int64_t *)(ctx->dsmall + 3), ctx->st));
+    stage_end(ctx, ST_MERGE);
+    long long W = 0;
+    CK(cudaMemcpyAsync(&W, ctx->dsmall + 3, sizeof W, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_MERGE);
+    ctx->W = W;
+    TRY(ensure(ctx, ctx->msa, (size_t)n * (size_t)W));
+    stage_begin(ctx, ST_ROWS);
+    CK((++ctx->launches, launch_rows)(P<uint8_t>(ctx->res), P<int64_t>(ctx->d_pstart), P<int32_t>(ctx->d_inv),
+                   P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->G),
+                   P<int32_t>(ctx->off), n, Lc, W, ctx->dLetters, P<uint8_t>(ctx->msa), ctx->st));
+    stage_end(ctx, ST_ROWS);
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_ROWS);
+    ctx->merged = true;
+  }
+  *width_out = ctx->W;
+  if (msa_out) {
+    CK(cudaMemcpyAsync(msa_out, ctx->msa.p, (size_t)n * (size_t)ctx->W, cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return MSA_OK;
+}
+
+int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out) {
+  if (!ctx || !sp_cost_out) return MSA_EINVAL;
+  if (!ctx->merged) return fail(ctx, MSA_ESTATE, "merge first");
+  TRY(set_device(ctx));
+  const int nsym = ctx->K + 2;
+  TRY(ensure(ctx, ctx->counts, sizeof(int32_t) * nsym * (size_t)ctx->W));
+  stage_begin(ctx, ST_SP);
+  CK(cudaMemsetAsync(ctx->counts.p, 0, sizeof(int32_t) * nsym * (size_t)ctx->W, ctx->st));
+  CK(cudaMemsetAsync(ctx->dsmall + 4, 0, sizeof(long long), ctx->st));
+  CK((++ctx->launches, launch_sp)(P<uint8_t>(ctx->msa), ctx->n, ctx->W, ctx->dSymLut, nsym, P<int32_t>(ctx->counts),
+               (unsigned long long *)(ctx->dsmall + 4), ctx->st));
+  stage_end(ctx, ST_SP);
+  long long v = 0;
+  CK(cudaMemcpyAsync(&v, ctx->dsmall + 4, sizeof v, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_SP);
+  *sp_cost_out = v;
+  return MSA_OK;
+}
+
+int msa_dims(msa_ctx *ctx, int64_t *dims_out) {
+  if (!ctx || !dims_out) return MSA_EINVAL;
+  dims_out[0] = ctx->n;
+  dims_out[1] = ctx->aligned ? ctx->center : -1;
+  dims_out[2] = ctx->aligned ? ctx->Lc : 0;
+  dims_out[3] = ctx->merged ? ctx->W : 0;
+  return MSA_OK;
+}
+
+int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_out) {
+  if (!ctx) return MSA_EINVAL;
+  for (int i = 0; i < n && i < ST_N; ++i) ms_out[i] = ctx->stage_ms[i];
+  if (counters_out) {
+    counters_out[0] = ctx->cells[0];
+    counters_out[1] = ctx->cells[1];
+    counters_out[2] = ctx->launches;
+  }
+  return MSA_OK;
+}
+
+}  // extern "C"

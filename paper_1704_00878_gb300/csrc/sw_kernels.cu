@@ -1,0 +1,544 @@
+// sw_kernels.cu -- affine-gap Smith-Waterman fills (HAlign-II Eq. 1-2 in
+// Gotoh's form) as anti-diagonal wavefronts over groups of G threads.
+//
+// A group of G lanes owns one pass of G*R query rows: lane t holds rows
+// [t*R, t*R+R) in registers and, at step k, fills column j = k - t of the
+// subject.  The bottom row of lane t (H and F) reaches lane t+1 through a warp
+// shuffle one step later, so the whole pass advances one anti-diagonal per
+// step without shared-memory traffic.  Queries longer than G*R rows take
+// several passes; the bottom row of one pass (H and F per column) is kept in a
+// small per-group global buffer for the next.
+//
+// Scores come from a query profile in shared memory: prof[r*stride + i] =
+// s(query_i, r), with every residue row starting on the same bank so the
+// lanes of a group (which read consecutive row blocks) never conflict.
+//
+// Per cell, with X = H - o carried down the column and E/F the horizontal /
+// vertical gap scores (all DPX instructions):
+//   D = max(Hdiag + s, E, 0);  F = max(F - e, Xup);  H = max(D, F);
+//   X = H - o;  E' = max(E - e, X);  best = max(best, H)
+// Packed mode keeps two subjects in the int16 halves of each register.
+#include "sw_kernels.cuh"
+#include <climits>
+#include <type_traits>
+
+namespace {
+
+template <int N, int I = 0> struct Unroll {
+  template <class F> __device__ __forceinline__ static void run(F &&f) {
+    f(std::integral_constant<int, I>{});
+    Unroll<N, I + 1>::run(f);
+  }
+};
+template <int N> struct Unroll<N, N> {
+  template <class F> __device__ __forceinline__ static void run(F &&) {}
+};
+
+__device__ __forceinline__ int dround_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// The R profile bytes of one residue row for one lane, as 32-bit words.
+template <int R> struct ProfRow {
+  uint32_t w[R / 4];
+  __device__ __forceinline__ void load(const int8_t *p) {
+    if constexpr (R % 16 == 0) {
+#pragma unroll
+      for (int i = 0; i < R / 16; ++i) {
+        const uint4 v = reinterpret_cast<const uint4 *>(p)[i];
+        w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+      }
+    } else if constexpr (R % 8 == 0) {
+#pragma unroll
+      for (int i = 0; i < R / 8; ++i) {
+        const uint2 v = reinterpret_cast<const uint2 *>(p)[i];
+        w[2 * i] = v.x; w[2 * i + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < R / 4; ++i) w[i] = reinterpret_cast<const uint32_t *>(p)[i];
+    }
+  }
+};
+
+// Residue code of column `col` of a subject (padding code past the end).
+__device__ __forceinline__ uint32_t residue_at(const uint8_t *__restrict__ r, int L, int col,
+                                               uint32_t padc) {
+  return col < L ? (uint32_t)__ldg(r + col) : padc;
+}
+
+// One pass of G*R rows, score only.  prof points at the pass's row 0.
+// scr_in: H,F of the row above the pass per column (nullptr: the top row of
+// the matrix, H = 0, F = -inf).  scr_out: where the last lane stores its
+// bottom row (nullptr for the last pass).  Returns the lane's best H (packed).
+template <int G, int R, bool PACK>
+__device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int stride,
+                                         const uint8_t *__restrict__ rA, int LA,
+                                         const uint8_t *__restrict__ rB, int LB, int Lw, int t,
+                                         int base_lane, int padc, int o, int e,
+                                         const int2 *__restrict__ scr_in,
+                                         int2 *__restrict__ scr_out) {
+  using C = Cell<PACK>;
+  const int negO = C::splat(-o), negE = C::splat(-e);
+  const int floorv = C::splat(-o);  // E and F never fall below -o (H >= 0)
+  const int low = PACK ? C::splat(-32768) : INT_MIN / 2;
+  const uint32_t pc = (uint32_t)padc;
+  auto fetch = [&](int col) -> uint32_t {
+    uint32_t v = residue_at(rA, LA, col, pc);
+    if constexpr (PACK) v |= residue_at(rB, LB, col, pc) << 8;
+    return v;
+  };
+
+  int H[R], E[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = floorv; }
+  int hbot = 0, fbot = floorv, htop_prev = 0, best = 0;
+  uint32_t resv = pc | (pc << 8);
+  uint32_t cur = fetch(t), nxt = fetch(G + t);
+  const int8_t *pb = prof + t * R;
+  const int steps = Lw + G - 1;
+
+  for (int k = 0; k < steps; ++k) {
+    const int kk = k & (G - 1);
+    if (kk == 0 && k > 0) { cur = nxt; nxt = fetch(k + G + t); }
+    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
+    uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
+    int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
+    int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    if (t == 0) {
+      rin = r0;
+      if (scr_in != nullptr && k < Lw) {
+        const int2 v = scr_in[k];
+        hin = v.x; fin = v.y;
+      } else {
+        hin = 0; fin = floorv;
+      }
+    }
+    resv = rin;
+    ProfRow<R> pa, pq;
+    pa.load(pb + (int)(resv & 0xffu) * stride);
+    if constexpr (PACK) pq.load(pb + (int)(resv >> 8) * stride);
+
+    int hdiag = htop_prev;
+    htop_prev = hin;
+    int xup = C::addmax(hin, negO, low);
+    int f = fin;
+    Unroll<R>::run([&](auto ic) {
+      constexpr int r = decltype(ic)::value;
+      int s;
+      if constexpr (PACK) s = C::template score<r & 3>(pa.w[r >> 2], pq.w[r >> 2]);
+      else s = C::template score<r & 3>(pa.w[r >> 2], 0u);
+      const int d = C::addmax_relu(hdiag, s, E[r]);
+      f = C::addmax(f, negE, xup);
+      hdiag = H[r];
+      const int hn = C::vmax(d, f);
+      const int x = C::addmax(hn, negO, low);
+      E[r] = C::addmax(E[r], negE, x);
+      H[r] = hn;
+      xup = x;
+      if constexpr ((r & 1) == 1) best = C::vmax3(best, H[r - 1], hn);
+    });
+    hbot = H[R - 1];
+    fbot = f;
+    if (scr_out != nullptr && t == G - 1) {
+      const int j = k - (G - 1);
+      if (j >= 0 && j < Lw) scr_out[j] = make_int2(hbot, fbot);
+    }
+  }
+  return best;
+}
+
+// ------------------------------------------------------------ center scores
+// Work item = (query q, block of SPI consecutive subjects).  The CTA builds q's
+// profile, each group aligns LANES subjects against it; results go straight
+// into the per-sequence sums of S used by the distance row sums.
+template <int G, int R, bool PACK>
+__global__ void __launch_bounds__(kCenterThreads)
+k_center(SeqSet ss, Scoring sc, CenterJob job) {
+  extern __shared__ __align__(16) int8_t smem[];
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  __shared__ long long s_item;
+  __shared__ unsigned long long s_qsum;
+  constexpr int NT = kCenterThreads, NG = NT / G, LANES = PACK ? 2 : 1, SPI = NG * LANES;
+  const int K = sc.K, padc = K;
+  const int stride = dround_up(job.npass * G * R, MSA_PROF_ALIGN);
+  for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = sc.M[i];
+  const int g = threadIdx.x / G, t = threadIdx.x % G;
+  const int base_lane = (threadIdx.x & 31) - t;
+  int2 *scr = job.scratch + ((size_t)blockIdx.x * NG + g) * 2 * job.scratch_cols;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = (long long)atomicAdd(job.counter, 1ull);
+      s_qsum = 0ull;
+    }
+    __syncthreads();
+    long long item = s_item;
+    if (item >= job.n_items) break;
+    item = job.n_items - 1 - item;  // longest queries first
+    int lo = 0, hi = job.qe - job.qb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (job.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int q = job.mode == 0 ? job.qb + lo : job.qlist[job.qb + lo];
+    const int s0 = (job.mode == 0 ? q : 0) + (int)(item - job.prefix[lo]) * SPI;
+    const int Lq = ss.len[q];
+    const uint8_t *rq = ss.res + ss.pstart[q];
+    const int np = (Lq + G * R - 1) / (G * R);
+    const int prow = np * G * R;
+    for (int idx = threadIdx.x; idx < (K + 1) * prow; idx += NT) {
+      const int r = idx / prow, i = idx - r * prow;
+      int v = MSA_PAD_SCORE;
+      if (r < K && i < Lq) v = sM[rq[i] * K + r];
+      smem[r * stride + i] = (int8_t)v;
+    }
+    __syncthreads();
+
+    const int sA = s0 + g * LANES, sB = sA + 1;
+    const bool vA = sA < ss.n, vB = PACK && sB < ss.n;
+    const int LA = vA ? ss.len[sA] : 0, LB = vB ? ss.len[sB] : 0;
+    const uint8_t *rA = ss.res + (vA ? ss.pstart[sA] : 0);
+    const uint8_t *rB = ss.res + (vB ? ss.pstart[sB] : 0);
+    const int Lw = __reduce_max_sync(MSA_FULL_MASK, max(LA, LB));
+    int best = 0;
+    if (Lw > 0) {
+      for (int p = 0; p < np; ++p) {
+        const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
+        int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
+        const int b = wave_pass<G, R, PACK>(smem + p * G * R, stride, rA, LA, rB, LB, Lw, t,
+                                            base_lane, padc, sc.o, sc.e, sin, sout);
+        best = Cell<PACK>::vmax(best, b);
+        __syncwarp();
+      }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+      best = Cell<PACK>::vmax(best, __shfl_xor_sync(MSA_FULL_MASK, best, off));
+    if (t == 0) {
+      unsigned long long qadd = 0;
+#pragma unroll
+      for (int l = 0; l < LANES; ++l) {
+        const int s = l ? sB : sA;
+        if (!(l ? vB : vA)) continue;
+        const int S = l ? Cell<PACK>::lane1(best) : Cell<PACK>::lane0(best);
+        if (PACK && S > job.sat_thresh) {
+          const unsigned slot = atomicAdd(job.ovf_count, 1u);
+          if (slot < (unsigned)job.ovf_cap) job.ovf[slot] = make_int2(q, s);
+          else atomicOr(job.err, MSA_DERR_OVERFLOW);
+          continue;
+        }
+        if (job.mode == 0) {
+          if (s == q) job.self[q] = S;
+          else { atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S); qadd += (unsigned long long)(long long)S; }
+        } else {
+          atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+        }
+      }
+      if (qadd) atomicAdd(&s_qsum, qadd);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_qsum) atomicAdd(&job.pairsum[q], s_qsum);
+  }
+}
+
+// ------------------------------------------------------------ pair list
+// Each group takes one pair at a time; its own profile holds the current
+// pass's G*R query rows.
+template <int G>
+__global__ void __launch_bounds__(256) k_pairs(SeqSet ss, Scoring sc, PairJob job) {
+  constexpr int R = kPairsR, NT = 256, NG = NT / G, SR = G * R, GPW = 32 / G;
+  extern __shared__ __align__(16) int8_t smem[];
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  const int K = sc.K, padc = K;
+  for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = sc.M[i];
+  __syncthreads();
+  const int g = threadIdx.x / G, t = threadIdx.x % G, lane = threadIdx.x & 31;
+  const int base_lane = lane - t;
+  int8_t *prof = smem + (size_t)g * (K + 1) * SR;
+  int2 *scr = job.scratch + ((size_t)blockIdx.x * NG + g) * 2 * job.scratch_cols;
+
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = (int)atomicAdd(job.counter, (unsigned long long)GPW);
+    base = __shfl_sync(MSA_FULL_MASK, base, 0);
+    if (base >= job.npairs) break;
+    const int pi = base + lane / G;
+    const bool valid = pi < job.npairs;
+    int a = 0, b = 0;
+    if (valid) { const int2 pr = job.pairs[pi]; a = pr.x; b = pr.y; }
+    const int La = valid ? ss.len[a] : 0, Lb = valid ? ss.len[b] : 0;
+    const uint8_t *ra = ss.res + ss.pstart[a], *rb = ss.res + ss.pstart[b];
+    const int Lw = __reduce_max_sync(MSA_FULL_MASK, Lb);
+    const int np = __reduce_max_sync(MSA_FULL_MASK, (La + SR - 1) / SR);
+    int best = 0;
+    for (int p = 0; p < np; ++p) {
+      __syncwarp();
+      for (int idx = t; idx < (K + 1) * SR; idx += G) {
+        const int r = idx / SR, i = idx - r * SR, qi = p * SR + i;
+        int v = MSA_PAD_SCORE;
+        if (r < K && qi < La) v = sM[ra[qi] * K + r];
+        prof[idx] = (int8_t)v;
+      }
+      __syncwarp();
+      if (Lw > 0) {
+        const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
+        int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
+        best = max(best, wave_pass<G, R, false>(prof, SR, rb, Lb, nullptr, 0, Lw, t, base_lane,
+                                                padc, sc.o, sc.e, sin, sout));
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+      best = max(best, __shfl_xor_sync(MSA_FULL_MASK, best, off));
+    if (valid && t == 0) job.out[job.dst[pi]] = best;
+  }
+}
+
+// ------------------------------------------------------------ codes
+// One pass of 32*16 center rows against one subject, int32 cells, writing
+// the 4-bit traceback code of every cell: bits 0-1 the source of H (0 zero,
+// 1 diagonal, 2 F, 3 E; ties in that order), bit 2 "E extended", bit 3 "F
+// extended" (extension only when strictly better than opening).  Each lane
+// also keeps, per row, the first column reaching the row's maximum.
+__device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int stride,
+                                           const uint8_t *__restrict__ rs, int Ls, int t,
+                                           int blk, int nblk, int padc, int o, int e,
+                                           const int2 *__restrict__ scr_in,
+                                           int2 *__restrict__ scr_out, uint2 *__restrict__ cout,
+                                           int &bv, int &bi, int &bj) {
+  constexpr int G = kCodesG, R = kCodesR;
+  int H[R], E[R], rb[R], rj[R];
+  uint32_t emask = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = -o; rb[r] = 0; rj[r] = 0; }
+  int hbot = 0, fbot = -o, htop_prev = 0;
+  const uint32_t pc = (uint32_t)padc;
+  uint32_t resv = pc;
+  uint32_t cur = residue_at(rs, Ls, t, pc), nxt = residue_at(rs, Ls, G + t, pc);
+  const int8_t *pb = prof + t * R;
+  const bool wr = blk < nblk;
+  const int steps = Ls + G - 1;
+  for (int k = 0; k < steps; ++k) {
+    const int kk = k & (G - 1);
+    if (kk == 0 && k > 0) { cur = nxt; nxt = residue_at(rs, Ls, k + G + t, pc); }
+    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, kk);
+    uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
+    int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
+    int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    if (t == 0) {
+      rin = r0;
+      if (scr_in != nullptr && k < Ls) {
+        const int2 v = scr_in[k];
+        hin = v.x; fin = v.y;
+      } else {
+        hin = 0; fin = -o;
+      }
+    }
+    resv = rin;
+    ProfRow<R> pa;
+    pa.load(pb + (int)resv * stride);
+    const int j = k - t;
+    int hdiag = htop_prev;
+    htop_prev = hin;
+    int xup = hin - o;
+    int f = fin;
+    uint32_t lo = 0, hi = 0;
+    uint32_t enew = 0;
+    Unroll<R>::run([&](auto ic) {
+      constexpr int r = decltype(ic)::value;
+      const int s = Cell<false>::template score<r & 3>(pa.w[r >> 2], 0u);
+      const int dv = hdiag + s;
+      const int fe = f - e;
+      const int fv = max(fe, xup);
+      const uint32_t fext = fe > xup ? 1u : 0u;
+      const int ev = E[r];
+      const int hv = max(max(dv, 0), max(ev, fv));
+      const uint32_t src = hv == 0 ? 0u : (hv == dv ? 1u : (hv == fv ? 2u : 3u));
+      const uint32_t code = src | (((emask >> r) & 1u) << 2) | (fext << 3);
+      if constexpr (r < 8) lo |= code << (4 * r);
+      else hi |= code << (4 * (r - 8));
+      hdiag = H[r];
+      H[r] = hv;
+      const int x = hv - o;
+      const int ee = ev - e;
+      E[r] = max(ee, x);
+      enew |= (ee > x ? 1u : 0u) << r;
+      if (hv > rb[r]) { rb[r] = hv; rj[r] = j; }
+      f = fv;
+      xup = x;
+    });
+    emask = enew;
+    hbot = H[R - 1];
+    fbot = f;
+    if (wr && j >= 0 && j < Ls) cout[j] = make_uint2(lo, hi);
+    if (scr_out != nullptr && t == G - 1 && j >= 0 && j < Ls) scr_out[j] = make_int2(hbot, fbot);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (rb[r] > bv) { bv = rb[r]; bi = blk * R + r + 1; bj = rj[r] + 1; }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob job) {
+  constexpr int G = kCodesG, R = kCodesR, NT = 256, NW = NT / 32;
+  extern __shared__ __align__(16) int8_t smem[];
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  const int K = sc.K, padc = K;
+  const int rows = job.npass * G * R;
+  const int stride = dround_up(rows, MSA_PROF_ALIGN);
+  for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = sc.M[i];
+  __syncthreads();
+  const int Lc = ss.len[job.center];
+  const uint8_t *rc = ss.res + ss.pstart[job.center];
+  for (int idx = threadIdx.x; idx < (K + 1) * rows; idx += NT) {
+    const int r = idx / rows, i = idx - r * rows;
+    int v = MSA_PAD_SCORE;
+    if (r < K && i < Lc) v = sM[rc[i] * K + r];
+    smem[r * stride + i] = (int8_t)v;
+  }
+  __syncthreads();
+  const int t = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nblk = (Lc + R - 1) / R;
+  int2 *scr = job.scratch + ((size_t)blockIdx.x * NW + wid) * 2 * job.scratch_cols;
+  const int nsub = job.se - job.sb;
+  for (;;) {
+    int x = 0;
+    if (t == 0) x = (int)atomicAdd(job.counter, 1ull);
+    x = __shfl_sync(MSA_FULL_MASK, x, 0);
+    if (x >= nsub) break;
+    const int k = job.se - 1 - x;  // longest first
+    const int Ls = ss.len[k];
+    const uint8_t *rs = ss.res + ss.pstart[k];
+    uint2 *cbase = reinterpret_cast<uint2 *>(job.codes + job.code_off[k - job.sb]);
+    int bv = 0, bi = 0, bj = 0;
+    for (int p = 0; p < job.npass; ++p) {
+      const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
+      int2 *sout = p + 1 < job.npass ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
+      const int blk = p * G + t;
+      codes_pass(smem + p * G * R, stride, rs, Ls, t, blk, nblk, padc, sc.o, sc.e, sin, sout,
+                 cbase + (size_t)blk * Ls, bv, bi, bj);
+      __syncwarp();
+    }
+    // best cell over the group: largest H, then smallest row, then smallest column
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const int ov = __shfl_xor_sync(MSA_FULL_MASK, bv, off);
+      const int oi = __shfl_xor_sync(MSA_FULL_MASK, bi, off);
+      const int oj = __shfl_xor_sync(MSA_FULL_MASK, bj, off);
+      const bool take = ov > bv || (ov == bv && (oi < bi || (oi == bi && oj < bj)));
+      if (take) { bv = ov; bi = oi; bj = oj; }
+    }
+    if (t == 0) {
+      int32_t *b = job.best + (size_t)(k - job.sb) * 3;
+      b[0] = bv;
+      b[1] = bv > 0 ? bi : 0;
+      b[2] = bv > 0 ? bj : 0;
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+
+const WaveShape kCenterShapes[] = {{8, 8}, {8, 12}, {8, 16}, {16, 8}, {16, 12},
+                                   {16, 16}, {32, 8}, {32, 12}, {32, 16}};
+const int kNumCenterShapes = sizeof(kCenterShapes) / sizeof(kCenterShapes[0]);
+
+int center_smem_bytes(int K, int rows_alloc) {
+  return (K + 1) * round_up_int(rows_alloc, MSA_PROF_ALIGN);
+}
+
+typedef void (*center_fn)(SeqSet, Scoring, CenterJob);
+
+static center_fn center_kernel(int shape, bool packed) {
+#define MSA_SHAPE_CASE(idx, G, R)                         \
+  case idx:                                               \
+    return packed ? k_center<G, R, true> : k_center<G, R, false>;
+  switch (shape) {
+    MSA_SHAPE_CASE(0, 8, 8)
+    MSA_SHAPE_CASE(1, 8, 12)
+    MSA_SHAPE_CASE(2, 8, 16)
+    MSA_SHAPE_CASE(3, 16, 8)
+    MSA_SHAPE_CASE(4, 16, 12)
+    MSA_SHAPE_CASE(5, 16, 16)
+    MSA_SHAPE_CASE(6, 32, 8)
+    MSA_SHAPE_CASE(7, 32, 12)
+    MSA_SHAPE_CASE(8, 32, 16)
+    default: return nullptr;
+  }
+#undef MSA_SHAPE_CASE
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+static int occupancy_grid(const void *fn, int threads, int smem) {
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * sm_count();
+}
+
+int center_grid(int shape, bool packed, int smem) {
+  center_fn fn = center_kernel(shape, packed);
+  if (!fn) return 0;
+  return occupancy_grid((const void *)fn, kCenterThreads, smem);
+}
+
+cudaError_t launch_center(int shape, bool packed, const SeqSet &ss, const Scoring &sc,
+                          const CenterJob &job, int grid, cudaStream_t st) {
+  center_fn fn = center_kernel(shape, packed);
+  if (!fn) return cudaErrorInvalidValue;
+  const WaveShape ws = kCenterShapes[shape];
+  const int smem = center_smem_bytes(sc.K, job.npass * ws.G * ws.R);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  fn<<<grid, kCenterThreads, smem, st>>>(ss, sc, job);
+  return cudaGetLastError();
+}
+
+typedef void (*pairs_fn)(SeqSet, Scoring, PairJob);
+static pairs_fn pairs_kernel(int G) {
+  return G == 8 ? k_pairs<8> : (G == 32 ? k_pairs<32> : nullptr);
+}
+int pairs_rows(int G) { return G * kPairsR; }
+static int pairs_smem(int G, int K) { return (256 / G) * (K + 1) * G * kPairsR; }
+
+int pairs_grid(int G) {
+  pairs_fn fn = pairs_kernel(G);
+  if (!fn) return 0;
+  return occupancy_grid((const void *)fn, 256, pairs_smem(G, MSA_MAX_ALPHABET));
+}
+
+cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJob &job,
+                         int grid, cudaStream_t st) {
+  pairs_fn fn = pairs_kernel(G);
+  if (!fn) return cudaErrorInvalidValue;
+  const int smem = pairs_smem(G, sc.K);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  fn<<<grid, 256, smem, st>>>(ss, sc, job);
+  return cudaGetLastError();
+}
+
+int codes_smem_bytes(int K, int rows_alloc) {
+  return (K + 1) * round_up_int(rows_alloc, MSA_PROF_ALIGN);
+}
+
+int codes_grid(int smem) { return occupancy_grid((const void *)k_codes, 256, smem); }
+
+cudaError_t launch_codes(const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
+                         cudaStream_t st) {
+  const int smem = codes_smem_bytes(sc.K, job.npass * kCodesG * kCodesR);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute((const void *)k_codes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_codes<<<grid, 256, smem, st>>>(ss, sc, job);
+  return cudaGetLastError();
+}

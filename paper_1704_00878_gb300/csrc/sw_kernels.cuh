@@ -1,0 +1,77 @@
+// sw_kernels.cuh -- launch interfaces of the Smith-Waterman kernels.
+#pragma once
+#include "common.cuh"
+
+// Per-sequence device layout produced by the encode kernel (sorted order).
+struct SeqSet {
+  const uint8_t *res;     // residues (alphabet index; padding code = K), 16-B aligned per sequence
+  const int64_t *pstart;  // start of sequence k in res
+  const int32_t *len;     // length of sequence k
+  int n;
+};
+
+struct Scoring {
+  const int8_t *M;        // K x K, device
+  int K, o, e;
+};
+
+// All-pairs / reference-pairs scores for center selection.
+struct CenterJob {
+  int mode;                       // 0: query q vs subjects [q, n) ; 1: query qlist[x] vs [0, n)
+  const int32_t *qlist;           // mode 1 (sorted indices)
+  int qb, qe;                     // query range (sorted index for mode 0, qlist index for mode 1)
+  const int64_t *prefix;          // device, qe-qb+1 entries: first item of each query
+  int64_t n_items;
+  int npass;                      // passes of the longest query in the range
+  unsigned long long *counter;    // zeroed before launch
+  unsigned long long *pairsum;    // int64 sums of S over the listed partners (sorted index)
+  int32_t *self;                  // mode 0: S(q,q)
+  int sat_thresh;                 // packed cells: lanes whose best exceeds this are re-run in int32
+  int2 *ovf; unsigned *ovf_count; int ovf_cap; unsigned *err;
+  int2 *scratch; int scratch_cols;
+};
+
+// Arbitrary pair list (int32 cells).
+struct PairJob {
+  const int2 *pairs;              // (a, b) sorted indices; a = rows (query), b = columns
+  const int32_t *dst;             // output slot of each listed pair
+  int32_t *out;
+  int npairs;
+  unsigned long long *counter;
+  int2 *scratch; int scratch_cols;
+};
+
+// Alignment to the center with 4-bit traceback codes (int32 cells).
+struct CodesJob {
+  int center;                     // sorted index
+  int sb, se;                     // subjects: sorted indices [sb, se), longest first
+  const int64_t *code_off;        // byte offset of each subject's codes (indexed k - sb)
+  uint8_t *codes;
+  int32_t *best;                  // per subject (indexed k - sb): {score, i2, j2}
+  int npass;
+  unsigned long long *counter;
+  int2 *scratch; int scratch_cols;
+};
+
+// Variant table for the packed center kernel: threads per group and rows per thread.
+struct WaveShape { int G, R; };
+extern const WaveShape kCenterShapes[];
+extern const int kNumCenterShapes;
+
+int center_smem_bytes(int K, int rows_alloc);
+cudaError_t launch_center(int shape, bool packed, const SeqSet &ss, const Scoring &sc,
+                          const CenterJob &job, int grid, cudaStream_t st);
+int center_grid(int shape, bool packed, int smem);
+
+cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJob &job,
+                         int grid, cudaStream_t st);
+int pairs_grid(int G);
+int pairs_rows(int G);
+
+cudaError_t launch_codes(const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
+                         cudaStream_t st);
+int codes_smem_bytes(int K, int rows_alloc);
+int codes_grid(int smem);
+constexpr int kCodesG = 32, kCodesR = 16;
+constexpr int kPairsR = 16;
+constexpr int kCenterThreads = 256;
