@@ -34,9 +34,12 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "batched_uneven_10k"
 METRIC = "GCUPS and % of integer/DPX roofline; end-to-end MSA sec (learned vs exact center)"
 UNIT = "GCUPS"
-# ALU roofline of the packed DP: 152 SMs x 128 integer lanes x 2.07 GHz max
-# clock / 3 integer ops per cell (6 DPX ops per packed pair of int16 cells).
-SMS, INT_LANES, MAX_GHZ, OPS_PER_CELL = 152, 128, 2.07, 3.0
+# ALU roofline of the packed DP: 152 SMs x 64 integer (DPX) lanes per clock x
+# 2.07 GHz maximum SM clock / 3 integer instructions per cell (the Gotoh
+# update is 6 DPX instructions per packed pair of int16 cells).  64 lanes per
+# SM per clock is the issue rate msa_probe_int_rate measures for the DPX
+# instructions on GB300 (half the 128 FP32 lanes).
+SMS, INT_LANES, MAX_GHZ, OPS_PER_CELL = 152, 64, 2.07, 3.0
 ALU_PEAK_GCUPS = SMS * INT_LANES * MAX_GHZ / OPS_PER_CELL
 
 
@@ -50,6 +53,10 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the sequence count")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--length", default=None,
+                    help="override lengths, e.g. uniform:340:360 (profiling cases)")
+    ap.add_argument("--only-center", action="store_true",
+                    help="time the exact-center selection alone (profiling cases)")
     return ap.parse_args()
 
 
@@ -190,7 +197,12 @@ def run_ours(args):
 
     # weak scaling: every rank aligns its own independent set of the same shape
     base_seed = generate.__globals__["WORKLOADS"][args.workload].seed
-    letters, offsets, w, _ = generate(args.workload, n=args.n, seed=base_seed + 1000 * rank)
+    length = None
+    if args.length:
+        kind, lo, hi = args.length.split(":")
+        length = (kind, int(lo), int(hi))
+    letters, offsets, w, _ = generate(args.workload, n=args.n, seed=base_seed + 1000 * rank,
+                                      length=length)
     alph, M, _, _ = scoring(w.kind)
     n = offsets.size - 1
     stream = torch.cuda.current_stream()
@@ -245,6 +257,22 @@ def run_ours(args):
         launches = b.msa_stage_times(h)[1]["launches"] - launches0
         return total_ms, cells, center_ms, center_cells, launches, out
 
+    if args.only_center:
+        for _ in range(args.warmup):
+            b.msa_load(h, dlet, offsets)
+            b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        b.msa_load(h, dlet, offsets)
+        t0 = time.perf_counter()
+        c, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        dt = time.perf_counter() - t0
+        ms, cnt = b.msa_stage_times(h)
+        print(json.dumps({"only_center": True, "n": n, "center": c, "wall_s": dt,
+                          "center_kernel_ms": ms["center_kernels"], "cells": cnt["center_cells"],
+                          "gcups": cnt["center_cells"] / (ms["center_kernels"] * 1e-3) / 1e9}))
+        ctx.close()
+        return
+
+    rate, per_clk = b.msa_probe_int_rate(b.MSA_PROBE_VIADDMAX_S16X2)
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize()
@@ -294,7 +322,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_center (exact-center DP, packed int16x2)",
                      "achieved": achieved, "peak": ALU_PEAK_GCUPS, "unit": UNIT,
                      "frac": achieved / ALU_PEAK_GCUPS if achieved else None, "traffic": None,
-                     "peak_source": "152 SMs x 128 int lanes x 2.07 GHz / 3 ops per cell"},
+                     "peak_source": "152 SMs x 64 DPX lanes/clk x 2.07 GHz / 3 DPX ops per cell",
+                     "peak_measured": rate / OPS_PER_CELL / 1e9,
+                     "dpx_ops_per_clk_sm_measured": per_clk},
         "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
         "clocks": clocks,
         "e2e": {"value": e2e_all / (e2e_max * 1e-3) / 1e9, "unit": UNIT,

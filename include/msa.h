@@ -57,7 +57,10 @@ typedef struct {
     const int8_t *matrix;   /* alphabet x alphabet substitution scores s(a,b) = matrix[a*alphabet+b], host */
     int32_t alphabet;       /* 1 .. MSA_MAX_ALPHABET */
     const char *letters;    /* alphabet characters, index k <-> letters[k]; '-' is reserved */
-    int32_t gap_open;       /* W_k = gap_open + (k-1)*gap_extend (Eq. 2), gap_open >= gap_extend >= 1 */
+    int32_t gap_open;       /* W_k = gap_open + (k-1)*gap_extend (Eq. 2), gap_open >= gap_extend >= 1,
+                               and -128 <= s(a,b) + gap_open <= 127 for every entry (the
+                               score profiles hold s + gap_open as int8); packed int16
+                               cells also need s(a,b) + gap_open >= 0 */
     int32_t gap_extend;
     int32_t precision;      /* MSA_AUTO | MSA_INT16 | MSA_INT32 */
     int32_t sat_limit;      /* int16 overflow guard, 0 = 32767; smaller values force the
@@ -65,8 +68,9 @@ typedef struct {
 } msa_params;
 
 /* Create a context.  cuda_stream: a cudaStream_t (NULL = the legacy default
- * stream).  Copies the matrix and letters.  EINVAL on a bad alphabet, gap
- * pair or precision. */
+ * stream).  Copies the matrix and letters.  EINVAL on a bad alphabet, an
+ * asymmetric matrix (distances assume S(A,B) = S(B,A)), a bad gap pair or
+ * precision. */
 int msa_create(msa_ctx **out, const msa_params *params, void *cuda_stream);
 void msa_destroy(msa_ctx *ctx);
 const char *msa_last_error(const msa_ctx *ctx);

@@ -52,6 +52,7 @@ _SIGS = {
     "msa_sp_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -201,6 +202,18 @@ def msa_stage_times(ctx):
     _check(ctx, lib().msa_stage_times(ctx, _ptr(ms), len(STAGES), _ptr(cnt)))
     return (dict(zip(STAGES, (float(x) for x in ms))),
             {"center_cells": int(cnt[0]), "align_cells": int(cnt[1]), "launches": int(cnt[2])})
+
+
+MSA_PROBE_VIADDMAX_S16X2, MSA_PROBE_VIMAX3_S16X2, MSA_PROBE_VIADDMAX_S32, MSA_PROBE_PRMT = 0, 1, 2, 3
+
+
+def msa_probe_int_rate(op):
+    """(instructions/s, instructions per clock per SM) of one integer op."""
+    r = np.zeros(2, np.float64)
+    rc = lib().msa_probe_int_rate(int(op), _ptr(r[:1]), _ptr(r[1:]))
+    if rc != MSA_OK:
+        raise MSAError(rc, "probe failed")
+    return float(r[0]), float(r[1])
 
 
 class Context:

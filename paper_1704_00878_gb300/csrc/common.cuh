@@ -34,7 +34,7 @@ template <> struct Cell<false> {
   static __device__ __forceinline__ int addmax(int a, int b, int c) { return __viaddmax_s32(a, b, c); }
   // max(a + b, c, 0)
   static __device__ __forceinline__ int addmax_relu(int a, int b, int c) { return __viaddmax_s32_relu(a, b, c); }
-  static __device__ __forceinline__ int vmax(int a, int b) { return max(a, b); }
+  static __device__ __forceinline__ int vmax(int a, int b) { return __vimax_s32_relu(a, b); }
   static __device__ __forceinline__ int vmax3(int a, int b, int c) { return __vimax3_s32(a, b, c); }
   // a + b (both lanes when packed)
   static __device__ __forceinline__ int add(int a, int b) { return a + b; }
@@ -60,7 +60,11 @@ template <> struct Cell<true> {
   static __device__ __forceinline__ int addmax_relu(int a, int b, int c) {
     return (int)__viaddmax_s16x2_relu((unsigned)a, (unsigned)b, (unsigned)c);
   }
-  static __device__ __forceinline__ int vmax(int a, int b) { return (int)__vmaxs2((unsigned)a, (unsigned)b); }
+  // max(a, b, 0): the native DPX form (values fed here are never negative
+  // where it matters; __vmaxs2 would be emulated with two instructions)
+  static __device__ __forceinline__ int vmax(int a, int b) {
+    return (int)__vimax_s16x2_relu((unsigned)a, (unsigned)b);
+  }
   static __device__ __forceinline__ int vmax3(int a, int b, int c) {
     return (int)__vimax3_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
   }

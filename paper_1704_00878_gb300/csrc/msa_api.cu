@@ -27,7 +27,7 @@ enum Stage { ST_ENCODE = 0, ST_CENTER, ST_ALIGN, ST_TRACE, ST_MERGE, ST_ROWS, ST
 struct msa_ctx {
   int dev = 0;
   cudaStream_t st = nullptr;
-  int K = 0, o = 0, e = 0, precision = MSA_AUTO, sat_limit = 32767, smax = 0;
+  int K = 0, o = 0, e = 0, precision = MSA_AUTO, sat_limit = 32767, smax = 0, smin = 0;
   std::vector<int8_t> hM;
   std::string letters;
   uint8_t hlut[256];
@@ -210,152 +210,172 @@ int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector
 }
 
 // ------------------------------------------------------------ center planning
-// Pass height choice for one query: the packed kernel variant whose rows x
-// (columns + ramp) cost is smallest, with a small charge per extra pass.
-int choose_shape(int Lq, int Ls_est) {
-  int best = 0;
+// Largest pre-packed profile (bytes) a paired-query launch may hold in shared
+// memory; longer queries use the single-query kernel with an int8 profile.
+constexpr int kMaxPairedProfile = 110 * 1024;
+
+// Modelled cost of one query against subjects of length ~Ls_est with a
+// variant: rows x (columns + ramp), a charge per extra pass (scratch traffic,
+// a second sweep of the subject), the per-column overhead of small R, and the
+// byte unpacking of the single-query packed kernel.
+double variant_cost(int v, int Lq, int Ls_est) {
+  const CenterVariant &cv = kCenterVariants[v];
+  const int rows = cv.G * cv.R;
+  const int np = (Lq + rows - 1) / rows;
+  double c = (double)np * rows * (Ls_est + cv.G - 1 + (np > 1 ? 48 : 0)) * (1.0 + 3.0 / cv.R);
+  if (!cv.paired && cv.packed) c *= 1.2;
+  return c;
+}
+
+int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
+  int best = -1;
   double best_cost = 1e300;
-  for (int s = 0; s < kNumCenterShapes; ++s) {
-    const int G = kCenterShapes[s].G, R = kCenterShapes[s].R;
-    const int rows = G * R;
+  for (int v = 0; v < kNumCenterVariants; ++v) {
+    const CenterVariant &cv = kCenterVariants[v];
+    if (cv.packed != packed) continue;
+    const int rows = cv.G * cv.R;
     const int np = (Lq + rows - 1) / rows;
-    const double cost = (double)np * rows * (Ls_est + G - 1 + 24) * (R == 8 ? 1.08 : 1.0);
-    if (cost < best_cost) { best_cost = cost; best = s; }
+    const int smem = center_smem_bytes(v, ctx->K, np * rows);
+    if (cv.paired && smem > kMaxPairedProfile) continue;
+    if (smem > 200 * 1024) continue;
+    const double c = variant_cost(v, Lq, Ls_est);
+    if (c < best_cost) { best_cost = c; best = v; }
   }
   return best;
 }
 
-struct ClassRange {
-  int shape, qb, qe, npass;
-};
-
-// Split an ascending list of query lengths into contiguous runs with the same
-// kernel variant.
-std::vector<ClassRange> plan_classes(const std::vector<int> &qlen, bool packed, int Ls_est_mode,
-                                     double Ls_mean) {
-  std::vector<ClassRange> out;
-  const int nq = (int)qlen.size();
-  int x = 0;
-  while (x < nq) {
-    const int Lq = qlen[x];
-    const int shape = packed ? choose_shape(Lq, Ls_est_mode ? (int)Ls_mean : Lq) : 8;
-    int y = x + 1;
-    while (y < nq) {
-      const int s2 = packed ? choose_shape(qlen[y], Ls_est_mode ? (int)Ls_mean : qlen[y]) : 8;
-      if (s2 != shape) break;
-      ++y;
-    }
-    const int rows = kCenterShapes[shape].G * kCenterShapes[shape].R;
-    const int np = (qlen[y - 1] + rows - 1) / rows;
-    out.push_back({shape, x, y, np});
-    x = y;
-  }
-  return out;
-}
+// int16 lanes need every biased score s + o >= 0 (the lane-local add) and,
+// under MSA_AUTO, an a-priori bound on any local score of a sequence of
+// length Lq that stays below the overflow guard.
+int sat_thresh(msa_ctx *ctx) { return ctx->sat_limit - ctx->smax - ctx->o; }
 
 bool use_packed(msa_ctx *ctx, int Lq) {
-  if (ctx->precision == MSA_INT32) return false;
+  if (ctx->precision == MSA_INT32 || ctx->smin + ctx->o < 0) return false;
   if (ctx->precision == MSA_INT16) return true;
-  // a-priori bound on any local score involving a sequence of length Lq
-  const long long bound = (long long)Lq * ctx->smax;
-  return bound <= (long long)ctx->sat_limit - ctx->smax;
+  const long long bound = (long long)Lq * std::max(ctx->smax, 0);
+  return bound <= (long long)sat_thresh(ctx);
+}
+
+struct CenterClass {
+  int variant, ub, ue;  // item units [ub, ue): query pairs (paired) or queries
+};
+
+int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
+                 const std::vector<int> &qlen, float &center_ms) {
+  const CenterVariant &cv = kCenterVariants[cc.variant];
+  const int n = ctx->n, NG = kCenterThreads / cv.G;
+  std::vector<int64_t> prefix(cc.ue - cc.ub + 1, 0);
+  int maxlen = 0;
+  for (int u = cc.ub; u < cc.ue; ++u) {
+    int64_t items;
+    if (cv.paired) {
+      const int xa = 2 * u;
+      const int xb = std::min(2 * u + 1, nq_list - 1);
+      maxlen = std::max(maxlen, std::max(qlen[xa], qlen[xb]));
+      items = mode == 0 ? (n - xa + NG - 1) / NG : (n + NG - 1) / NG;
+    } else {
+      const int spi = NG * (cv.packed ? 2 : 1);
+      maxlen = std::max(maxlen, qlen[u]);
+      items = mode == 0 ? (n - u + spi - 1) / spi : (n + spi - 1) / spi;
+    }
+    prefix[u - cc.ub + 1] = prefix[u - cc.ub] + items;
+  }
+  const int rows = cv.G * cv.R;
+  const int npass = (maxlen + rows - 1) / rows;
+  TRY(ensure(ctx, ctx->prefix, sizeof(int64_t) * prefix.size()));
+  CK(cudaMemcpyAsync(ctx->prefix.p, prefix.data(), sizeof(int64_t) * prefix.size(),
+                     cudaMemcpyHostToDevice, ctx->st));
+  const int smem = center_smem_bytes(cc.variant, ctx->K, npass * rows);
+  const int grid = center_grid(cc.variant, smem);
+  if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * NG * 2 * ctx->maxlen * sizeof(int2)));
+  CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+  CenterJob job;
+  job.mode = mode;
+  job.qlist = P<int32_t>(ctx->qlist);
+  job.nq = nq_list;
+  job.qb = cc.ub;
+  job.qe = cc.ue;
+  job.prefix = P<int64_t>(ctx->prefix);
+  job.n_items = prefix.back();
+  job.npass = npass;
+  job.counter = ctx->dcounter;
+  job.pairsum = P<unsigned long long>(ctx->pairsum);
+  job.self = P<int32_t>(ctx->self);
+  job.sat_thresh = sat_thresh(ctx);
+  job.ovf = P<int2>(ctx->ovf);
+  job.ovf_count = ctx->derr + 1;
+  job.ovf_cap = (int)(ctx->ovf.cap / sizeof(int2));
+  job.err = ctx->derr;
+  job.scratch = P<int2>(ctx->scratch);
+  job.scratch_cols = ctx->maxlen;
+  stage_begin(ctx, ST_CENTER_K);
+  CK((++ctx->launches, launch_center)(cc.variant, seqset(ctx), scoring(ctx), job, grid, ctx->st));
+  stage_end(ctx, ST_CENTER_K);
+  // the prefix buffer is reused by the next class: wait for this one
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_CENTER_K);
+  center_ms += ctx->stage_ms[ST_CENTER_K];
+  return MSA_OK;
 }
 
 int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   // qsorted: ascending sorted indices of the queries (mode 1); mode 0 uses all.
   const int n = ctx->n;
-  const SeqSet ss = seqset(ctx);
-  const Scoring sc = scoring(ctx);
   std::vector<int> qlen;
   if (mode == 0) qlen.assign(ctx->len_sorted.begin(), ctx->len_sorted.end());
   else for (int q : qsorted) qlen.push_back(ctx->len_sorted[q]);
+  const int nq = (int)qlen.size();
   double mean = 0;
   for (int k = 0; k < n; ++k) mean += ctx->len_sorted[k];
   mean /= n;
   std::vector<int64_t> suffix(n + 1, 0);
   for (int k = n - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + ctx->len_sorted[k];
-
   if (mode == 1) {
     TRY(ensure(ctx, ctx->qlist, sizeof(int32_t) * qsorted.size()));
     CK(cudaMemcpyAsync(ctx->qlist.p, qsorted.data(), sizeof(int32_t) * qsorted.size(),
                        cudaMemcpyHostToDevice, ctx->st));
   }
-  // split the (ascending) query list into a packed run and an int32 run: a
-  // local score is at most min(Lq, Ls) * smax <= Lq * smax, so the query
-  // length alone decides whether int16 lanes are safe
-  std::vector<std::pair<int, int>> runs;  // [b, e) with packing flag
-  std::vector<bool> packed_of;
-  {
-    int x = 0;
-    const int nq = (int)qlen.size();
-    while (x < nq) {
-      const bool pk = use_packed(ctx, qlen[x]);
-      int y = x + 1;
-      while (y < nq && use_packed(ctx, qlen[y]) == pk) ++y;
-      runs.push_back({x, y});
-      packed_of.push_back(pk);
-      x = y;
-    }
+  // Queries ascend in length: a packed prefix [0, x1), an int32 rest.  The
+  // local score of any pair is at most min(Lq, Ls) * smax <= Lq * smax.
+  int x1 = 0;
+  while (x1 < nq && use_packed(ctx, qlen[x1])) ++x1;
+  auto est = [&](int Lq) { return mode == 0 ? Lq : (int)mean; };
+
+  std::vector<CenterClass> classes;
+  // packed part: query pairs [0, ceil(x1/2))
+  const int npairs = (x1 + 1) / 2;
+  for (int p = 0; p < npairs;) {
+    const int Lq = qlen[std::min(2 * p + 1, x1 - 1)];
+    const int v = choose_variant(ctx, Lq, est(Lq), true);
+    if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", Lq);
+    int pe = p + 1;
+    while (pe < npairs && choose_variant(ctx, qlen[std::min(2 * pe + 1, x1 - 1)],
+                                         est(qlen[std::min(2 * pe + 1, x1 - 1)]), true) == v)
+      ++pe;
+    if (kCenterVariants[v].paired) classes.push_back({v, p, pe});
+    else classes.push_back({v, 2 * p, std::min(2 * pe, x1)});
+    p = pe;
+  }
+  // int32 part: single queries [x1, nq)
+  for (int x = x1; x < nq;) {
+    const int v = choose_variant(ctx, qlen[x], est(qlen[x]), false);
+    if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", qlen[x]);
+    int xe = x + 1;
+    while (xe < nq && choose_variant(ctx, qlen[xe], est(qlen[xe]), false) == v) ++xe;
+    classes.push_back({v, x, xe});
+    x = xe;
+  }
+  float center_ms = 0.f;
+  for (const CenterClass &cc : classes) {
+    // a paired class may not pair across the packed / int32 boundary
+    const int nq_list = kCenterVariants[cc.variant].paired ? x1 : nq;
+    TRY(launch_class(ctx, mode, nq_list, cc, qlen, center_ms));
   }
   int64_t cells = 0;
-  float center_ms = 0.f;
-  for (size_t ri = 0; ri < runs.size(); ++ri) {
-    const bool pk = packed_of[ri];
-    std::vector<int> sub(qlen.begin() + runs[ri].first, qlen.begin() + runs[ri].second);
-    std::vector<ClassRange> cls = plan_classes(sub, pk, mode, mean);
-    for (ClassRange cr : cls) {
-      cr.qb += runs[ri].first;
-      cr.qe += runs[ri].first;
-      const int G = kCenterShapes[cr.shape].G, R = kCenterShapes[cr.shape].R;
-      const int spi = (kCenterThreads / G) * (pk ? 2 : 1);
-      std::vector<int64_t> prefix(cr.qe - cr.qb + 1, 0);
-      for (int x = cr.qb; x < cr.qe; ++x) {
-        const int nsub = mode == 0 ? n - x : n;
-        prefix[x - cr.qb + 1] = prefix[x - cr.qb] + (nsub + spi - 1) / spi;
-      }
-      if (mode == 0)  // real cells: q against subjects [q, n)
-        for (int x = cr.qb; x < cr.qe; ++x) cells += (int64_t)ctx->len_sorted[x] * suffix[x];
-      TRY(ensure(ctx, ctx->prefix, sizeof(int64_t) * prefix.size()));
-      CK(cudaMemcpyAsync(ctx->prefix.p, prefix.data(), sizeof(int64_t) * prefix.size(),
-                         cudaMemcpyHostToDevice, ctx->st));
-      const int smem = center_smem_bytes(ctx->K, cr.npass * G * R);
-      const int grid = center_grid(cr.shape, pk, smem);
-      if (cr.npass > 1) {
-        const size_t scr = (size_t)grid * (kCenterThreads / G) * 2 * ctx->maxlen * sizeof(int2);
-        TRY(ensure(ctx, ctx->scratch, scr));
-      }
-      CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
-      CenterJob job;
-      job.mode = mode;
-      job.qlist = P<int32_t>(ctx->qlist);
-      job.qb = cr.qb;
-      job.qe = cr.qe;
-      job.prefix = P<int64_t>(ctx->prefix);
-      job.n_items = prefix.back();
-      job.npass = cr.npass;
-      job.counter = ctx->dcounter;
-      job.pairsum = P<unsigned long long>(ctx->pairsum);
-      job.self = P<int32_t>(ctx->self);
-      job.sat_thresh = ctx->sat_limit - ctx->smax;
-      job.ovf = P<int2>(ctx->ovf);
-      job.ovf_count = ctx->derr + 1;
-      job.ovf_cap = (int)(ctx->ovf.cap / sizeof(int2));
-      job.err = ctx->derr;
-      job.scratch = P<int2>(ctx->scratch);
-      job.scratch_cols = ctx->maxlen;
-      stage_begin(ctx, ST_CENTER_K);
-      CK((++ctx->launches, launch_center)(cr.shape, pk, ss, sc, job, grid, ctx->st));
-      stage_end(ctx, ST_CENTER_K);
-      // the prefix buffer is reused by the next class: wait for this one
-      CK(cudaStreamSynchronize(ctx->st));
-      stage_collect(ctx, ST_CENTER_K);
-      center_ms += ctx->stage_ms[ST_CENTER_K];
-    }
-  }
-  if (mode == 1) {
-    double sumL = 0;
-    for (int k = 0; k < n; ++k) sumL += ctx->len_sorted[k];
-    for (int q : qsorted) cells += (int64_t)((double)ctx->len_sorted[q] * sumL);
+  if (mode == 0) {
+    for (int x = 0; x < nq; ++x) cells += (int64_t)ctx->len_sorted[x] * suffix[x];
+  } else {
+    for (int q : qsorted) cells += (int64_t)ctx->len_sorted[q] * suffix[0];
   }
   ctx->cells[0] = cells;
   ctx->stage_ms[ST_CENTER_K] = center_ms;
@@ -374,8 +394,10 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     std::iota(dst.begin(), dst.end(), 0);
     TRY(ensure(ctx, ctx->ovf_scores, sizeof(int32_t) * cnt));
     TRY(run_pairs(ctx, ov, dst, P<int32_t>(ctx->ovf_scores)));
-    CK((++ctx->launches, launch_apply_overflow)(mode == 0 ? 0 : 1, P<int2>(ctx->ovf), P<int32_t>(ctx->ovf_scores), cnt,
-                             P<unsigned long long>(ctx->pairsum), P<int32_t>(ctx->self), ctx->st));
+    CK((++ctx->launches, launch_apply_overflow)(mode == 0 ? 0 : 1, P<int2>(ctx->ovf),
+                                                P<int32_t>(ctx->ovf_scores), cnt,
+                                                P<unsigned long long>(ctx->pairsum),
+                                                P<int32_t>(ctx->self), ctx->st));
   }
   return MSA_OK;
 }
@@ -412,8 +434,17 @@ int msa_create(msa_ctx **out, const msa_params *p, void *cuda_stream) {
   ctx->sat_limit = p->sat_limit > 0 ? std::min(p->sat_limit, 32767) : 32767;
   ctx->hM.assign(p->matrix, p->matrix + ctx->K * ctx->K);
   ctx->letters.assign(p->letters, p->letters + ctx->K);
-  ctx->smax = 0;
-  for (int8_t v : ctx->hM) ctx->smax = std::max<int>(ctx->smax, v);
+  ctx->smax = -128;
+  ctx->smin = 127;
+  for (int8_t v : ctx->hM) {
+    ctx->smax = std::max<int>(ctx->smax, v);
+    ctx->smin = std::min<int>(ctx->smin, v);
+  }
+  // the profiles hold s + o as int8
+  if (ctx->smax + ctx->o > 127 || ctx->smin + ctx->o < -128) {
+    delete ctx;
+    return MSA_EINVAL;
+  }
   memset(ctx->hlut, 255, sizeof ctx->hlut);
   for (int a = 0; a < ctx->K; ++a) ctx->hlut[(uint8_t)ctx->letters[a]] = (uint8_t)a;
   ctx->st = (cudaStream_t)cuda_stream;

@@ -9,14 +9,14 @@
 // several passes; the bottom row of one pass (H and F per column) is kept in a
 // small per-group global buffer for the next.
 //
-// Scores come from a query profile in shared memory: prof[r*stride + i] =
-// s(query_i, r), with every residue row starting on the same bank so the
-// lanes of a group (which read consecutive row blocks) never conflict.
+// Scores come from a query profile in shared memory, biased by the gap-open
+// penalty: prof[r*stride + i] = s(query_i, r) + o, every residue row starting
+// on the same bank so the lanes of one load phase never conflict.
 //
-// Per cell, with X = H - o carried down the column and E/F the horizontal /
-// vertical gap scores (all DPX instructions):
-//   D = max(Hdiag + s, E, 0);  F = max(F - e, Xup);  H = max(D, F);
-//   X = H - o;  E' = max(E - e, X);  best = max(best, H)
+// Per cell (all DPX instructions but the first add), with E* = E + o and
+// F* = F + o:
+//   P = Hdiag + (s + o);  F* = max(F*_up - e, H_up);  M = max(P, E*, F*);
+//   H = max(M - o, 0);    E*' = max(E* - e, H);       best = max(best, H)
 // Packed mode keeps two subjects in the int16 halves of each register.
 #include "sw_kernels.cuh"
 #include <climits>
@@ -65,10 +65,17 @@ __device__ __forceinline__ uint32_t residue_at(const uint8_t *__restrict__ r, in
   return col < L ? (uint32_t)__ldg(r + col) : padc;
 }
 
-// One pass of G*R rows, score only.  prof points at the pass's row 0.
-// scr_in: H,F of the row above the pass per column (nullptr: the top row of
-// the matrix, H = 0, F = -inf).  scr_out: where the last lane stores its
-// bottom row (nullptr for the last pass).  Returns the lane's best H (packed).
+// One pass of G*R rows, score only.  prof points at the pass's row 0 and
+// holds s(query_i, r) + o (>= 0; padding rows hold 0, i.e. a score of -o).
+// The cell update works with E* = E + o and F* = F + o:
+//   P  = Hdiag + (s + o)          one 32-bit add: never carries across the
+//                                 int16 lanes because every lane stays >= 0
+//   F* = max(F*_up - e, H_up)     M = max(P, E*, F*)     H = max(M - o, 0)
+//   E*' = max(E* - e, H)          best = max(best, H)
+// i.e. 4.5 DPX instructions per register of cells, the lane-local add aside.
+// scr_in: H,F* of the row above the pass per column (nullptr: the top row of
+// the matrix, H = 0, F* = 0 (F = -o)).  scr_out: where the last lane stores
+// its bottom row (nullptr for the last pass).  Returns the lane's best H.
 template <int G, int R, bool PACK>
 __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int stride,
                                          const uint8_t *__restrict__ rA, int LA,
@@ -78,8 +85,6 @@ __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int st
                                          int2 *__restrict__ scr_out) {
   using C = Cell<PACK>;
   const int negO = C::splat(-o), negE = C::splat(-e);
-  const int floorv = C::splat(-o);  // E and F never fall below -o (H >= 0)
-  const int low = PACK ? C::splat(-32768) : INT_MIN / 2;
   const uint32_t pc = (uint32_t)padc;
   auto fetch = [&](int col) -> uint32_t {
     uint32_t v = residue_at(rA, LA, col, pc);
@@ -89,10 +94,16 @@ __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int st
 
   int H[R], E[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = floorv; }
-  int hbot = 0, fbot = floorv, htop_prev = 0, best = 0;
+  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = 0; }
+  int hbot = 0, fbot = 0, htop_prev = 0, best = 0;
   uint32_t resv = pc | (pc << 8);
   uint32_t cur = fetch(t), nxt = fetch(G + t);
+  // the row above the pass, prefetched two columns ahead
+  int2 sv0 = make_int2(0, 0), sv1 = make_int2(0, 0);
+  if (scr_in != nullptr) {
+    if (0 < Lw) sv0 = scr_in[0];
+    if (1 < Lw) sv1 = scr_in[1];
+  }
   const int8_t *pb = prof + t * R;
   const int steps = Lw + G - 1;
 
@@ -103,14 +114,14 @@ __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int st
     uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
     int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
     int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    const int2 sv = sv0;
+    sv0 = sv1;
+    if (scr_in != nullptr && k + 2 < Lw) sv1 = scr_in[k + 2];
     if (t == 0) {
       rin = r0;
-      if (scr_in != nullptr && k < Lw) {
-        const int2 v = scr_in[k];
-        hin = v.x; fin = v.y;
-      } else {
-        hin = 0; fin = floorv;
-      }
+      const bool above = scr_in != nullptr && k < Lw;
+      hin = above ? sv.x : 0;
+      fin = above ? sv.y : 0;
     }
     resv = rin;
     ProfRow<R> pa, pq;
@@ -119,21 +130,21 @@ __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int st
 
     int hdiag = htop_prev;
     htop_prev = hin;
-    int xup = C::addmax(hin, negO, low);
+    int hup = hin;
     int f = fin;
     Unroll<R>::run([&](auto ic) {
       constexpr int r = decltype(ic)::value;
       int s;
       if constexpr (PACK) s = C::template score<r & 3>(pa.w[r >> 2], pq.w[r >> 2]);
       else s = C::template score<r & 3>(pa.w[r >> 2], 0u);
-      const int d = C::addmax_relu(hdiag, s, E[r]);
-      f = C::addmax(f, negE, xup);
+      const int pdiag = hdiag + s;              // lanes stay in [0, 32767]: no carry
+      f = C::addmax(f, negE, hup);              // F*
+      const int m = C::vmax3(pdiag, E[r], f);   // max(P, E*, F*)
+      const int hn = C::addmax_relu(m, negO, 0);
+      E[r] = C::addmax(E[r], negE, hn);         // E* of the next column
       hdiag = H[r];
-      const int hn = C::vmax(d, f);
-      const int x = C::addmax(hn, negO, low);
-      E[r] = C::addmax(E[r], negE, x);
       H[r] = hn;
-      xup = x;
+      hup = hn;
       if constexpr ((r & 1) == 1) best = C::vmax3(best, H[r - 1], hn);
     });
     hbot = H[R - 1];
@@ -187,8 +198,8 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
     const int prow = np * G * R;
     for (int idx = threadIdx.x; idx < (K + 1) * prow; idx += NT) {
       const int r = idx / prow, i = idx - r * prow;
-      int v = MSA_PAD_SCORE;
-      if (r < K && i < Lq) v = sM[rq[i] * K + r];
+      int v = 0;  // padding: score -o
+      if (r < K && i < Lq) v = sM[rq[i] * K + r] + sc.o;
       smem[r * stride + i] = (int8_t)v;
     }
     __syncthreads();
@@ -240,6 +251,188 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
   }
 }
 
+// ------------------------------------------------------------ paired queries
+// The int16 lanes hold two queries (adjacent in length order) against ONE
+// subject, so the profile can be stored pre-packed: prof[r*stride + i] =
+// (s(qA_i, r) + o) | (s(qB_i, r) + o) << 16, and P = Hdiag + prof is a single
+// add with no unpacking.  Lane t reads R words (R/4 16-byte loads) at word
+// offset t*R; with R/4 odd the eight lanes of a load phase hit eight
+// different 16-byte bank groups whatever residues they read.
+template <int G, int R>
+__device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, int stride,
+                                            const uint8_t *__restrict__ rs, int Ls, int Lw, int t,
+                                            int base_lane, int padc, int o, int e,
+                                            const int2 *__restrict__ scr_in,
+                                            int2 *__restrict__ scr_out) {
+  using C = Cell<true>;
+  static_assert(R % 4 == 0 && (R / 4) % 2 == 1, "R/4 must be odd");
+  const int negO = C::splat(-o), negE = C::splat(-e);
+  const uint32_t pc = (uint32_t)padc;
+  int H[R], E[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = 0; }
+  int hbot = 0, fbot = 0, htop_prev = 0, best = 0;
+  uint32_t resv = pc;
+  uint32_t cur = residue_at(rs, Ls, t, pc), nxt = residue_at(rs, Ls, G + t, pc);
+  int2 sv0 = make_int2(0, 0), sv1 = make_int2(0, 0);
+  if (scr_in != nullptr) {
+    if (0 < Lw) sv0 = scr_in[0];
+    if (1 < Lw) sv1 = scr_in[1];
+  }
+  const uint32_t *pb = prof + t * R;
+  const int steps = Lw + G - 1;
+  for (int k = 0; k < steps; ++k) {
+    const int kk = k & (G - 1);
+    if (kk == 0 && k > 0) { cur = nxt; nxt = residue_at(rs, Ls, k + G + t, pc); }
+    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
+    uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
+    int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
+    int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    const int2 sv = sv0;
+    sv0 = sv1;
+    if (scr_in != nullptr && k + 2 < Lw) sv1 = scr_in[k + 2];
+    if (t == 0) {
+      rin = r0;
+      const bool above = scr_in != nullptr && k < Lw;
+      hin = above ? sv.x : 0;
+      fin = above ? sv.y : 0;
+    }
+    resv = rin;
+    const uint4 *pr = reinterpret_cast<const uint4 *>(pb + resv * stride);
+    uint32_t w[R];
+#pragma unroll
+    for (int c = 0; c < R / 4; ++c) {
+      const uint4 v = pr[c];
+      w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+    }
+    int hdiag = htop_prev;
+    htop_prev = hin;
+    int hup = hin;
+    int f = fin;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int pdiag = hdiag + (int)w[r];       // both lanes stay in [0, 32767]
+      f = C::addmax(f, negE, hup);
+      const int m = C::vmax3(pdiag, E[r], f);
+      const int hn = C::addmax_relu(m, negO, 0);
+      E[r] = C::addmax(E[r], negE, hn);
+      hdiag = H[r];
+      H[r] = hn;
+      hup = hn;
+      if ((r & 1) == 1) best = C::vmax3(best, H[r - 1], hn);
+    }
+    hbot = H[R - 1];
+    fbot = f;
+    if (scr_out != nullptr && t == G - 1) {
+      const int j = k - (G - 1);
+      if (j >= 0 && j < Lw) scr_out[j] = make_int2(hbot, fbot);
+    }
+  }
+  return best;
+}
+
+// Work item = (query pair p, block of NG consecutive subjects, one per group).
+template <int G, int R>
+__global__ void __launch_bounds__(kCenterThreads)
+k_center2(SeqSet ss, Scoring sc, CenterJob job) {
+  extern __shared__ __align__(16) uint32_t smem32[];
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  __shared__ long long s_item;
+  __shared__ unsigned long long s_qsum[2];
+  constexpr int NT = kCenterThreads, NG = NT / G;
+  const int K = sc.K, padc = K, o = sc.o;
+  const int stride = dround_up(job.npass * G * R, 32);
+  for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = sc.M[i];
+  const int g = threadIdx.x / G, t = threadIdx.x % G;
+  const int base_lane = (threadIdx.x & 31) - t;
+  int2 *scr = job.scratch + ((size_t)blockIdx.x * NG + g) * 2 * job.scratch_cols;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = (long long)atomicAdd(job.counter, 1ull);
+      s_qsum[0] = s_qsum[1] = 0ull;
+    }
+    __syncthreads();
+    long long item = s_item;
+    if (item >= job.n_items) break;
+    item = job.n_items - 1 - item;  // longest queries first
+    int lo = 0, hi = job.qe - job.qb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (job.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int pidx = job.qb + lo;  // pair index: queries 2*pidx, 2*pidx+1 of the query list
+    const int xa = 2 * pidx, xb = 2 * pidx + 1;
+    const int qA = job.mode == 0 ? xa : job.qlist[xa];
+    const int qB = xb < job.nq ? (job.mode == 0 ? xb : job.qlist[xb]) : -1;
+    const int s0 = (job.mode == 0 ? xa : 0) + (int)(item - job.prefix[lo]) * NG;
+    const int LqA = ss.len[qA], LqB = qB >= 0 ? ss.len[qB] : 0;
+    const uint8_t *ra = ss.res + ss.pstart[qA];
+    const uint8_t *rb = ss.res + ss.pstart[qB >= 0 ? qB : qA];
+    const int np = (max(LqA, LqB) + G * R - 1) / (G * R);
+    const int prow = np * G * R;
+    for (int idx = threadIdx.x; idx < (K + 1) * prow; idx += NT) {
+      const int r = idx / prow, i = idx - r * prow;
+      uint32_t a = 0, b = 0;  // padding: score -o
+      if (r < K) {
+        if (i < LqA) a = (uint32_t)(sM[ra[i] * K + r] + o);
+        if (i < LqB) b = (uint32_t)(sM[rb[i] * K + r] + o);
+      }
+      smem32[r * stride + i] = a | (b << 16);
+    }
+    __syncthreads();
+
+    const int s = s0 + g;
+    const bool valid = s < ss.n;
+    const int Ls = valid ? ss.len[s] : 0;
+    const uint8_t *rs = ss.res + (valid ? ss.pstart[s] : 0);
+    const int Lw = __reduce_max_sync(MSA_FULL_MASK, Ls);
+    int best = 0;
+    if (Lw > 0) {
+      for (int p = 0; p < np; ++p) {
+        const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
+        int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
+        const int b = wave_pass_pp<G, R>(smem32 + p * G * R, stride, rs, Ls, Lw, t, base_lane,
+                                         padc, o, sc.e, sin, sout);
+        best = Cell<true>::vmax(best, b);
+        __syncwarp();
+      }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+      best = Cell<true>::vmax(best, __shfl_xor_sync(MSA_FULL_MASK, best, off));
+    if (t == 0 && valid) {
+#pragma unroll
+      for (int l = 0; l < 2; ++l) {
+        const int q = l ? qB : qA;
+        if (q < 0) continue;
+        // all pairs: lane B's first subject (the lane-A query) is counted by lane A
+        if (job.mode == 0 && l == 1 && s < qB) continue;
+        const int S = l ? Cell<true>::lane1(best) : Cell<true>::lane0(best);
+        if (S > job.sat_thresh) {
+          const unsigned slot = atomicAdd(job.ovf_count, 1u);
+          if (slot < (unsigned)job.ovf_cap) job.ovf[slot] = make_int2(q, s);
+          else atomicOr(job.err, MSA_DERR_OVERFLOW);
+          continue;
+        }
+        if (job.mode == 0) {
+          if (s == q) job.self[q] = S;
+          else {
+            atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+            atomicAdd(&s_qsum[l], (unsigned long long)(long long)S);
+          }
+        } else {
+          atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && job.mode == 0) {
+      if (s_qsum[0]) atomicAdd(&job.pairsum[qA], s_qsum[0]);
+      if (qB >= 0 && s_qsum[1]) atomicAdd(&job.pairsum[qB], s_qsum[1]);
+    }
+  }
+}
+
 // ------------------------------------------------------------ pair list
 // Each group takes one pair at a time; its own profile holds the current
 // pass's G*R query rows.
@@ -274,8 +467,8 @@ __global__ void __launch_bounds__(256) k_pairs(SeqSet ss, Scoring sc, PairJob jo
       __syncwarp();
       for (int idx = t; idx < (K + 1) * SR; idx += G) {
         const int r = idx / SR, i = idx - r * SR, qi = p * SR + i;
-        int v = MSA_PAD_SCORE;
-        if (r < K && qi < La) v = sM[ra[qi] * K + r];
+        int v = 0;  // padding: score -o
+        if (r < K && qi < La) v = sM[ra[qi] * K + r] + sc.o;
         prof[idx] = (int8_t)v;
       }
       __syncwarp();
@@ -441,33 +634,43 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
 
 // ------------------------------------------------------------ host side
 
-const WaveShape kCenterShapes[] = {{8, 8}, {8, 12}, {8, 16}, {16, 8}, {16, 12},
-                                   {16, 16}, {32, 8}, {32, 12}, {32, 16}};
-const int kNumCenterShapes = sizeof(kCenterShapes) / sizeof(kCenterShapes[0]);
+// Kernel variants of center selection.  Paired-query variants (k_center2)
+// carry two queries in the int16 lanes; single-query variants (k_center) carry
+// two subjects (packed) or one (int32).  Every shape keeps the profile loads
+// free of shared-memory bank conflicts.
+const CenterVariant kCenterVariants[] = {
+    {1, 8, 12, true},  {1, 8, 20, true},  {1, 8, 28, true},  {1, 16, 12, true},
+    {1, 16, 20, true}, {1, 16, 28, true}, {1, 32, 12, true}, {1, 32, 20, true},
+    {1, 32, 28, true}, {0, 32, 16, true}, {0, 32, 24, true}, {0, 8, 16, false},
+    {0, 16, 16, false}, {0, 32, 16, false}};
+const int kNumCenterVariants = sizeof(kCenterVariants) / sizeof(kCenterVariants[0]);
 
-int center_smem_bytes(int K, int rows_alloc) {
+int center_smem_bytes(int variant, int K, int rows_alloc) {
+  const CenterVariant &v = kCenterVariants[variant];
+  if (v.paired) return (K + 1) * round_up_int(rows_alloc, 32) * 4;
   return (K + 1) * round_up_int(rows_alloc, MSA_PROF_ALIGN);
 }
 
 typedef void (*center_fn)(SeqSet, Scoring, CenterJob);
 
-static center_fn center_kernel(int shape, bool packed) {
-#define MSA_SHAPE_CASE(idx, G, R)                         \
-  case idx:                                               \
-    return packed ? k_center<G, R, true> : k_center<G, R, false>;
-  switch (shape) {
-    MSA_SHAPE_CASE(0, 8, 8)
-    MSA_SHAPE_CASE(1, 8, 12)
-    MSA_SHAPE_CASE(2, 8, 16)
-    MSA_SHAPE_CASE(3, 16, 8)
-    MSA_SHAPE_CASE(4, 16, 12)
-    MSA_SHAPE_CASE(5, 16, 16)
-    MSA_SHAPE_CASE(6, 32, 8)
-    MSA_SHAPE_CASE(7, 32, 12)
-    MSA_SHAPE_CASE(8, 32, 16)
+static center_fn center_kernel(int variant) {
+  switch (variant) {
+    case 0: return k_center2<8, 12>;
+    case 1: return k_center2<8, 20>;
+    case 2: return k_center2<8, 28>;
+    case 3: return k_center2<16, 12>;
+    case 4: return k_center2<16, 20>;
+    case 5: return k_center2<16, 28>;
+    case 6: return k_center2<32, 12>;
+    case 7: return k_center2<32, 20>;
+    case 8: return k_center2<32, 28>;
+    case 9: return k_center<32, 16, true>;
+    case 10: return k_center<32, 24, true>;
+    case 11: return k_center<8, 16, false>;
+    case 12: return k_center<16, 16, false>;
+    case 13: return k_center<32, 16, false>;
     default: return nullptr;
   }
-#undef MSA_SHAPE_CASE
 }
 
 static int sm_count() {
@@ -486,18 +689,18 @@ static int occupancy_grid(const void *fn, int threads, int smem) {
   return per_sm * sm_count();
 }
 
-int center_grid(int shape, bool packed, int smem) {
-  center_fn fn = center_kernel(shape, packed);
+int center_grid(int variant, int smem) {
+  center_fn fn = center_kernel(variant);
   if (!fn) return 0;
   return occupancy_grid((const void *)fn, kCenterThreads, smem);
 }
 
-cudaError_t launch_center(int shape, bool packed, const SeqSet &ss, const Scoring &sc,
-                          const CenterJob &job, int grid, cudaStream_t st) {
-  center_fn fn = center_kernel(shape, packed);
+cudaError_t launch_center(int variant, const SeqSet &ss, const Scoring &sc, const CenterJob &job,
+                          int grid, cudaStream_t st) {
+  center_fn fn = center_kernel(variant);
   if (!fn) return cudaErrorInvalidValue;
-  const WaveShape ws = kCenterShapes[shape];
-  const int smem = center_smem_bytes(sc.K, job.npass * ws.G * ws.R);
+  const CenterVariant &v = kCenterVariants[variant];
+  const int smem = center_smem_bytes(variant, sc.K, job.npass * v.G * v.R);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   fn<<<grid, kCenterThreads, smem, st>>>(ss, sc, job);

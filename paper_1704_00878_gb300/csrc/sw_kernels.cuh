@@ -19,7 +19,8 @@ struct Scoring {
 struct CenterJob {
   int mode;                       // 0: query q vs subjects [q, n) ; 1: query qlist[x] vs [0, n)
   const int32_t *qlist;           // mode 1 (sorted indices)
-  int qb, qe;                     // query range (sorted index for mode 0, qlist index for mode 1)
+  int nq;                         // queries in the list (mode 0: n)
+  int qb, qe;                     // item-unit range: queries (single) or query pairs (paired)
   const int64_t *prefix;          // device, qe-qb+1 entries: first item of each query
   int64_t n_items;
   int npass;                      // passes of the longest query in the range
@@ -53,15 +54,16 @@ struct CodesJob {
   int2 *scratch; int scratch_cols;
 };
 
-// Variant table for the packed center kernel: threads per group and rows per thread.
-struct WaveShape { int G, R; };
-extern const WaveShape kCenterShapes[];
-extern const int kNumCenterShapes;
+// Kernel variants of center selection: paired = two queries in the int16
+// lanes (k_center2), else one query with two packed subjects or int32 cells.
+struct CenterVariant { int paired, G, R; bool packed; };
+extern const CenterVariant kCenterVariants[];
+extern const int kNumCenterVariants;
 
-int center_smem_bytes(int K, int rows_alloc);
-cudaError_t launch_center(int shape, bool packed, const SeqSet &ss, const Scoring &sc,
-                          const CenterJob &job, int grid, cudaStream_t st);
-int center_grid(int shape, bool packed, int smem);
+int center_smem_bytes(int variant, int K, int rows_alloc);
+cudaError_t launch_center(int variant, const SeqSet &ss, const Scoring &sc, const CenterJob &job,
+                          int grid, cudaStream_t st);
+int center_grid(int variant, int smem);
 
 cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJob &job,
                          int grid, cudaStream_t st);

@@ -125,10 +125,11 @@ def _mutate(rng, seq, w, cdf, bg_cdf):
     return out
 
 
-def generate(name_or_workload, n=None, seed=None):
+def generate(name_or_workload, n=None, seed=None, length=None):
     """Return (letters_ascii uint8[total], offsets int64[n+1], workload, family int64[n]).
 
-    `n` and `seed` override the workload's count and seed (same distributions).
+    `n` and `seed` override the workload's count and seed (same distributions);
+    `length` overrides the length distribution (same tuple form as Workload).
     """
     w = WORKLOADS[name_or_workload] if isinstance(name_or_workload, str) else name_or_workload
     n = w.n if n is None else int(n)
@@ -142,7 +143,7 @@ def generate(name_or_workload, n=None, seed=None):
     ancestors = [np.searchsorted(bg_cdf, rng.random(w.ancestor_len), side="right")
                  for _ in range(w.families)]
     n_gen = n - 1 if w.center_seq else n
-    lens = _lengths(rng, w.length, n_gen)
+    lens = _lengths(rng, w.length if length is None else tuple(length), n_gen)
     fams = rng.integers(0, w.families, size=n_gen)
     seqs = []
     if w.center_seq:

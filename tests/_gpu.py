@@ -29,6 +29,6 @@ def oracle_problem(letters, offsets, alph, M, o, e):
 
 def random_set(rng, n, lo, hi, alph, emit=None):
     emit = emit or alph
-    seqs = [bytes(rng.choice(list(emit.encode()), size=int(rng.integers(lo, hi + 1))))
-            for _ in range(n)]
+    pool = np.frombuffer(emit.encode(), dtype=np.uint8)
+    seqs = [rng.choice(pool, size=int(rng.integers(lo, hi + 1))) for _ in range(n)]
     return pack_sequences(seqs)
