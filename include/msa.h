@@ -87,6 +87,34 @@ int msa_load(msa_ctx *ctx, const uint8_t *letters, const int64_t *offsets, int64
  * sequence); scores_out: host or device int32[npairs]. */
 int msa_pair_scores(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, int32_t *scores_out);
 
+/* Allocation-free variant of msa_pair_scores.  The paper has no counterpart;
+ * this entry point exists for callers that must not allocate device memory:
+ * code that runs while a CUDA graph is being captured, processes whose device
+ * memory belongs to another allocator, or services that forbid driver
+ * allocations once they are running.  It needs no context and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   residues: device uint8, alphabet indices 0..alphabet-1 (already encoded);
+ *     sequence i is residues[offsets[i] .. offsets[i+1]).
+ *   offsets: device int64[n+1].  pairs: device int64[npairs][2] (row
+ *     sequence, column sequence).  scores_out: device int32[npairs].
+ *   max_len: the longest sequence any listed pair touches, 1..MSA_MAX_LEN;
+ *     a pair touching a longer sequence (or an index outside 0..n-1) gets
+ *     score -1 and the call returns MSA_ERANGE.
+ *   matrix: host alphabet x alphabet scores, gap_open/gap_extend as in
+ *     msa_params; cuda_stream: where the work runs (NULL = legacy stream).
+ * Working memory is one fixed 32 MiB array per device, held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up that array's device address (with the device current); make that
+ * first call before any stream capture begins.  All calls on a device share
+ * the array and each call clears its counter, so calls that overlap on the
+ * GPU race: run them one after another.  Long sequences shrink the number of
+ * thread blocks that fit the array (32 at max_len = MSA_MAX_LEN).  Returns
+ * after the stream has finished the call. */
+int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int64_t n,
+                            const int64_t *pairs, int64_t npairs, int32_t max_len,
+                            const int8_t *matrix, int32_t alphabet, int32_t gap_open,
+                            int32_t gap_extend, int32_t *scores_out, void *cuda_stream);
+
 /* Choose the center star sequence (Figure 3's first MapReduce step).
  * EXACT: center = argmin_i sum_j d(i,j), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B)
  *   over all j (lowest index on ties).

@@ -53,6 +53,10 @@ _SIGS = {
     "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_pair_scores_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                               ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                               ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -135,6 +139,23 @@ def msa_pair_scores(ctx, pairs, out=None):
     res = np.zeros(pr.shape[0], np.int32) if out is None else out
     _check(ctx, lib().msa_pair_scores(ctx, _ptr(pr), pr.shape[0], _ptr(res)))
     return res
+
+
+def msa_pair_scores_noalloc(residues, offsets, pairs, max_len, matrix, gap_open, gap_extend,
+                            scores_out, stream=None):
+    """Allocation-free pair scores for callers that cannot allocate device
+    memory: every array is a CUDA tensor the caller owns (residues uint8
+    alphabet indices, offsets int64[n+1], pairs int64[npairs, 2], scores_out
+    int32[npairs]); matrix is a host array.  Raises MSAError on failure."""
+    M = np.ascontiguousarray(matrix, dtype=np.int8)
+    st = getattr(stream, "cuda_stream", stream)
+    rc = lib().msa_pair_scores_noalloc(_ptr(residues), _ptr(offsets), offsets.numel() - 1,
+                                       _ptr(pairs), pairs.shape[0], int(max_len), _ptr(M),
+                                       int(M.shape[0]), int(gap_open), int(gap_extend),
+                                       _ptr(scores_out), ctypes.c_void_p(st) if st else None)
+    if rc != MSA_OK:
+        raise MSAError(rc, "msa_pair_scores_noalloc failed")
+    return scores_out
 
 
 def msa_select_center(ctx, mode, refs=None):

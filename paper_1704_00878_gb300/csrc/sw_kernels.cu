@@ -20,6 +20,8 @@
 // Packed mode keeps two subjects in the int16 halves of each register.
 #include "sw_kernels.cuh"
 #include <climits>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
 namespace {
@@ -744,4 +746,170 @@ cudaError_t launch_codes(const SeqSet &ss, const Scoring &sc, const CodesJob &jo
     cudaFuncSetAttribute((const void *)k_codes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_codes<<<grid, 256, smem, st>>>(ss, sc, job);
   return cudaGetLastError();
+}
+
+// ===================================================================
+// Allocation-free pair scores (msa_pair_scores_noalloc in include/msa.h).
+//
+// Some callers cannot allocate device memory: code that runs while a CUDA
+// graph is being captured, processes whose device memory is owned by another
+// allocator, or latency-critical services that forbid driver allocations
+// after start-up.  This entry point serves them: the caller passes every
+// input and output buffer, and the only working memory is the fixed array
+// below, which each GPU that loads the library holds until the process exits.
+// Every call on a device shares it, so calls that overlap on the GPU race;
+// issue them one after another (for example on one stream).
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;  // 32 MiB per device
+constexpr size_t kNoallocControlBytes = 256;               // counter + error word
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocG = 32;  // one group per warp, 512 query rows per pass
+
+struct NoallocArgs {
+  int8_t M[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  int K, o, e, max_len;
+  const uint8_t *res;        // alphabet indices, sequence i at offsets[i] .. offsets[i+1]
+  const int64_t *offsets;    // n + 1 entries
+  int64_t n;
+  const int64_t *pairs;      // npairs x 2
+  int64_t npairs;
+  int32_t *out;
+  unsigned char *scratch;    // device address of g_noalloc_scratch
+  int scratch_cols;          // columns of each group's boundary rows (= max_len)
+};
+
+// The pair-list kernel with its inputs read straight from caller buffers and
+// its counter, error word and boundary rows in the fixed array.
+__global__ void __launch_bounds__(256) k_pairs_noalloc(NoallocArgs a) {
+  constexpr int G = kNoallocG, R = kPairsR, NT = 256, NG = NT / G, SR = G * R;
+  extern __shared__ __align__(16) int8_t smem[];
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  const int K = a.K, padc = K;
+  for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = a.M[i];
+  __syncthreads();
+  unsigned long long *counter = reinterpret_cast<unsigned long long *>(a.scratch);
+  unsigned *err = reinterpret_cast<unsigned *>(a.scratch + 8);
+  int2 *rows = reinterpret_cast<int2 *>(a.scratch + kNoallocControlBytes);
+  const int g = threadIdx.x / G, t = threadIdx.x % G;
+  int8_t *prof = smem + (size_t)g * (K + 1) * SR;
+  int2 *scr = rows + ((size_t)blockIdx.x * NG + g) * 2 * a.scratch_cols;
+  for (;;) {
+    long long pi = 0;
+    if (t == 0) pi = (long long)atomicAdd(counter, 1ull);
+    pi = __shfl_sync(MSA_FULL_MASK, pi, 0);
+    if (pi >= a.npairs) break;
+    const int64_t ia = a.pairs[2 * pi], ib = a.pairs[2 * pi + 1];
+    bool ok = ia >= 0 && ia < a.n && ib >= 0 && ib < a.n;
+    int La = 0, Lb = 0;
+    const uint8_t *ra = a.res, *rb = a.res;
+    if (ok) {
+      const int64_t la = a.offsets[ia + 1] - a.offsets[ia], lb = a.offsets[ib + 1] - a.offsets[ib];
+      ok = la >= 1 && la <= a.max_len && lb >= 1 && lb <= a.max_len;
+      if (ok) {
+        La = (int)la; Lb = (int)lb;
+        ra = a.res + a.offsets[ia];
+        rb = a.res + a.offsets[ib];
+      }
+    }
+    if (!ok) {  // the whole warp takes this branch together
+      if (t == 0) { a.out[pi] = -1; atomicOr(err, 1u); }
+      continue;
+    }
+    const int np = (La + SR - 1) / SR;
+    int best = 0;
+    for (int p = 0; p < np; ++p) {
+      __syncwarp();
+      for (int idx = t; idx < (K + 1) * SR; idx += G) {
+        const int r = idx / SR, i = idx - r * SR, qi = p * SR + i;
+        int v = 0;
+        if (r < K && qi < La) v = sM[ra[qi] * K + r] + a.o;
+        prof[idx] = (int8_t)v;
+      }
+      __syncwarp();
+      const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * a.scratch_cols : nullptr;
+      int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * a.scratch_cols : nullptr;
+      best = max(best, wave_pass<G, R, false>(prof, SR, rb, Lb, nullptr, 0, Lb, t, 0, padc, a.o,
+                                              a.e, sin, sout));
+      __syncwarp();
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+      best = max(best, __shfl_xor_sync(MSA_FULL_MASK, best, off));
+    if (t == 0) a.out[pi] = best;
+  }
+}
+
+// Device address of g_noalloc_scratch per device, looked up once (with that
+// device current) by the first call made on it.
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[64] = {};
+
+}  // namespace
+
+extern "C" int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int64_t n,
+                                       const int64_t *pairs, int64_t npairs, int32_t max_len,
+                                       const int8_t *matrix, int32_t alphabet, int32_t gap_open,
+                                       int32_t gap_extend, int32_t *scores_out,
+                                       void *cuda_stream) {
+  if (npairs == 0) return MSA_OK;
+  if (!residues || !offsets || !pairs || !scores_out || !matrix || n < 1 || npairs < 0)
+    return MSA_EINVAL;
+  if (alphabet < 1 || alphabet > MSA_MAX_ALPHABET) return MSA_EINVAL;
+  if (gap_extend < 1 || gap_open < gap_extend) return MSA_EINVAL;
+  if (max_len < 1 || max_len > MSA_MAX_LEN) return MSA_ERANGE;
+  NoallocArgs a;
+  memset(&a, 0, sizeof a);
+  for (int i = 0; i < alphabet * alphabet; ++i) {
+    const int v = matrix[i] + gap_open;
+    if (v > 127 || v < -128) return MSA_EINVAL;
+    a.M[i] = matrix[i];
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MSA_ECUDA;
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return MSA_ECUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  constexpr int NG = 256 / kNoallocG;
+  const int np_max = (max_len + kNoallocG * kPairsR - 1) / (kNoallocG * kPairsR);
+  const size_t per_cta = np_max > 1 ? (size_t)NG * 2 * max_len * sizeof(int2) : 0;
+  const int smem = NG * (alphabet + 1) * kNoallocG * kPairsR;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute((const void *)k_pairs_noalloc,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return MSA_ECUDA;
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_noalloc, 256, smem);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long grid = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+  if (per_cta > 0)
+    grid = std::min<long long>(grid, (long long)((kNoallocScratchBytes - kNoallocControlBytes) / per_cta));
+  if (grid < 1) return MSA_ERANGE;
+  a.K = alphabet; a.o = gap_open; a.e = gap_extend; a.max_len = max_len;
+  a.res = residues; a.offsets = offsets; a.n = n; a.pairs = pairs; a.npairs = npairs;
+  a.out = scores_out;
+  a.scratch = static_cast<unsigned char *>(base);
+  a.scratch_cols = max_len;
+  // the work counter and the error word must start at zero on every call
+  if (cudaMemsetAsync(base, 0, kNoallocControlBytes, st) != cudaSuccess) return MSA_ECUDA;
+  k_pairs_noalloc<<<(unsigned)grid, 256, smem, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return MSA_ECUDA;
+  unsigned herr = 0;
+  if (cudaMemcpyAsync(&herr, static_cast<unsigned char *>(base) + 8, sizeof herr,
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MSA_ECUDA;
+  return herr ? MSA_ERANGE : MSA_OK;
 }
