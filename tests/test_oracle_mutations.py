@@ -26,17 +26,36 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(name, tmp_path):
-    old, new = MUTATIONS[name]
+# mistakes in the fp64 network oracle, caught by tests/test_net_oracle.py
+NET_MUTATIONS = {
+    "pool_drops_1_over_L": ("dy4 = np.tile(de / L, (L, 1))", "dy4 = np.tile(de, (L, 1))"),
+    "relu_gate_missing": ("dz2 = da2 * (a2 > 0)", "dz2 = da2"),
+    "taps_flipped": ("out += xp[k:k + L] @ W[k]", "out += xp[k:k + L] @ W[TAPS - 1 - k]"),
+    "adam_no_bias_correction": ("mh = m / (1 - beta1 ** step)", "mh = m"),
+}
+
+
+def _run_mutated(tmp_path, rel_src, old, new, pins, name):
     for d in ("oracle", "seqgen", "tests"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    src = tmp_path / "oracle" / "msa_oracle.c"
+    src = tmp_path / rel_src
     text = src.read_text()
     assert text.count(old) == 1, "mutation site moved: " + name
     src.write_text(text.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], cwd=tmp_path,
+                        pins], cwd=tmp_path,
                        stdout=subprocess.PIPE, stderr=subprocess.STDOUT, timeout=600)
     assert r.returncode == 1, r.stdout.decode()[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    _run_mutated(tmp_path, "oracle/msa_oracle.c", old, new, "tests/test_oracle_pins.py", name)
+
+
+@pytest.mark.parametrize("name", sorted(NET_MUTATIONS))
+def test_planted_network_mistake_is_caught(name, tmp_path):
+    old, new = NET_MUTATIONS[name]
+    _run_mutated(tmp_path, "oracle/net.py", old, new, "tests/test_net_oracle.py", name)
