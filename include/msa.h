@@ -119,7 +119,8 @@ int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int
  * EXACT: center = argmin_i sum_j d(i,j), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B)
  *   over all j (lowest index on ties).
  * EXACT_SAMPLED: the same sum over j in refs (host int64[nref], distinct).
- * LEARNED: argmin_i ||e_i - mean(e)||^2 over the selector's embeddings.
+ * LEARNED: argmin_i ||e_i - mean(e)||^2 over the selector's embeddings
+ *   (msa_selector_*); ESTATE if no parameters are set.
  * FIRST: 0.
  * center_out: host int64; sum_dist_out (nullable, host int64): the winning
  * row sum (EXACT modes), else 0.  ESTATE for LEARNED without a selector. */
@@ -164,6 +165,64 @@ int msa_merge_gaps(msa_ctx *ctx, uint8_t *msa_out, int64_t *width_out);
  * avg SP = cost / (n(n-1)/2).  sp_cost_out: host int64. */
 int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out);
 
+/* ------------------------------------------------------------------ */
+/* Learned center selector.  The paper selects the center with Smith-
+ * Waterman scores over all pairs (O(n^2) alignments); the selector is a 1-D
+ * convolutional embedding network whose squared embedding distances are
+ * trained to follow the normalised exact distance
+ *   t(A,B) = d(A,B) / (S(A,A) + S(B,B)),  d as in msa_select_center,
+ * so that the center can be picked in O(n): argmin_i ||e_i - mean(e)||^2.
+ * Architecture (fixed): one-hot residues over 32 channels -> 9-tap conv to
+ * 128 channels + ReLU -> two 9-tap 128->128 convs + ReLU -> 9-tap 128->64
+ * conv -> mean over the sequence's positions.  Compute in bf16 on the
+ * tensor cores with fp32 accumulation; fp32 master weights; Adam.
+ * Parameters (fp32, flat, in this order): W1 [9][32][128], b1 [128],
+ * W2 [9][128][128], b2 [128], W3 [9][128][128], b3 [128], W4 [9][128][64],
+ * b4 [64]; W[tap][in][out] multiplies the input row at offset tap-4. */
+typedef struct {
+    int32_t steps;        /* optimizer steps */
+    int32_t batch_pairs;  /* pairs per step */
+    float lr, beta1, beta2, eps;   /* Adam */
+    uint64_t seed;        /* pair shuffling (and the initial weights if none are set) */
+} msa_train_cfg;
+
+/* Set the selector's parameters: params host or device float[count] with
+ * count = the parameter count (msa_selector_params), or NULL for the seeded
+ * default initialisation (He-uniform, zero biases).  Resets Adam. */
+int msa_selector_init(msa_ctx *ctx, uint64_t seed, const float *params, int64_t count);
+
+/* Copy the fp32 parameters to params_out (host or device, nullable) and/or
+ * report their count (count_out, nullable, host). */
+int msa_selector_params(msa_ctx *ctx, float *params_out, int64_t *count_out);
+
+/* Training targets t(A,B) of listed pairs (host int64[npairs][2], input
+ * indices), computed with the exact Smith-Waterman kernel; targets_out host
+ * or device float[npairs]. */
+int msa_selector_targets(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, float *targets_out);
+
+/* Mean pair loss (||e_A - e_B||^2 - t)^2 over the listed pairs and its
+ * gradient with respect to every parameter, without updating them.
+ * pairs host int64[npairs][2]; targets host float[npairs]; grad_out host or
+ * device float[count] (nullable); loss_out host or device float (nullable). */
+int msa_selector_grad(msa_ctx *ctx, const int64_t *pairs, const float *targets, int64_t npairs,
+                      float *grad_out, float *loss_out);
+
+/* Train: cfg->steps Adam steps over batches of cfg->batch_pairs pairs drawn
+ * from the list (reshuffled every pass).  targets: host float[npairs], or
+ * NULL to compute them with the exact kernel.  Initialises the parameters
+ * from cfg->seed if none are set.  losses_out: host float[cfg->steps]
+ * (nullable), the loss of each step's batch before its update. */
+int msa_selector_train(msa_ctx *ctx, const int64_t *pairs, const float *targets, int64_t npairs,
+                       const msa_train_cfg *cfg, float *losses_out);
+
+/* Embeddings of every loaded sequence, host or device float[n][64]. */
+int msa_selector_embed(msa_ctx *ctx, float *emb_out);
+
+/* Save / load the parameters (8-byte magic "MSASEL1", int64 count, fp32
+ * values). */
+int msa_save_selector(msa_ctx *ctx, const char *path);
+int msa_load_selector(msa_ctx *ctx, const char *path);
+
 /* Sizes of the current state: dims_out host int64[4] = {n, center (-1 if
  * none), Lc (center length, 0 if none), W (MSA width, 0 before a merge)}. */
 int msa_dims(msa_ctx *ctx, int64_t *dims_out);
@@ -171,7 +230,7 @@ int msa_dims(msa_ctx *ctx, int64_t *dims_out);
 /* Device milliseconds of the stages of the last calls, CUDA events on the
  * context stream: [0] encode, [1] center selection, [2] align DP, [3]
  * traceback, [4] merge, [5] rows, [6] SP, [7] center DP kernels alone, [8]
- * align DP kernels alone.  counters_out (nullable, int64[3]): DP cells of the
+ * align DP kernels alone, [9] selector (embedding or training).  counters_out (nullable, int64[3]): DP cells of the
  * last center selection, DP cells of the last alignment, kernels launched by
  * this context since msa_create. */
 int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_out);

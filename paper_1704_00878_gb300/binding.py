@@ -19,13 +19,19 @@ MSA_CENTER_EXACT, MSA_CENTER_EXACT_SAMPLED, MSA_CENTER_LEARNED, MSA_CENTER_FIRST
 MSA_MAX_LEN = 8192
 
 STAGES = ("encode", "center", "align_dp", "traceback", "merge", "rows", "sp", "center_kernels",
-          "align_kernels")
+          "align_kernels", "selector")
 
 
 class MSAError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (code %d)" % (msg, code))
         self.code = code
+
+
+class msa_train_cfg(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch_pairs", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
 class msa_params(ctypes.Structure):
@@ -53,6 +59,16 @@ _SIGS = {
     "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
+    "msa_selector_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_selector_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "msa_selector_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_selector_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.POINTER(msa_train_cfg), ctypes.c_void_p]),
+    "msa_selector_embed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_save_selector": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "msa_load_selector": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "msa_pair_scores_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -223,6 +239,66 @@ def msa_stage_times(ctx):
     _check(ctx, lib().msa_stage_times(ctx, _ptr(ms), len(STAGES), _ptr(cnt)))
     return (dict(zip(STAGES, (float(x) for x in ms))),
             {"center_cells": int(cnt[0]), "align_cells": int(cnt[1]), "launches": int(cnt[2])})
+
+
+def msa_selector_init(ctx, seed=0, params=None):
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, lib().msa_selector_init(ctx, int(seed), _ptr(p), 0 if p is None else p.size))
+
+
+def msa_selector_params(ctx):
+    cnt = np.zeros(1, np.int64)
+    _check(ctx, lib().msa_selector_params(ctx, None, _ptr(cnt)))
+    out = np.zeros(int(cnt[0]), np.float32)
+    _check(ctx, lib().msa_selector_params(ctx, _ptr(out), _ptr(cnt)))
+    return out
+
+
+def msa_selector_targets(ctx, pairs):
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    out = np.zeros(pr.shape[0], np.float32)
+    _check(ctx, lib().msa_selector_targets(ctx, _ptr(pr), pr.shape[0], _ptr(out)))
+    return out
+
+
+def msa_selector_grad(ctx, pairs, targets):
+    """(loss, gradient float32[count])."""
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    t = np.ascontiguousarray(targets, dtype=np.float32)
+    cnt = np.zeros(1, np.int64)
+    _check(ctx, lib().msa_selector_params(ctx, None, _ptr(cnt)))
+    g = np.zeros(int(cnt[0]), np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(ctx, lib().msa_selector_grad(ctx, _ptr(pr), _ptr(t), pr.shape[0], _ptr(g), _ptr(loss)))
+    return float(loss[0]), g
+
+
+def msa_selector_train(ctx, pairs, targets=None, steps=100, batch_pairs=256, lr=1e-3,
+                       beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
+    """Returns the per-step batch losses (float32[steps])."""
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.float32)
+    cfg = msa_train_cfg(int(steps), int(batch_pairs), float(lr), float(beta1), float(beta2),
+                        float(eps), int(seed))
+    losses = np.zeros(max(1, int(steps)), np.float32)
+    _check(ctx, lib().msa_selector_train(ctx, _ptr(pr), _ptr(t), pr.shape[0], ctypes.byref(cfg),
+                                         _ptr(losses)))
+    return losses[:int(steps)]
+
+
+def msa_selector_embed(ctx, out=None):
+    n = msa_dims(ctx)[0]
+    res = np.zeros((n, 64), np.float32) if out is None else out
+    _check(ctx, lib().msa_selector_embed(ctx, _ptr(res)))
+    return res
+
+
+def msa_save_selector(ctx, path):
+    _check(ctx, lib().msa_save_selector(ctx, str(path).encode()))
+
+
+def msa_load_selector(ctx, path):
+    _check(ctx, lib().msa_load_selector(ctx, str(path).encode()))
 
 
 MSA_PROBE_VIADDMAX_S16X2, MSA_PROBE_VIMAX3_S16X2, MSA_PROBE_VIADDMAX_S32, MSA_PROBE_PRMT = 0, 1, 2, 3

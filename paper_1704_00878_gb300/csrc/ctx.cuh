@@ -1,0 +1,110 @@
+// ctx.cuh -- the context behind the C ABI and the host helpers shared by
+// its translation units (msa_api.cu, selector.cu).  Private to the library.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "msa.h"
+#include "msa_kernels.cuh"
+#include "sw_kernels.cuh"
+
+namespace msa_detail {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+enum Stage {
+  ST_ENCODE = 0, ST_CENTER, ST_ALIGN, ST_TRACE, ST_MERGE, ST_ROWS, ST_SP, ST_CENTER_K, ST_ALIGN_K,
+  ST_SELECTOR, ST_N
+};
+
+struct Selector;  // the learned center selector (selector.cu)
+void selector_free(Selector *s);
+
+}  // namespace msa_detail
+
+struct msa_ctx {
+  using DevBuf = msa_detail::DevBuf;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  int K = 0, o = 0, e = 0, precision = MSA_AUTO, sat_limit = 32767, smax = 0, smin = 0;
+  std::vector<int8_t> hM;
+  std::string letters;
+  uint8_t hlut[256];
+  std::string err;
+
+  // scoring tables on the device
+  int8_t *dM = nullptr;
+  char *dLetters = nullptr;
+  uint8_t *dLut = nullptr, *dSymLut = nullptr;
+
+  // the loaded set (sorted by length, ascending, stable)
+  int n = 0, maxlen = 0;
+  std::vector<int32_t> len_sorted, perm, inv;
+  std::vector<int64_t> pstart;
+  DevBuf res, d_pstart, d_len, d_perm, d_inv, d_srcoff, staging;
+
+  // center selection
+  DevBuf pairsum, self, rowsum, prefix, qlist, ovf, ovf_scores, ovf_dst, part_val, part_idx,
+      pairs, pair_dst, pair_out;
+  bool have_rowsum = false;
+
+  // alignment
+  int64_t center = -1;
+  int Lc = 0;
+  DevBuf ins, occ, seg, score, codes, code_off, best;
+  bool aligned = false;
+
+  // merge
+  DevBuf G, off, msa, counts;
+  int64_t W = 0;
+  bool merged = false;
+
+  // small device scalars
+  unsigned long long *dcounter = nullptr;
+  unsigned *derr = nullptr;     // derr[0] error bits, derr[1] overflow count
+  long long *dsmall = nullptr;  // [0] total, [1] argmin val, [2] argmin idx, [3] width, [4] sp
+  DevBuf scratch;
+
+  cudaEvent_t ev[2 * msa_detail::ST_N] = {};
+  float stage_ms[msa_detail::ST_N] = {};
+  int64_t cells[2] = {0, 0};
+  int64_t launches = 0;
+  size_t codes_budget = (size_t)4 << 30;
+
+  msa_detail::Selector *sel = nullptr;
+};
+
+namespace msa_detail {
+
+int fail(msa_ctx *c, int code, const char *fmt, ...);
+int ensure(msa_ctx *ctx, DevBuf &b, size_t bytes);
+template <class T> T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+bool is_device_ptr(const void *p);
+int set_device(msa_ctx *ctx);
+void stage_begin(msa_ctx *ctx, int s);
+void stage_end(msa_ctx *ctx, int s);
+void stage_collect(msa_ctx *ctx, int s);
+SeqSet seqset(msa_ctx *ctx);
+Scoring scoring(msa_ctx *ctx);
+int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector<int32_t> &dst_in,
+              int32_t *d_out);
+int selector_center(msa_ctx *ctx, int64_t *center_out);
+
+}  // namespace msa_detail
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return msa_detail::fail(ctx, e_ == cudaErrorMemoryAllocation ? MSA_ENOMEM : MSA_ECUDA, \
+                              "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)                \
+  do {                           \
+    int r_ = (expr);             \
+    if (r_ != MSA_OK) return r_; \
+  } while (0)

@@ -13,67 +13,9 @@
 #include "msa_kernels.cuh"
 #include "sw_kernels.cuh"
 
-namespace {
+#include "ctx.cuh"
 
-struct DevBuf {
-  void *p = nullptr;
-  size_t cap = 0;
-};
-
-enum Stage { ST_ENCODE = 0, ST_CENTER, ST_ALIGN, ST_TRACE, ST_MERGE, ST_ROWS, ST_SP, ST_CENTER_K, ST_ALIGN_K, ST_N };
-
-}  // namespace
-
-struct msa_ctx {
-  int dev = 0;
-  cudaStream_t st = nullptr;
-  int K = 0, o = 0, e = 0, precision = MSA_AUTO, sat_limit = 32767, smax = 0, smin = 0;
-  std::vector<int8_t> hM;
-  std::string letters;
-  uint8_t hlut[256];
-  std::string err;
-
-  // scoring tables on the device
-  int8_t *dM = nullptr;
-  char *dLetters = nullptr;
-  uint8_t *dLut = nullptr, *dSymLut = nullptr;
-
-  // the loaded set (sorted by length, ascending, stable)
-  int n = 0, maxlen = 0;
-  std::vector<int32_t> len_sorted, perm, inv;
-  std::vector<int64_t> pstart;
-  DevBuf res, d_pstart, d_len, d_perm, d_inv, d_srcoff, staging;
-
-  // center selection
-  DevBuf pairsum, self, rowsum, prefix, qlist, ovf, ovf_scores, ovf_dst, part_val, part_idx,
-      pairs, pair_dst, pair_out;
-  bool have_rowsum = false;
-
-  // alignment
-  int64_t center = -1;
-  int Lc = 0;
-  DevBuf ins, occ, seg, score, codes, code_off, best;
-  bool aligned = false;
-
-  // merge
-  DevBuf G, off, msa, counts;
-  int64_t W = 0;
-  bool merged = false;
-
-  // small device scalars: [0] counter, [1] err + ovf_count, [2..] totals
-  unsigned long long *dcounter = nullptr;
-  unsigned *derr = nullptr;     // derr[0] error bits, derr[1] overflow count
-  long long *dsmall = nullptr;  // [0] total, [1] argmin val, [2] argmin idx, [3] width, [4] sp
-  DevBuf scratch;
-
-  cudaEvent_t ev[2 * ST_N] = {};
-  float stage_ms[ST_N] = {};
-  int64_t cells[2] = {0, 0};
-  int64_t launches = 0;
-  size_t codes_budget = (size_t)4 << 30;
-};
-
-namespace {
+namespace msa_detail {
 
 int fail(msa_ctx *c, int code, const char *fmt, ...) {
   char buf[512];
@@ -84,20 +26,6 @@ int fail(msa_ctx *c, int code, const char *fmt, ...) {
   if (c) c->err = buf;
   return code;
 }
-
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? MSA_ENOMEM : MSA_ECUDA,          \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
-  } while (0)
-
-#define TRY(expr)              \
-  do {                         \
-    int r_ = (expr);           \
-    if (r_ != MSA_OK) return r_; \
-  } while (0)
 
 int ensure(msa_ctx *ctx, DevBuf &b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -114,7 +42,6 @@ int ensure(msa_ctx *ctx, DevBuf &b, size_t bytes) {
   return MSA_OK;
 }
 
-template <class T> T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
 
 bool is_device_ptr(const void *p) {
   cudaPointerAttributes a;
@@ -402,7 +329,9 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   return MSA_OK;
 }
 
-}  // namespace
+}  // namespace msa_detail
+
+using namespace msa_detail;
 
 // ================================================================== C ABI
 
@@ -487,6 +416,8 @@ int msa_create(msa_ctx **out, const msa_params *p, void *cuda_stream) {
 void msa_destroy(msa_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
+  selector_free(ctx->sel);
+  ctx->sel = nullptr;
   DevBuf *bufs[] = {&ctx->res, &ctx->d_pstart, &ctx->d_len, &ctx->d_perm, &ctx->d_inv,
                     &ctx->d_srcoff, &ctx->staging, &ctx->pairsum, &ctx->self, &ctx->rowsum,
                     &ctx->prefix, &ctx->qlist, &ctx->ovf, &ctx->ovf_scores, &ctx->ovf_dst,
@@ -613,7 +544,7 @@ int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
     *center_out = 0;
     return MSA_OK;
   }
-  if (mode == MSA_CENTER_LEARNED) return fail(ctx, MSA_ESTATE, "no trained selector loaded");
+  if (mode == MSA_CENTER_LEARNED) return selector_center(ctx, center_out);
   if (mode != MSA_CENTER_EXACT && mode != MSA_CENTER_EXACT_SAMPLED)
     return fail(ctx, MSA_EINVAL, "unknown center mode %d", mode);
   const int n = ctx->n;
