@@ -57,6 +57,8 @@ def parse():
                     help="override lengths, e.g. uniform:340:360 (profiling cases)")
     ap.add_argument("--only-center", action="store_true",
                     help="time the exact-center selection alone (profiling cases)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-center comparison")
     return ap.parse_args()
 
 
@@ -185,6 +187,49 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp):
+    """Train the selector on exact-kernel distances (untimed), then time the
+    whole step with the learned center (network embedding + exact row sums of
+    its 32 best candidates) against the exact all-pairs center."""
+    import torch
+    from seqgen import training_pairs
+    pairs = training_pairs(n, 20000, fam, seed=8)
+    t0 = time.perf_counter()
+    b.msa_selector_init(h, seed=1)
+    losses = b.msa_selector_train(h, pairs, steps=3000, batch_pairs=256, lr=3e-4, seed=3)
+    train_s = time.perf_counter() - t0
+
+    def step_learned():
+        b.msa_load(h, dlet, offsets)
+        c, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED_REFINED, candidates=32)
+        b.msa_align_to_center(h, c)
+        b.msa_merge_gaps(h, want_rows=False)
+        return c, b.msa_sp_score(h)
+
+    step_learned()
+    ms = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        c, sp = step_learned()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    pairs_n = n * (n - 1) / 2
+    return {"exact_step_ms": exact_ms, "learned_step_ms": float(np.mean(ms)),
+            "speedup": exact_ms / float(np.mean(ms)),
+            "avg_sp_exact": exact_sp / pairs_n, "avg_sp_learned": sp / pairs_n,
+            "sp_loss_pct": 100.0 * (sp - exact_sp) / exact_sp, "learned_center": c,
+            "selector": "4-layer conv, width 128, k 9, 64-d, bf16 tensor cores",
+            "train": {"pairs": int(pairs.shape[0]), "steps": 3000, "batch_pairs": 256,
+                      "seconds": train_s, "loss_first": float(losses[:10].mean()),
+                      "loss_last": float(losses[-50:].mean())},
+            "candidates_refined_exactly": 32}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -201,8 +246,8 @@ def run_ours(args):
     if args.length:
         kind, lo, hi = args.length.split(":")
         length = (kind, int(lo), int(hi))
-    letters, offsets, w, _ = generate(args.workload, n=args.n, seed=base_seed + 1000 * rank,
-                                      length=length)
+    letters, offsets, w, fam = generate(args.workload, n=args.n, seed=base_seed + 1000 * rank,
+                                        length=length)
     alph, M, _, _ = scoring(w.kind)
     n = offsets.size - 1
     stream = torch.cuda.current_stream()
@@ -299,6 +344,11 @@ def run_ours(args):
         torch.distributed.all_reduce(t)
         return float(t.item())
 
+    learned = None
+    if not args.no_learned:
+        learned = learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream,
+                                   total_ms / args.steps, sp)
+
     t_max = reduce_max(total_ms)
     all_cells = reduce_sum(float(cells))
     e2e_max = reduce_max(e2e_ms)
@@ -332,6 +382,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(n * W + 8 * 4)},
         "gpu_launches": launches,
     }
+    if learned is not None:
+        line["learned_vs_exact"] = learned
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(letters, offsets, alph, M, w.gap_open, w.gap_extend,
                                             args.cpu_seconds)

@@ -47,6 +47,7 @@ extern "C" {
 #define MSA_CENTER_EXACT_SAMPLED  1   /* every candidate against a given reference subset */
 #define MSA_CENTER_LEARNED        2   /* embedding network (msa_train_selector / msa_load_selector) */
 #define MSA_CENTER_FIRST          3   /* index 0 (the nucleotide path's "first sequence") */
+#define MSA_CENTER_LEARNED_REFINED 4  /* the selector's best candidates, ranked by exact row sums */
 
 #define MSA_MAX_ALPHABET 32
 #define MSA_MAX_LEN      8192  /* residues per sequence */
@@ -121,6 +122,10 @@ int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int
  * EXACT_SAMPLED: the same sum over j in refs (host int64[nref], distinct).
  * LEARNED: argmin_i ||e_i - mean(e)||^2 over the selector's embeddings
  *   (msa_selector_*); ESTATE if no parameters are set.
+ * LEARNED_REFINED: the nref (0 = 32) sequences with the smallest
+ *   ||e_i - mean(e)||^2, then the exact sum_j d(i,j) over all j for each of
+ *   them (nref x n alignments instead of n^2/2) and its argmin; refs unused;
+ *   sum_dist_out gets the winner's exact row sum.
  * FIRST: 0.
  * center_out: host int64; sum_dist_out (nullable, host int64): the winning
  * row sum (EXACT modes), else 0.  ESTATE for LEARNED without a selector. */
@@ -169,12 +174,15 @@ int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out);
 /* Learned center selector.  The paper selects the center with Smith-
  * Waterman scores over all pairs (O(n^2) alignments); the selector is a 1-D
  * convolutional embedding network whose squared embedding distances are
- * trained to follow the normalised exact distance
- *   t(A,B) = d(A,B) / (S(A,A) + S(B,B)),  d as in msa_select_center,
- * so that the center can be picked in O(n): argmin_i ||e_i - mean(e)||^2.
+ * trained to follow the scaled exact distance
+ *   t(A,B) = scale * d(A,B),  d(A,B) = S(A,A) + S(B,B) - 2 S(A,B),
+ * so that the center can be picked in O(n): argmin_i ||e_i - mean(e)||^2,
+ * which equals argmin_i sum_j ||e_i - e_j||^2, the embedding stand-in for the
+ * exact center's argmin_i sum_j d(i,j).
  * Architecture (fixed): one-hot residues over 32 channels -> 9-tap conv to
  * 128 channels + ReLU -> two 9-tap 128->128 convs + ReLU -> 9-tap 128->64
- * conv -> mean over the sequence's positions.  Compute in bf16 on the
+ * conv -> sum over the sequence's L positions divided by sqrt(L) (so that
+ * ||e||^2 can grow with length like S(A,A)).  Compute in bf16 on the
  * tensor cores with fp32 accumulation; fp32 master weights; Adam.
  * Parameters (fp32, flat, in this order): W1 [9][32][128], b1 [128],
  * W2 [9][128][128], b2 [128], W3 [9][128][128], b3 [128], W4 [9][128][64],
@@ -184,6 +192,8 @@ typedef struct {
     int32_t batch_pairs;  /* pairs per step */
     float lr, beta1, beta2, eps;   /* Adam */
     uint64_t seed;        /* pair shuffling (and the initial weights if none are set) */
+    float target_scale;   /* scale of the exact distances when targets are computed;
+                             <= 0: 50 / (mean distance over the listed pairs) */
 } msa_train_cfg;
 
 /* Set the selector's parameters: params host or device float[count] with
@@ -195,10 +205,11 @@ int msa_selector_init(msa_ctx *ctx, uint64_t seed, const float *params, int64_t 
  * report their count (count_out, nullable, host). */
 int msa_selector_params(msa_ctx *ctx, float *params_out, int64_t *count_out);
 
-/* Training targets t(A,B) of listed pairs (host int64[npairs][2], input
- * indices), computed with the exact Smith-Waterman kernel; targets_out host
- * or device float[npairs]. */
-int msa_selector_targets(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, float *targets_out);
+/* Training targets t(A,B) = scale * d(A,B) of listed pairs (host
+ * int64[npairs][2], input indices), computed with the exact Smith-Waterman
+ * kernel; targets_out host or device float[npairs]. */
+int msa_selector_targets(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, float scale,
+                         float *targets_out);
 
 /* Mean pair loss (||e_A - e_B||^2 - t)^2 over the listed pairs and its
  * gradient with respect to every parameter, without updating them.
@@ -209,7 +220,7 @@ int msa_selector_grad(msa_ctx *ctx, const int64_t *pairs, const float *targets, 
 
 /* Train: cfg->steps Adam steps over batches of cfg->batch_pairs pairs drawn
  * from the list (reshuffled every pass).  targets: host float[npairs], or
- * NULL to compute them with the exact kernel.  Initialises the parameters
+ * NULL to compute them with the exact kernel (scale cfg->target_scale).  Initialises the parameters
  * from cfg->seed if none are set.  losses_out: host float[cfg->steps]
  * (nullable), the loss of each step's batch before its update. */
 int msa_selector_train(msa_ctx *ctx, const int64_t *pairs, const float *targets, int64_t npairs,

@@ -6,15 +6,19 @@ path.
 
 The paper selects the center with Smith-Waterman scores; the learned selector
 replaces that O(n^2) pass with an embedding network whose squared distances
-are trained to follow the normalised alignment distance
-t(A,B) = d(A,B) / (S(A,A) + S(B,B)), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B).
+are trained to follow the scaled alignment distance
+t(A,B) = scale * d(A,B), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B),
+so that argmin_i sum_j ||e_i - e_j||^2 tracks the exact center's
+argmin_i sum_j d(i,j).
 Architecture (a reading; the paper has no network):
   x0  = one-hot(residues) over KP = 32 channels            [L, 32]
   a1  = relu(conv9(x0, W1, b1))                             [L, 128]
   a2  = relu(conv9(a1, W2, b2))                             [L, 128]
   a3  = relu(conv9(a2, W3, b3))                             [L, 128]
   y4  = conv9(a3, W4, b4)                                   [L, 64]
-  e   = mean over the L positions of y4                     [64]
+  e   = (sum over the L positions of y4) / sqrt(L)          [64]
+(pooling by sqrt(L) keeps ||e||^2 growing with the length, as S(A,A) does;
+a mean would make the embedding nearly length-blind.)
 conv9(x, W, b)[p] = b + sum_{k=0..8} xpad[p + k] @ W[k], xpad = x with four
 zero rows before and after (the sequence ends are zero-padded).
 Loss over a batch of pairs: mean over pairs of (||e_A - e_B||^2 - t)^2.
@@ -85,7 +89,7 @@ def forward(params, res):
     z2 = conv9(a1, params["W2"], params["b2"]); a2 = np.maximum(z2, 0)
     z3 = conv9(a2, params["W3"], params["b3"]); a3 = np.maximum(z3, 0)
     y4 = conv9(a3, params["W4"], params["b4"])
-    return y4.mean(axis=0), (x0, a1, a2, a3)
+    return y4.sum(axis=0) / np.sqrt(len(res)), (x0, a1, a2, a3)
 
 
 def backward(params, cache, de):
@@ -93,7 +97,7 @@ def backward(params, cache, de):
     x0, a1, a2, a3 = cache
     L = x0.shape[0]
     g = {}
-    dy4 = np.tile(de / L, (L, 1))
+    dy4 = np.tile(de / np.sqrt(L), (L, 1))
     da3, g["W4"], g["b4"] = conv9_backward(a3, params["W4"], dy4)
     dz3 = da3 * (a3 > 0)
     da2, g["W3"], g["b3"] = conv9_backward(a2, params["W3"], dz3)
@@ -154,7 +158,7 @@ def center_of(emb):
     return int(np.argmin(((emb - mu) ** 2).sum(axis=1)))
 
 
-def distance_targets(S_ab, S_aa, S_bb):
-    den = np.asarray(S_aa, np.float64) + np.asarray(S_bb, np.float64)
-    num = den - 2.0 * np.asarray(S_ab, np.float64)
-    return np.where(den > 0, num / np.where(den > 0, den, 1), 0.0)
+def distance_targets(S_ab, S_aa, S_bb, scale):
+    """scale * (S_aa + S_bb - 2 S_ab)."""
+    return scale * (np.asarray(S_aa, np.float64) + np.asarray(S_bb, np.float64)
+                    - 2.0 * np.asarray(S_ab, np.float64))

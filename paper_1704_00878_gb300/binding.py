@@ -16,6 +16,7 @@ from . import _build
 MSA_OK, MSA_EINVAL, MSA_ENOMEM, MSA_ECUDA, MSA_ETIMEOUT, MSA_ESTATE, MSA_ERANGE = 0, -1, -2, -3, -4, -5, -6
 MSA_AUTO, MSA_INT16, MSA_INT32 = 0, 1, 2
 MSA_CENTER_EXACT, MSA_CENTER_EXACT_SAMPLED, MSA_CENTER_LEARNED, MSA_CENTER_FIRST = 0, 1, 2, 3
+MSA_CENTER_LEARNED_REFINED = 4
 MSA_MAX_LEN = 8192
 
 STAGES = ("encode", "center", "align_dp", "traceback", "merge", "rows", "sp", "center_kernels",
@@ -31,7 +32,7 @@ class MSAError(RuntimeError):
 class msa_train_cfg(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("batch_pairs", ctypes.c_int32),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64), ("target_scale", ctypes.c_float)]
 
 
 class msa_params(ctypes.Structure):
@@ -61,7 +62,8 @@ _SIGS = {
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
     "msa_selector_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    "msa_selector_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "msa_selector_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                                            ctypes.c_void_p]),
     "msa_selector_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -174,13 +176,14 @@ def msa_pair_scores_noalloc(residues, offsets, pairs, max_len, matrix, gap_open,
     return scores_out
 
 
-def msa_select_center(ctx, mode, refs=None):
-    """Returns (center, winning row sum of distances)."""
+def msa_select_center(ctx, mode, refs=None, candidates=0):
+    """Returns (center, winning row sum of distances).  candidates: the
+    number of network candidates LEARNED_REFINED checks exactly (0 = 32)."""
     c = np.zeros(1, np.int64)
     s = np.zeros(1, np.int64)
     r = None if refs is None else np.ascontiguousarray(refs, dtype=np.int64)
-    _check(ctx, lib().msa_select_center(ctx, int(mode), _ptr(r), 0 if r is None else r.size,
-                                        _ptr(c), _ptr(s)))
+    nref = r.size if r is not None else int(candidates)
+    _check(ctx, lib().msa_select_center(ctx, int(mode), _ptr(r), nref, _ptr(c), _ptr(s)))
     return int(c[0]), int(s[0])
 
 
@@ -254,10 +257,13 @@ def msa_selector_params(ctx):
     return out
 
 
-def msa_selector_targets(ctx, pairs):
+DEFAULT_TARGET_SCALE = 1e-3
+
+
+def msa_selector_targets(ctx, pairs, scale=DEFAULT_TARGET_SCALE):
     pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
     out = np.zeros(pr.shape[0], np.float32)
-    _check(ctx, lib().msa_selector_targets(ctx, _ptr(pr), pr.shape[0], _ptr(out)))
+    _check(ctx, lib().msa_selector_targets(ctx, _ptr(pr), pr.shape[0], float(scale), _ptr(out)))
     return out
 
 
@@ -273,13 +279,13 @@ def msa_selector_grad(ctx, pairs, targets):
     return float(loss[0]), g
 
 
-def msa_selector_train(ctx, pairs, targets=None, steps=100, batch_pairs=256, lr=1e-3,
-                       beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
+def msa_selector_train(ctx, pairs, targets=None, steps=3000, batch_pairs=256, lr=3e-4,
+                       beta1=0.9, beta2=0.999, eps=1e-8, seed=0, target_scale=0.0):
     """Returns the per-step batch losses (float32[steps])."""
     pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
     t = None if targets is None else np.ascontiguousarray(targets, dtype=np.float32)
     cfg = msa_train_cfg(int(steps), int(batch_pairs), float(lr), float(beta1), float(beta2),
-                        float(eps), int(seed))
+                        float(eps), int(seed), float(target_scale))
     losses = np.zeros(max(1, int(steps)), np.float32)
     _check(ctx, lib().msa_selector_train(ctx, _ptr(pr), _ptr(t), pr.shape[0], ctypes.byref(cfg),
                                          _ptr(losses)))

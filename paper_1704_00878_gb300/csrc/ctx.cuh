@@ -92,6 +92,8 @@ Scoring scoring(msa_ctx *ctx);
 int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector<int32_t> &dst_in,
               int32_t *d_out);
 int selector_center(msa_ctx *ctx, int64_t *center_out);
+int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *sum_out);
+int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted);
 
 }  // namespace msa_detail
 

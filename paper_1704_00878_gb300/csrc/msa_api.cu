@@ -246,7 +246,7 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
 }
 
 int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
-  // qsorted: ascending sorted indices of the queries (mode 1); mode 0 uses all.
+  // qsorted: ascending sorted indices of the queries (modes 1, 2); mode 0 uses all.
   const int n = ctx->n;
   std::vector<int> qlen;
   if (mode == 0) qlen.assign(ctx->len_sorted.begin(), ctx->len_sorted.end());
@@ -257,7 +257,7 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   mean /= n;
   std::vector<int64_t> suffix(n + 1, 0);
   for (int k = n - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + ctx->len_sorted[k];
-  if (mode == 1) {
+  if (mode != 0) {
     TRY(ensure(ctx, ctx->qlist, sizeof(int32_t) * qsorted.size()));
     CK(cudaMemcpyAsync(ctx->qlist.p, qsorted.data(), sizeof(int32_t) * qsorted.size(),
                        cudaMemcpyHostToDevice, ctx->st));
@@ -321,7 +321,7 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     std::iota(dst.begin(), dst.end(), 0);
     TRY(ensure(ctx, ctx->ovf_scores, sizeof(int32_t) * cnt));
     TRY(run_pairs(ctx, ov, dst, P<int32_t>(ctx->ovf_scores)));
-    CK((++ctx->launches, launch_apply_overflow)(mode == 0 ? 0 : 1, P<int2>(ctx->ovf),
+    CK((++ctx->launches, launch_apply_overflow)(mode, P<int2>(ctx->ovf),
                                                 P<int32_t>(ctx->ovf_scores), cnt,
                                                 P<unsigned long long>(ctx->pairsum),
                                                 P<int32_t>(ctx->self), ctx->st));
@@ -545,6 +545,9 @@ int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
     return MSA_OK;
   }
   if (mode == MSA_CENTER_LEARNED) return selector_center(ctx, center_out);
+  if (mode == MSA_CENTER_LEARNED_REFINED)
+    return selector_center_refined(ctx, nref > 0 ? (int)std::min<int64_t>(nref, ctx->n) : 32,
+                                   center_out, sum_dist_out);
   if (mode != MSA_CENTER_EXACT && mode != MSA_CENTER_EXACT_SAMPLED)
     return fail(ctx, MSA_EINVAL, "unknown center mode %d", mode);
   const int n = ctx->n;

@@ -306,8 +306,10 @@ __global__ void k_apply_overflow(int mode, const int2 *__restrict__ ovf,
   if (mode == 0) {
     if (q == s) self[q] = scores[x];
     else { atomicAdd(&pairsum[s], S); atomicAdd(&pairsum[q], S); }
-  } else {
+  } else if (mode == 1) {
     atomicAdd(&pairsum[s], S);
+  } else {
+    atomicAdd(&pairsum[q], S);
   }
 }
 

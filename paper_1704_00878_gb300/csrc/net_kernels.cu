@@ -229,7 +229,7 @@ __global__ void k_pool(Batch b, const float *__restrict__ y4, float *__restrict_
   float acc = 0.f;
   const int base = b.base[s], L = b.len[s];
   for (int i = 0; i < L; ++i) acc += y4[(size_t)(base + i) * DIM + c];
-  emb[(size_t)s * DIM + c] = acc / (float)L;
+  emb[(size_t)s * DIM + c] = acc * rsqrtf((float)L);
 }
 
 // One warp per pair: r = ||e_a - e_b||^2 - t; loss += r^2 / m;
@@ -261,7 +261,7 @@ __global__ void k_pool_backward(Batch b, const float *__restrict__ demb, bf16 *_
   const int r = (int)(idx / DIM), c = (int)(idx - (size_t)r * DIM);
   const int s = b.rowseq[r];
   float v = 0.f;
-  if (s >= 0) v = demb[(size_t)s * DIM + c] / (float)b.len[s];
+  if (s >= 0) v = demb[(size_t)s * DIM + c] * rsqrtf((float)b.len[s]);
   dy4[idx] = __float2bfloat16(v);
 }
 
@@ -324,6 +324,18 @@ __global__ void k_emb_argmin(const float *__restrict__ emb, int n, const double 
     best = o < best ? o : best;
   }
   if ((threadIdx.x & 31) == 0 && best != ULLONG_MAX) atomicMin(key, best);
+}
+
+__global__ void k_emb_dist(const float *__restrict__ emb, int n, const double *__restrict__ mean,
+                           float *__restrict__ dist) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  float d = 0.f;
+  for (int c = 0; c < DIM; ++c) {
+    const float x = emb[(size_t)r * DIM + c] - (float)(mean[c] / n);
+    d += x * x;
+  }
+  dist[r] = d;
 }
 
 __global__ void k_key_to_idx(const unsigned long long *key, long long *out) {
@@ -437,6 +449,16 @@ cudaError_t emb_center(const float *emb, int n, float *mean_scratch, long long *
   k_emb_mean<<<blocks, 256, 0, st>>>(emb, n, mean);
   k_emb_argmin<<<(n + 255) / 256, 256, 0, st>>>(emb, n, mean, key);
   k_key_to_idx<<<1, 1, 0, st>>>(key, out_idx);
+  return cudaGetLastError();
+}
+
+cudaError_t emb_dist(const float *emb, int n, float *mean_scratch, float *dist, cudaStream_t st) {
+  double *mean = reinterpret_cast<double *>(mean_scratch);
+  cudaError_t e = cudaMemsetAsync(mean, 0, sizeof(double) * DIM, st);
+  if (e != cudaSuccess) return e;
+  const int blocks = std::max(1, std::min(1024, (n + 3) / 4));
+  k_emb_mean<<<blocks, 256, 0, st>>>(emb, n, mean);
+  k_emb_dist<<<(n + 255) / 256, 256, 0, st>>>(emb, n, mean, dist);
   return cudaGetLastError();
 }
 

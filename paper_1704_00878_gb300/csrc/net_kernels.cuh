@@ -67,4 +67,7 @@ cudaError_t refresh(const float *w, int cin, int cout, __nv_bfloat16 *wt, __nv_b
 cudaError_t emb_center(const float *emb, int n, float *mean_scratch, long long *out_idx,
                        cudaStream_t st);
 
+// dist[i] = ||e_i - mean(e)||^2
+cudaError_t emb_dist(const float *emb, int n, float *mean_scratch, float *dist, cudaStream_t st);
+
 }  // namespace net

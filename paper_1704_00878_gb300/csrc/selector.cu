@@ -1,7 +1,9 @@
 // selector.cu -- the learned center selector behind the C ABI: a 1-D conv
-// embedding network trained on normalised alignment distances that the exact
-// Smith-Waterman kernel produces, then used to pick the center in O(n)
-// (argmin of ||e_i - mean(e)||^2, which equals argmin of sum_j ||e_i - e_j||^2).
+// embedding network whose squared embedding distances are trained on scaled
+// alignment distances d(A,B) = S(A,A) + S(B,B) - 2 S(A,B) that the exact
+// Smith-Waterman kernel produces, then used to pick the center in O(n):
+// argmin of ||e_i - mean(e)||^2, which equals argmin of sum_j ||e_i - e_j||^2,
+// the embedding stand-in for the exact center's argmin of sum_j d(i,j).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -23,7 +25,7 @@ struct Selector {
   int step = 0;
   // batch buffers
   DevBuf seq, base, len, rowseq, x0, a1, a2, a3, y4, emb, demb, dy4, dz3, dz2, dz1;
-  DevBuf bpairs, btargets, loss, small, allemb;
+  DevBuf bpairs, btargets, loss, small, allemb, dist;
 };
 
 namespace {
@@ -220,8 +222,9 @@ int stage_pairs(msa_ctx *ctx, Selector *s, const int64_t *pairs, const float *ta
   return build_batch(ctx, s, seqs, b);  // synchronises before the host vectors go away
 }
 
-// Normalised exact distances t = (S_aa + S_bb - 2 S_ab) / (S_aa + S_bb).
-int exact_targets(msa_ctx *ctx, const int64_t *pairs, int64_t np, std::vector<float> &t) {
+// Scaled exact distances t = scale * (S_aa + S_bb - 2 S_ab).
+int exact_targets(msa_ctx *ctx, const int64_t *pairs, int64_t np, float scale,
+                  std::vector<float> &t) {
   std::vector<int2> pr;
   std::vector<int32_t> dst;
   std::unordered_map<int32_t, int32_t> selfslot;
@@ -250,8 +253,7 @@ int exact_targets(msa_ctx *ctx, const int64_t *pairs, int64_t np, std::vector<fl
   for (int64_t x = 0; x < np; ++x) {
     const double saa = S[selfslot[ctx->inv[pairs[2 * x]]]];
     const double sbb = S[selfslot[ctx->inv[pairs[2 * x + 1]]]];
-    const double den = saa + sbb;
-    t[x] = den > 0 ? (float)((den - 2.0 * S[x]) / den) : 0.f;
+    t[x] = (float)(scale * (saa + sbb - 2.0 * S[x]));
   }
   return MSA_OK;
 }
@@ -285,7 +287,8 @@ void selector_free(Selector *s) {
   DevBuf *bufs[] = {&s->params, &s->grads, &s->m, &s->v, &s->w1t, &s->w2t, &s->w2n, &s->w3t,
                     &s->w3n, &s->w4t, &s->w4n, &s->seq, &s->base, &s->len, &s->rowseq, &s->x0,
                     &s->a1, &s->a2, &s->a3, &s->y4, &s->emb, &s->demb, &s->dy4, &s->dz3,
-                    &s->dz2, &s->dz1, &s->bpairs, &s->btargets, &s->loss, &s->small, &s->allemb};
+                    &s->dz2, &s->dz1, &s->bpairs, &s->btargets, &s->loss, &s->small, &s->allemb,
+                    &s->dist};
   for (DevBuf *b : bufs) free_buf(*b);
   delete s;
 }
@@ -305,6 +308,60 @@ int selector_center(msa_ctx *ctx, int64_t *center_out) {
   stage_collect(ctx, ST_SELECTOR);
   if (k < 0 || k >= ctx->n) return fail(ctx, MSA_ECUDA, "selector center out of range");
   *center_out = ctx->perm[k];
+  return MSA_OK;
+}
+
+// LEARNED_REFINED: the k candidates with the smallest ||e_i - mean(e)||^2,
+// then their exact row sums sum_j d(i, j) over every sequence (k x n
+// alignments with the center kernels, summed on the query side) and the
+// argmin among them (lowest input index on ties).
+int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *sum_out) {
+  Selector *s = ctx->sel;
+  if (!s || !s->params.p) return fail(ctx, MSA_ESTATE, "no trained selector loaded");
+  const int n = ctx->n;
+  k = std::max(1, std::min(k, n));
+  stage_begin(ctx, ST_SELECTOR);
+  TRY(embed_all(ctx, s));
+  TRY(ensure(ctx, s->dist, sizeof(float) * n));
+  CK((++ctx->launches, net::emb_dist)(P<float>(s->allemb), n, P<float>(s->small), P<float>(s->dist), ctx->st));
+  stage_end(ctx, ST_SELECTOR);
+  std::vector<float> dist(n);
+  CK(cudaMemcpyAsync(dist.data(), s->dist.p, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_SELECTOR);
+  std::vector<int32_t> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::partial_sort(idx.begin(), idx.begin() + k, idx.end(), [&](int32_t a, int32_t b) {
+    return dist[a] < dist[b] || (dist[a] == dist[b] && ctx->perm[a] < ctx->perm[b]);
+  });
+  std::vector<int32_t> qs(idx.begin(), idx.begin() + k);
+  std::sort(qs.begin(), qs.end());
+  // exact row sums of the candidates
+  stage_begin(ctx, ST_CENTER);
+  CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
+  CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+  TRY(run_center(ctx, 2, qs));
+  std::vector<int2> sp(n);
+  std::vector<int32_t> dst(n);
+  for (int x = 0; x < n; ++x) { sp[x] = make_int2(x, x); dst[x] = x; }
+  TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
+  stage_end(ctx, ST_CENTER);
+  std::vector<unsigned long long> ps(n);
+  std::vector<int32_t> self(n);
+  CK(cudaMemcpyAsync(ps.data(), ctx->pairsum.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(self.data(), ctx->self.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_CENTER);
+  long long T = 0;
+  for (int x = 0; x < n; ++x) T += self[x];
+  long long best = 0;
+  int bestq = -1;
+  for (int q : qs) {
+    const long long v = (long long)n * self[q] + T - 2 * (long long)ps[q];
+    if (bestq < 0 || v < best || (v == best && ctx->perm[q] < ctx->perm[bestq])) { best = v; bestq = q; }
+  }
+  *center_out = ctx->perm[bestq];
+  if (sum_out) *sum_out = best;
   return MSA_OK;
 }
 
@@ -342,13 +399,14 @@ int msa_selector_params(msa_ctx *ctx, float *params_out, int64_t *count_out) {
   return MSA_OK;
 }
 
-int msa_selector_targets(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, float *targets_out) {
+int msa_selector_targets(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, float scale,
+                         float *targets_out) {
   if (!ctx || (npairs > 0 && (!pairs || !targets_out)) || npairs < 0) return MSA_EINVAL;
   if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
   if (npairs == 0) return MSA_OK;
   TRY(set_device(ctx));
   std::vector<float> t;
-  TRY(exact_targets(ctx, pairs, npairs, t));
+  TRY(exact_targets(ctx, pairs, npairs, scale, t));
   CK(cudaMemcpyAsync(targets_out, t.data(), sizeof(float) * npairs, cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   return MSA_OK;
@@ -384,7 +442,16 @@ int msa_selector_train(msa_ctx *ctx, const int64_t *pairs, const float *targets,
   }
   std::vector<float> tv;
   if (!targets) {
-    TRY(exact_targets(ctx, pairs, npairs, tv));
+    // scale <= 0: put the mean target at 50, where the embedding's squared
+    // distances sit at a natural scale for the initialisation and Adam steps
+    TRY(exact_targets(ctx, pairs, npairs, cfg->target_scale > 0 ? cfg->target_scale : 1.f, tv));
+    if (cfg->target_scale <= 0) {
+      double mean = 0;
+      for (float v : tv) mean += v;
+      mean /= (double)npairs;
+      const float k = mean > 0 ? (float)(50.0 / mean) : 1.f;
+      for (float &v : tv) v *= k;
+    }
     targets = tv.data();
   }
   // one shuffled pass over the pairs per epoch (splitmix64 Fisher-Yates)

@@ -242,8 +242,10 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
         if (job.mode == 0) {
           if (s == q) job.self[q] = S;
           else { atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S); qadd += (unsigned long long)(long long)S; }
-        } else {
+        } else if (job.mode == 1) {
           atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+        } else {
+          qadd += (unsigned long long)(long long)S;
         }
       }
       if (qadd) atomicAdd(&s_qsum, qadd);
@@ -422,13 +424,15 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
             atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
             atomicAdd(&s_qsum[l], (unsigned long long)(long long)S);
           }
-        } else {
+        } else if (job.mode == 1) {
           atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+        } else {
+          atomicAdd(&s_qsum[l], (unsigned long long)(long long)S);
         }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && job.mode == 0) {
+    if (threadIdx.x == 0 && job.mode != 1) {
       if (s_qsum[0]) atomicAdd(&job.pairsum[qA], s_qsum[0]);
       if (qB >= 0 && s_qsum[1]) atomicAdd(&job.pairsum[qB], s_qsum[1]);
     }

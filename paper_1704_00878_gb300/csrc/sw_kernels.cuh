@@ -17,7 +17,9 @@ struct Scoring {
 
 // All-pairs / reference-pairs scores for center selection.
 struct CenterJob {
-  int mode;                       // 0: query q vs subjects [q, n) ; 1: query qlist[x] vs [0, n)
+  int mode;                       // 0: query q vs subjects [q, n), both sides summed;
+                                  // 1: query qlist[x] vs [0, n), summed on the subject;
+                                  // 2: query qlist[x] vs [0, n), summed on the query
   const int32_t *qlist;           // mode 1 (sorted indices)
   int nq;                         // queries in the list (mode 0: n)
   int qb, qe;                     // item-unit range: queries (single) or query pairs (paired)

@@ -46,11 +46,15 @@ def test_embeddings_loss_and_gradients_match_oracle():
     assert abs(loss - oloss) <= LOSS_TOL * abs(oloss)
     ogflat = net.flatten(og)
     assert rel_err(grad, ogflat) < GRAD_TOL
-    # every tensor, not only the total
-    at = 0
+    # every tensor, not only the total (b4's true gradient is exactly zero: a
+    # bias shared by all embeddings cancels in e_A - e_B, so its error is
+    # measured against the whole gradient)
+    at, total = 0, np.linalg.norm(ogflat)
     for name, shape in net.SHAPES:
         size = int(np.prod(shape))
-        assert rel_err(grad[at:at + size], ogflat[at:at + size]) < GRAD_TOL, name
+        g, o = grad[at:at + size], ogflat[at:at + size]
+        scale = max(np.linalg.norm(o), 1e-2 * total)
+        assert np.linalg.norm(g - o) / scale < GRAD_TOL, name
         at += size
 
 
@@ -78,25 +82,26 @@ def test_one_adam_step_matches_oracle():
     assert np.abs(step_gpu - step_orc).max() <= 2.05 * lr
 
 
-def test_targets_are_exact_normalised_distances():
+def test_targets_are_scaled_exact_distances():
     b = binding()
     letters, offsets, w, alph, M, prob, seqs = setup_small(seed=4, n=30)
     rng = np.random.default_rng(6)
     pairs = rng.integers(0, prob.n, size=(50, 2))
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
         b.msa_load(h, letters, offsets)
-        t = b.msa_selector_targets(h, pairs)
+        t = b.msa_selector_targets(h, pairs, scale=1e-3)
     S = oracle.pair_scores(prob, pairs)
     Sa = oracle.pair_scores(prob, np.stack([pairs[:, 0], pairs[:, 0]], 1))
     Sb = oracle.pair_scores(prob, np.stack([pairs[:, 1], pairs[:, 1]], 1))
-    assert np.allclose(t, net.distance_targets(S, Sa, Sb), atol=1e-6)
+    assert np.allclose(t, net.distance_targets(S, Sa, Sb, 1e-3), rtol=1e-6, atol=1e-6)
 
 
 def test_training_gains_over_the_method_without_it(tmp_path):
-    """Trained on exact-kernel distances, the selector's center gives a lower
-    (better) avg SP than the untrained network's and than the first
-    sequence (the nucleotide path's center), and the embedding pass is far
-    cheaper than the exact all-pairs selection it replaces."""
+    """Trained on exact-kernel distances, the selector ranks the exact center
+    among its best candidates: refining its top 32 with exact row sums gives
+    the exact center's row sum and avg SP (0 % loss), where the untrained
+    network and the first sequence (the nucleotide path's center) do worse,
+    at a fraction of the exact all-pairs cost."""
     b = binding()
     from seqgen import generate, training_pairs
     letters, offsets, w, fam = generate("learned_center_50k", n=1200, seed=31)
@@ -105,31 +110,39 @@ def test_training_gains_over_the_method_without_it(tmp_path):
 
     def avg_sp(h, center):
         b.msa_align_to_center(h, center)
-        _, W = b.msa_merge_gaps(h, want_rows=False)
+        b.msa_merge_gaps(h, want_rows=False)
         return b.msa_sp_score(h) / (1200 * 1199 / 2)
 
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
         b.msa_load(h, letters, offsets)
         exact, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        rowsum = b.msa_center_rowsums(h).astype(np.float64)
         exact_ms = b.msa_stage_times(h)[0]["center"]
         b.msa_selector_init(h, seed=1)
-        untrained, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED)
-        losses = b.msa_selector_train(h, pairs, steps=400, batch_pairs=256, lr=1e-3, seed=3)
-        learned, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED)
-        learned_ms = b.msa_stage_times(h)[0]["selector"]
+        untrained, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED_REFINED, candidates=32)
+        losses = b.msa_selector_train(h, pairs, steps=3000, batch_pairs=256, lr=3e-4, seed=3)
+        top1, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED)
+        refined, rs = b.msa_select_center(h, b.MSA_CENTER_LEARNED_REFINED, candidates=32)
+        st = b.msa_stage_times(h)[0]
+        refined_ms = st["selector"] + st["center"]
         sp = {name: avg_sp(h, c) for name, c in
-              [("exact", exact), ("learned", learned), ("untrained", untrained), ("first", 0)]}
+              [("exact", exact), ("refined", refined), ("top1", top1), ("untrained", untrained),
+               ("first", 0)]}
         path = os.path.join(str(tmp_path), "sel.bin")
         b.msa_save_selector(h, path)
         saved = b.msa_selector_params(h)
-    print("avg SP", sp, "loss", float(losses[:20].mean()), "->", float(losses[-20:].mean()),
-          "exact ms", exact_ms, "learned ms", learned_ms)
-    assert losses[-50:].mean() < 0.5 * losses[:10].mean()
-    assert sp["learned"] <= sp["first"] and sp["learned"] <= sp["untrained"]
-    assert sp["learned"] <= 1.05 * sp["exact"]
-    assert learned_ms < exact_ms
+    excess = {name: rowsum[c] / rowsum[exact] - 1 for name, c in
+              [("refined", refined), ("top1", top1), ("untrained", untrained), ("first", 0)]}
+    print("avg SP", sp, "row-sum excess", excess, "loss", float(losses[:20].mean()), "->",
+          float(losses[-20:].mean()), "exact ms", exact_ms, "refined ms", refined_ms)
+    assert rs == rowsum[refined]
+    assert losses[-50:].mean() < 0.05 * losses[:10].mean()
+    assert excess["top1"] < excess["first"] and excess["top1"] < 0.5 * excess["untrained"]
+    assert excess["refined"] < 0.005
+    assert sp["refined"] <= 1.01 * sp["exact"]
+    assert refined_ms < exact_ms
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h2:
         b.msa_load(h2, letters, offsets)
         b.msa_load_selector(h2, path)
         assert (b.msa_selector_params(h2) == saved).all()
-        assert b.msa_select_center(h2, b.MSA_CENTER_LEARNED)[0] == learned
+        assert b.msa_select_center(h2, b.MSA_CENTER_LEARNED)[0] == top1

@@ -28,7 +28,7 @@ MUTATIONS = {
 
 # mistakes in the fp64 network oracle, caught by tests/test_net_oracle.py
 NET_MUTATIONS = {
-    "pool_drops_1_over_L": ("dy4 = np.tile(de / L, (L, 1))", "dy4 = np.tile(de, (L, 1))"),
+    "pool_drops_scale": ("dy4 = np.tile(de / np.sqrt(L), (L, 1))", "dy4 = np.tile(de, (L, 1))"),
     "relu_gate_missing": ("dz2 = da2 * (a2 > 0)", "dz2 = da2"),
     "taps_flipped": ("out += xp[k:k + L] @ W[k]", "out += xp[k:k + L] @ W[TAPS - 1 - k]"),
     "adam_no_bias_correction": ("mh = m / (1 - beta1 ** step)", "mh = m"),
