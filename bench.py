@@ -190,18 +190,18 @@ def run_reference(args):
 def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp):
     """Train the selector on exact-kernel distances (untimed), then time the
     whole step with the learned center (network embedding + exact row sums of
-    its 32 best candidates) against the exact all-pairs center."""
+    its 128 best candidates) against the exact all-pairs center."""
     import torch
     from seqgen import training_pairs
-    pairs = training_pairs(n, 20000, fam, seed=8)
+    pairs = training_pairs(n, 60000, fam, seed=8)
     t0 = time.perf_counter()
     b.msa_selector_init(h, seed=1)
-    losses = b.msa_selector_train(h, pairs, steps=3000, batch_pairs=256, lr=3e-4, seed=3)
+    losses = b.msa_selector_train(h, pairs, steps=6000, batch_pairs=256, lr=3e-4, seed=3)
     train_s = time.perf_counter() - t0
 
     def step_learned():
         b.msa_load(h, dlet, offsets)
-        c, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED_REFINED, candidates=32)
+        c, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED_REFINED, candidates=128)
         b.msa_align_to_center(h, c)
         b.msa_merge_gaps(h, want_rows=False)
         return c, b.msa_sp_score(h)
@@ -224,10 +224,10 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
             "avg_sp_exact": exact_sp / pairs_n, "avg_sp_learned": sp / pairs_n,
             "sp_loss_pct": 100.0 * (sp - exact_sp) / exact_sp, "learned_center": c,
             "selector": "4-layer conv, width 128, k 9, 64-d, bf16 tensor cores",
-            "train": {"pairs": int(pairs.shape[0]), "steps": 3000, "batch_pairs": 256,
+            "train": {"pairs": int(pairs.shape[0]), "steps": 6000, "batch_pairs": 256,
                       "seconds": train_s, "loss_first": float(losses[:10].mean()),
                       "loss_last": float(losses[-50:].mean())},
-            "candidates_refined_exactly": 32}
+            "candidates_refined_exactly": 128}
 
 
 def run_ours(args):
@@ -318,6 +318,10 @@ def run_ours(args):
         return
 
     rate, per_clk = b.msa_probe_int_rate(b.MSA_PROBE_VIADDMAX_S16X2)
+    b.msa_load(h, dlet, offsets)
+    t0 = time.perf_counter()
+    tune = b.msa_autotune(h)  # untimed: picks the center kernel variant per length bucket
+    tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize()
@@ -381,6 +385,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(letters.nbytes + offsets.nbytes),
                 "d2h_bytes_per_step": int(n * W + 8 * 4)},
         "gpu_launches": launches,
+        "autotune": {"seconds": tune_s, "buckets_timed": int((tune > 0).any(axis=1).sum()),
+                     "variants_timed": int((tune > 0).sum())},
     }
     if learned is not None:
         line["learned_vs_exact"] = learned

@@ -234,6 +234,17 @@ int msa_selector_embed(msa_ctx *ctx, float *emb_out);
 int msa_save_selector(msa_ctx *ctx, const char *path);
 int msa_load_selector(msa_ctx *ctx, const char *path);
 
+/* Autotuner: time every packed center-selection kernel variant (threads per
+ * query group x query rows per thread, paired or single query) on a sample
+ * of the loaded set per query-length bucket, and let later selections on
+ * this context pick, per bucket, the variant with the highest measured
+ * cells/s (instead of the built-in cost model).  Results do not depend on
+ * the variant.  rates_out (nullable, host double[buckets][variants], at most
+ * 21 x 16) and dims_out (nullable, host int32[2] = {buckets, variants}).
+ * Bucket edges: 1 48 80 112 144 176 208 256 320 384 448 512 640 768 896
+ * 1024 1280 1536 2048 3072 4096 8193. */
+int msa_autotune(msa_ctx *ctx, double *rates_out, int32_t *dims_out);
+
 /* Sizes of the current state: dims_out host int64[4] = {n, center (-1 if
  * none), Lc (center length, 0 if none), W (MSA width, 0 before a merge)}. */
 int msa_dims(msa_ctx *ctx, int64_t *dims_out);

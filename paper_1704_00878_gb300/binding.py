@@ -58,6 +58,7 @@ _SIGS = {
     "msa_merge_gaps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_sp_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
@@ -144,6 +145,15 @@ def msa_load(ctx, letters, offsets):
     """letters: uint8 ASCII (numpy, or torch host/CUDA); offsets: int64[n+1] host."""
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     _check(ctx, lib().msa_load(ctx, _ptr(letters), _ptr(off), off.size - 1))
+
+
+def msa_autotune(ctx):
+    """Measured cells/s per (length bucket, center variant): float64[buckets, variants]."""
+    rates = np.zeros((32, 32), np.float64)
+    dims = np.zeros(2, np.int32)
+    _check(ctx, lib().msa_autotune(ctx, _ptr(rates), _ptr(dims)))
+    nb, nv = int(dims[0]), int(dims[1])
+    return rates.ravel()[:nb * nv].reshape(nb, nv)
 
 
 def msa_dims(ctx):

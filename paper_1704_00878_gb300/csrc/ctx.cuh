@@ -75,6 +75,10 @@ struct msa_ctx {
   size_t codes_budget = (size_t)4 << 30;
 
   msa_detail::Selector *sel = nullptr;
+
+  // autotuner: measured cells/s of each center variant per query-length bucket
+  std::vector<int> tune_edges;                 // bucket b = [edges[b], edges[b+1])
+  std::vector<std::vector<double>> tune_rate;  // [bucket][variant], 0 = not measured
 };
 
 namespace msa_detail {

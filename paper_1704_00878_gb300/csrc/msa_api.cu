@@ -154,7 +154,29 @@ double variant_cost(int v, int Lq, int Ls_est) {
   return c;
 }
 
+bool variant_fits(msa_ctx *ctx, int v, int Lq) {
+  const CenterVariant &cv = kCenterVariants[v];
+  const int rows = cv.G * cv.R;
+  const int np = (Lq + rows - 1) / rows;
+  const int smem = center_smem_bytes(v, ctx->K, np * rows);
+  return !(cv.paired && smem > kMaxPairedProfile) && smem <= 200 * 1024;
+}
+
 int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
+  // measured rates (msa_autotune) take precedence over the cost model
+  if (packed && !ctx->tune_rate.empty()) {
+    for (size_t b = 0; b + 1 < ctx->tune_edges.size(); ++b) {
+      if (Lq < ctx->tune_edges[b] || Lq >= ctx->tune_edges[b + 1]) continue;
+      int best = -1;
+      double rate = 0;
+      for (int v = 0; v < kNumCenterVariants; ++v)
+        if (ctx->tune_rate[b][v] > rate && kCenterVariants[v].packed && variant_fits(ctx, v, Lq)) {
+          rate = ctx->tune_rate[b][v];
+          best = v;
+        }
+      if (best >= 0) return best;
+    }
+  }
   int best = -1;
   double best_cost = 1e300;
   for (int v = 0; v < kNumCenterVariants; ++v) {
@@ -188,9 +210,11 @@ struct CenterClass {
 };
 
 int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
-                 const std::vector<int> &qlen, float &center_ms) {
+                 const std::vector<int> &qlen, float &center_ms, int sub_off = 0, int sub_n = -1) {
   const CenterVariant &cv = kCenterVariants[cc.variant];
-  const int n = ctx->n, NG = kCenterThreads / cv.G;
+  const int NG = kCenterThreads / cv.G;
+  if (sub_n < 0) sub_n = ctx->n;
+  const int n = mode == 0 ? ctx->n : sub_n;
   std::vector<int64_t> prefix(cc.ue - cc.ub + 1, 0);
   int maxlen = 0;
   for (int u = cc.ub; u < cc.ue; ++u) {
@@ -220,6 +244,8 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
   job.mode = mode;
   job.qlist = P<int32_t>(ctx->qlist);
   job.nq = nq_list;
+  job.sub_off = sub_off;
+  job.sub_n = sub_n;
   job.qb = cc.ub;
   job.qe = cc.ue;
   job.prefix = P<int64_t>(ctx->prefix);
@@ -326,6 +352,51 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
                                                 P<unsigned long long>(ctx->pairsum),
                                                 P<int32_t>(ctx->self), ctx->st));
   }
+  return MSA_OK;
+}
+
+// Time every packed variant on a sample of each query-length bucket: up to
+// 16 queries of the bucket against a window of subjects at and after them
+// (query-side sums, nothing the selection reads), keeping the second run.
+int autotune(msa_ctx *ctx) {
+  static const int edges[] = {1, 48, 80, 112, 144, 176, 208, 256, 320, 384, 448, 512, 640,
+                              768, 896, 1024, 1280, 1536, 2048, 3072, 4096, MSA_MAX_LEN + 1};
+  const int nb = (int)(sizeof(edges) / sizeof(edges[0])) - 1;
+  const int n = ctx->n;
+  std::vector<std::vector<double>> rate(nb, std::vector<double>(kNumCenterVariants, 0.0));
+  TRY(ensure(ctx, ctx->pairsum, sizeof(unsigned long long) * n));
+  for (int b = 0; b < nb; ++b) {
+    const int lo = edges[b], hi = edges[b + 1];
+    const int xb = (int)(std::lower_bound(ctx->len_sorted.begin(), ctx->len_sorted.end(), lo) - ctx->len_sorted.begin());
+    const int xe = (int)(std::lower_bound(ctx->len_sorted.begin(), ctx->len_sorted.end(), hi) - ctx->len_sorted.begin());
+    if (xe <= xb) continue;
+    std::vector<int32_t> qs;
+    const int want = std::min(16, xe - xb);
+    for (int i = 0; i < want; ++i) qs.push_back(xb + (int)((int64_t)i * (xe - xb) / want));
+    std::vector<int> qlen;
+    double qcells = 0;
+    for (int q : qs) { qlen.push_back(ctx->len_sorted[q]); qcells += ctx->len_sorted[q]; }
+    const double lq = qcells / qs.size();
+    int sub_n = (int)std::max(256.0, std::min(4096.0, 2e10 / (qs.size() * lq * lq)));
+    sub_n = std::min(sub_n, n - xb);
+    double scells = 0;
+    for (int s = xb; s < xb + sub_n; ++s) scells += ctx->len_sorted[s];
+    TRY(ensure(ctx, ctx->qlist, sizeof(int32_t) * qs.size()));
+    CK(cudaMemcpyAsync(ctx->qlist.p, qs.data(), sizeof(int32_t) * qs.size(), cudaMemcpyHostToDevice, ctx->st));
+    for (int v = 0; v < kNumCenterVariants; ++v) {
+      const CenterVariant &cv = kCenterVariants[v];
+      if (!cv.packed || !variant_fits(ctx, v, hi - 1)) continue;
+      const int units = cv.paired ? ((int)qs.size() + 1) / 2 : (int)qs.size();
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        ms = 0.f;
+        TRY(launch_class(ctx, 2, (int)qs.size(), CenterClass{v, 0, units}, qlen, ms, xb, sub_n));
+      }
+      if (ms > 0) rate[b][v] = qcells * scells / (ms * 1e-3);
+    }
+  }
+  ctx->tune_edges.assign(edges, edges + nb + 1);
+  ctx->tune_rate = rate;
   return MSA_OK;
 }
 
@@ -821,6 +892,23 @@ int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out) {
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_SP);
   *sp_cost_out = v;
+  return MSA_OK;
+}
+
+int msa_autotune(msa_ctx *ctx, double *rates_out, int32_t *dims_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  TRY(set_device(ctx));
+  if (ctx->smin + ctx->o < 0 || ctx->precision == MSA_INT32) {
+    ctx->tune_rate.clear();  // no packed variants to time
+  } else {
+    TRY(autotune(ctx));
+  }
+  const int nb = ctx->tune_rate.empty() ? 0 : (int)ctx->tune_rate.size();
+  if (dims_out) { dims_out[0] = nb; dims_out[1] = kNumCenterVariants; }
+  if (rates_out)
+    for (int b = 0; b < nb; ++b)
+      for (int v = 0; v < kNumCenterVariants; ++v) rates_out[b * kNumCenterVariants + v] = ctx->tune_rate[b][v];
   return MSA_OK;
 }
 

@@ -193,7 +193,8 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
       if (job.prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
     const int q = job.mode == 0 ? job.qb + lo : job.qlist[job.qb + lo];
-    const int s0 = (job.mode == 0 ? q : 0) + (int)(item - job.prefix[lo]) * SPI;
+    const int s0 = (job.mode == 0 ? q : job.sub_off) + (int)(item - job.prefix[lo]) * SPI;
+    const int send = job.mode == 0 ? ss.n : job.sub_off + job.sub_n;
     const int Lq = ss.len[q];
     const uint8_t *rq = ss.res + ss.pstart[q];
     const int np = (Lq + G * R - 1) / (G * R);
@@ -207,7 +208,7 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
     __syncthreads();
 
     const int sA = s0 + g * LANES, sB = sA + 1;
-    const bool vA = sA < ss.n, vB = PACK && sB < ss.n;
+    const bool vA = sA < send, vB = PACK && sB < send;
     const int LA = vA ? ss.len[sA] : 0, LB = vB ? ss.len[sB] : 0;
     const uint8_t *rA = ss.res + (vA ? ss.pstart[sA] : 0);
     const uint8_t *rB = ss.res + (vB ? ss.pstart[sB] : 0);
@@ -337,7 +338,7 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
 
 // Work item = (query pair p, block of NG consecutive subjects, one per group).
 template <int G, int R>
-__global__ void __launch_bounds__(kCenterThreads)
+__global__ void __launch_bounds__(kCenterThreads, R <= 20 ? 3 : 2)
 k_center2(SeqSet ss, Scoring sc, CenterJob job) {
   extern __shared__ __align__(16) uint32_t smem32[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
@@ -368,7 +369,8 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
     const int xa = 2 * pidx, xb = 2 * pidx + 1;
     const int qA = job.mode == 0 ? xa : job.qlist[xa];
     const int qB = xb < job.nq ? (job.mode == 0 ? xb : job.qlist[xb]) : -1;
-    const int s0 = (job.mode == 0 ? xa : 0) + (int)(item - job.prefix[lo]) * NG;
+    const int s0 = (job.mode == 0 ? xa : job.sub_off) + (int)(item - job.prefix[lo]) * NG;
+    const int send = job.mode == 0 ? ss.n : job.sub_off + job.sub_n;
     const int LqA = ss.len[qA], LqB = qB >= 0 ? ss.len[qB] : 0;
     const uint8_t *ra = ss.res + ss.pstart[qA];
     const uint8_t *rb = ss.res + ss.pstart[qB >= 0 ? qB : qA];
@@ -386,7 +388,7 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
     __syncthreads();
 
     const int s = s0 + g;
-    const bool valid = s < ss.n;
+    const bool valid = s < send;
     const int Ls = valid ? ss.len[s] : 0;
     const uint8_t *rs = ss.res + (valid ? ss.pstart[s] : 0);
     const int Lw = __reduce_max_sync(MSA_FULL_MASK, Ls);

@@ -23,6 +23,7 @@ struct CenterJob {
   const int32_t *qlist;           // mode 1 (sorted indices)
   int nq;                         // queries in the list (mode 0: n)
   int qb, qe;                     // item-unit range: queries (single) or query pairs (paired)
+  int sub_off, sub_n;             // modes 1, 2: subjects [sub_off, sub_off + sub_n)
   const int64_t *prefix;          // device, qe-qb+1 entries: first item of each query
   int64_t n_items;
   int npass;                      // passes of the longest query in the range

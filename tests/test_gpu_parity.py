@@ -259,3 +259,34 @@ def test_batched_uneven_10k_full_size_sampled():
     for t in range(0, n, 97):
         assert bytes(rows[t]).replace(b"-", b"") == bytes(letters[offsets[t]:offsets[t + 1]])
     assert sp == oracle.sp_columns(rows)
+
+
+def test_autotuned_selection_is_unchanged():
+    """The autotuner only changes which kernel variant runs, never a result."""
+    b = binding()
+    letters, offsets, w, alph, M = workload("batched_uneven_10k", n=300, seed=12)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    oc, orow = oracle.exact_center(prob)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        rates = b.msa_autotune(h)
+        c, s = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        rows = b.msa_center_rowsums(h)
+    assert rates.shape[1] >= 9 and (rates > 0).sum() >= 9
+    assert (rows == orow).all() and c == oc
+
+
+def test_short_peptides_against_their_center():
+    """Peptides cut from a 500-residue ancestor (which is sequence 0):
+    sampled exact center and the whole MSA, bit-exact."""
+    b = binding()
+    letters, offsets, w, alph, M = workload("short_peptides_1m", n=1500, seed=5)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    refs = reference_sample(prob.n, 100, seed=3)
+    oc, orow = oracle.exact_center(prob, refs=refs)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        c, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT_SAMPLED, refs=refs)
+        assert (b.msa_center_rowsums(h) == orow).all() and c == oc
+        out = run_pipeline(b, h, letters, offsets, 0)
+    check_against_oracle(prob, 0, *out)
