@@ -59,6 +59,8 @@ def parse():
                     help="time the exact-center selection alone (profiling cases)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-center comparison")
+    ap.add_argument("--autotune", action="store_true",
+                    help="correct the center planner's cost model with measured rates first")
     return ap.parse_args()
 
 
@@ -320,7 +322,8 @@ def run_ours(args):
     rate, per_clk = b.msa_probe_int_rate(b.MSA_PROBE_VIADDMAX_S16X2)
     b.msa_load(h, dlet, offsets)
     t0 = time.perf_counter()
-    tune = b.msa_autotune(h)  # untimed: picks the center kernel variant per length bucket
+    # untimed: picks the center kernel variant per length bucket
+    tune = b.msa_autotune(h) if args.autotune else np.zeros((0, 0))
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         step_device()

@@ -219,7 +219,8 @@ int msa_selector_grad(msa_ctx *ctx, const int64_t *pairs, const float *targets, 
                       float *grad_out, float *loss_out);
 
 /* Train: cfg->steps Adam steps over batches of cfg->batch_pairs pairs drawn
- * from the list (reshuffled every pass).  targets: host float[npairs], or
+ * from the list (reshuffled every pass); the learning rate follows a cosine
+ * from cfg->lr at the first step to cfg->lr / 10 at the last.  targets: host float[npairs], or
  * NULL to compute them with the exact kernel (scale cfg->target_scale).  Initialises the parameters
  * from cfg->seed if none are set.  losses_out: host float[cfg->steps]
  * (nullable), the loss of each step's batch before its update. */
@@ -235,12 +236,14 @@ int msa_save_selector(msa_ctx *ctx, const char *path);
 int msa_load_selector(msa_ctx *ctx, const char *path);
 
 /* Autotuner: time every packed center-selection kernel variant (threads per
- * query group x query rows per thread, paired or single query) on a sample
- * of the loaded set per query-length bucket, and let later selections on
- * this context pick, per bucket, the variant with the highest measured
- * cells/s (instead of the built-in cost model).  Results do not depend on
- * the variant.  rates_out (nullable, host double[buckets][variants], at most
- * 21 x 16) and dims_out (nullable, host int32[2] = {buckets, variants}).
+ * query group x query rows per thread, paired or single query) per
+ * query-length bucket, on up to 128 of the bucket's queries against their
+ * real all-pairs partners (every sequence from the bucket on), and let later
+ * selections on this context scale the built-in cost model of each variant
+ * by its measured / modelled speed in the query's bucket.  Results do not depend on the
+ * variant.  rates_out (nullable, host double[buckets][variants], at most
+ * 21 x 16): measured cells per second, 0 where a variant was not timed;
+ * dims_out (nullable, host int32[2] = {buckets, variants}).
  * Bucket edges: 1 48 80 112 144 176 208 256 320 384 448 512 640 768 896
  * 1024 1280 1536 2048 3072 4096 8193. */
 int msa_autotune(msa_ctx *ctx, double *rates_out, int32_t *dims_out);

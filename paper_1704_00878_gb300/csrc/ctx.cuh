@@ -79,6 +79,7 @@ struct msa_ctx {
   // autotuner: measured cells/s of each center variant per query-length bucket
   std::vector<int> tune_edges;                 // bucket b = [edges[b], edges[b+1])
   std::vector<std::vector<double>> tune_rate;  // [bucket][variant], 0 = not measured
+  std::vector<std::vector<double>> tune_corr;  // [bucket][variant]: measured / modelled rate
 };
 
 namespace msa_detail {

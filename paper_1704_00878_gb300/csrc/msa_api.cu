@@ -163,20 +163,11 @@ bool variant_fits(msa_ctx *ctx, int v, int Lq) {
 }
 
 int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
-  // measured rates (msa_autotune) take precedence over the cost model
-  if (packed && !ctx->tune_rate.empty()) {
-    for (size_t b = 0; b + 1 < ctx->tune_edges.size(); ++b) {
-      if (Lq < ctx->tune_edges[b] || Lq >= ctx->tune_edges[b + 1]) continue;
-      int best = -1;
-      double rate = 0;
-      for (int v = 0; v < kNumCenterVariants; ++v)
-        if (ctx->tune_rate[b][v] > rate && kCenterVariants[v].packed && variant_fits(ctx, v, Lq)) {
-          rate = ctx->tune_rate[b][v];
-          best = v;
-        }
-      if (best >= 0) return best;
-    }
-  }
+  // msa_autotune's correction of the model for this length bucket, if any
+  const std::vector<double> *corr = nullptr;
+  if (packed && !ctx->tune_corr.empty())
+    for (size_t b = 0; b + 1 < ctx->tune_edges.size(); ++b)
+      if (Lq >= ctx->tune_edges[b] && Lq < ctx->tune_edges[b + 1]) corr = &ctx->tune_corr[b];
   int best = -1;
   double best_cost = 1e300;
   for (int v = 0; v < kNumCenterVariants; ++v) {
@@ -187,7 +178,8 @@ int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
     const int smem = center_smem_bytes(v, ctx->K, np * rows);
     if (cv.paired && smem > kMaxPairedProfile) continue;
     if (smem > 200 * 1024) continue;
-    const double c = variant_cost(v, Lq, Ls_est);
+    double c = variant_cost(v, Lq, Ls_est);
+    if (corr && (*corr)[v] > 0) c /= (*corr)[v];
     if (c < best_cost) { best_cost = c; best = v; }
   }
   return best;
@@ -292,29 +284,34 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   // local score of any pair is at most min(Lq, Ls) * smax <= Lq * smax.
   int x1 = 0;
   while (x1 < nq && use_packed(ctx, qlen[x1])) ++x1;
-  auto est = [&](int Lq) { return mode == 0 ? Lq : (int)mean; };
+  // partner length: all-pairs queries meet the (longer) sequences after them
+  auto est_at = [&](int x) {
+    return mode == 0 ? (int)(suffix[x] / std::max(1, n - x)) : (int)mean;
+  };
 
   std::vector<CenterClass> classes;
   // packed part: query pairs [0, ceil(x1/2))
   const int npairs = (x1 + 1) / 2;
   for (int p = 0; p < npairs;) {
-    const int Lq = qlen[std::min(2 * p + 1, x1 - 1)];
-    const int v = choose_variant(ctx, Lq, est(Lq), true);
-    if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", Lq);
+    const int xq = std::min(2 * p + 1, x1 - 1);
+    const int v = choose_variant(ctx, qlen[xq], est_at(xq), true);
+    if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", qlen[xq]);
     int pe = p + 1;
-    while (pe < npairs && choose_variant(ctx, qlen[std::min(2 * pe + 1, x1 - 1)],
-                                         est(qlen[std::min(2 * pe + 1, x1 - 1)]), true) == v)
+    while (pe < npairs) {
+      const int xe = std::min(2 * pe + 1, x1 - 1);
+      if (choose_variant(ctx, qlen[xe], est_at(xe), true) != v) break;
       ++pe;
+    }
     if (kCenterVariants[v].paired) classes.push_back({v, p, pe});
     else classes.push_back({v, 2 * p, std::min(2 * pe, x1)});
     p = pe;
   }
   // int32 part: single queries [x1, nq)
   for (int x = x1; x < nq;) {
-    const int v = choose_variant(ctx, qlen[x], est(qlen[x]), false);
+    const int v = choose_variant(ctx, qlen[x], est_at(x), false);
     if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", qlen[x]);
     int xe = x + 1;
-    while (xe < nq && choose_variant(ctx, qlen[xe], est(qlen[xe]), false) == v) ++xe;
+    while (xe < nq && choose_variant(ctx, qlen[xe], est_at(xe), false) == v) ++xe;
     classes.push_back({v, x, xe});
     x = xe;
   }
@@ -355,15 +352,17 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   return MSA_OK;
 }
 
-// Time every packed variant on a sample of each query-length bucket: up to
-// 16 queries of the bucket against a window of subjects at and after them
-// (query-side sums, nothing the selection reads), keeping the second run.
+// Time every packed variant on each query-length bucket: up to 128 queries
+// of the bucket, evenly spaced, against their real partners (every sequence
+// from the bucket on, as in the all-pairs selection; query-side sums, which
+// the selection never reads), keeping the second of two runs.
 int autotune(msa_ctx *ctx) {
   static const int edges[] = {1, 48, 80, 112, 144, 176, 208, 256, 320, 384, 448, 512, 640,
                               768, 896, 1024, 1280, 1536, 2048, 3072, 4096, MSA_MAX_LEN + 1};
   const int nb = (int)(sizeof(edges) / sizeof(edges[0])) - 1;
   const int n = ctx->n;
   std::vector<std::vector<double>> rate(nb, std::vector<double>(kNumCenterVariants, 0.0));
+  std::vector<std::vector<double>> corr(nb, std::vector<double>(kNumCenterVariants, 0.0));
   TRY(ensure(ctx, ctx->pairsum, sizeof(unsigned long long) * n));
   for (int b = 0; b < nb; ++b) {
     const int lo = edges[b], hi = edges[b + 1];
@@ -371,16 +370,14 @@ int autotune(msa_ctx *ctx) {
     const int xe = (int)(std::lower_bound(ctx->len_sorted.begin(), ctx->len_sorted.end(), hi) - ctx->len_sorted.begin());
     if (xe <= xb) continue;
     std::vector<int32_t> qs;
-    const int want = std::min(16, xe - xb);
+    const int want = std::min(128, xe - xb);
     for (int i = 0; i < want; ++i) qs.push_back(xb + (int)((int64_t)i * (xe - xb) / want));
     std::vector<int> qlen;
     double qcells = 0;
     for (int q : qs) { qlen.push_back(ctx->len_sorted[q]); qcells += ctx->len_sorted[q]; }
-    const double lq = qcells / qs.size();
-    int sub_n = (int)std::max(256.0, std::min(4096.0, 2e10 / (qs.size() * lq * lq)));
-    sub_n = std::min(sub_n, n - xb);
+    const int sub_off = xb, sub_n = n - xb;
     double scells = 0;
-    for (int s = xb; s < xb + sub_n; ++s) scells += ctx->len_sorted[s];
+    for (int s = sub_off; s < n; ++s) scells += ctx->len_sorted[s];
     TRY(ensure(ctx, ctx->qlist, sizeof(int32_t) * qs.size()));
     CK(cudaMemcpyAsync(ctx->qlist.p, qs.data(), sizeof(int32_t) * qs.size(), cudaMemcpyHostToDevice, ctx->st));
     for (int v = 0; v < kNumCenterVariants; ++v) {
@@ -390,13 +387,24 @@ int autotune(msa_ctx *ctx) {
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
         ms = 0.f;
-        TRY(launch_class(ctx, 2, (int)qs.size(), CenterClass{v, 0, units}, qlen, ms, xb, sub_n));
+        TRY(launch_class(ctx, 2, (int)qs.size(), CenterClass{v, 0, units}, qlen, ms, sub_off, sub_n));
       }
       if (ms > 0) rate[b][v] = qcells * scells / (ms * 1e-3);
+    }
+    // correction = measured / modelled rate, the model's rate being the
+    // sample's cells over its modelled cost (the same constant for all
+    // variants of the bucket)
+    const int ls = (int)(scells / sub_n);
+    for (int v = 0; v < kNumCenterVariants; ++v) {
+      if (rate[b][v] <= 0) continue;
+      double model = 0;
+      for (int L : qlen) model += variant_cost(v, L, ls);
+      corr[b][v] = rate[b][v] * model / (qcells * ls * (double)sub_n);
     }
   }
   ctx->tune_edges.assign(edges, edges + nb + 1);
   ctx->tune_rate = rate;
+  ctx->tune_corr = corr;
   return MSA_OK;
 }
 

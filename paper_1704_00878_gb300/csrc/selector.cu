@@ -483,8 +483,11 @@ int msa_selector_train(msa_ctx *ctx, const int64_t *pairs, const float *targets,
     TRY(stage_pairs(ctx, s, bpairs.data(), bt.data(), bp, b));
     TRY(forward_backward(ctx, s, b, bp));
     s->step += 1;
+    // cosine decay of the learning rate from lr to lr / 10 over the steps
+    const double frac = cfg->steps > 1 ? (double)step / (cfg->steps - 1) : 0.0;
+    const float lr = (float)(cfg->lr * (0.1 + 0.45 * (1.0 + std::cos(3.141592653589793 * frac))));
     CK((++ctx->launches, net::adam)(P<float>(s->params), P<float>(s->grads), P<float>(s->m), P<float>(s->v),
-                                    net::N_PARAMS, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, s->step, ctx->st));
+                                    net::N_PARAMS, lr, cfg->beta1, cfg->beta2, cfg->eps, s->step, ctx->st));
     TRY(refresh_all(ctx, s));
     if (losses_out)
       CK(cudaMemcpyAsync(losses_out + step, s->loss.p, sizeof(float), cudaMemcpyDeviceToHost, ctx->st));

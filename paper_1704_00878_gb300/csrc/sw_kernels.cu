@@ -338,7 +338,7 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
 
 // Work item = (query pair p, block of NG consecutive subjects, one per group).
 template <int G, int R>
-__global__ void __launch_bounds__(kCenterThreads, R <= 20 ? 3 : 2)
+__global__ void __launch_bounds__(kCenterThreads)
 k_center2(SeqSet ss, Scoring sc, CenterJob job) {
   extern __shared__ __align__(16) uint32_t smem32[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
