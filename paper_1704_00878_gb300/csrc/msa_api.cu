@@ -694,7 +694,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   ctx->aligned = ctx->merged = false;
   ctx->center = center;
   ctx->Lc = Lc;
-  const int R = kCodesR, G = kCodesG;
+  const int R = kCodesR, G = codes_group(Lc);
   const int nblk = (Lc + R - 1) / R;
   const int npass = (Lc + G * R - 1) / (G * R);
   const size_t row = (size_t)Lc + 1;
@@ -739,8 +739,8 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   const SeqSet ss = seqset(ctx);
   const Scoring sc = scoring(ctx);
   const int smem = codes_smem_bytes(ctx->K, npass * G * R);
-  const int grid = codes_grid(smem);
-  if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * 8 * 2 * ctx->maxlen * sizeof(int2)));
+  const int grid = codes_grid(G, smem);
+  if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
   float ms_dp = 0.f, ms_tb = 0.f;
   int64_t cells = 0;
   for (int k = 0; k < n; ++k) cells += (int64_t)Lc * ctx->len_sorted[k];
@@ -759,7 +759,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
     // offsets inside the batch are relative to the batch start
-    CK((++ctx->launches, launch_codes)(ss, sc, job, grid, ctx->st));
+    CK((++ctx->launches, launch_codes)(G, ss, sc, job, grid, ctx->st));
     stage_end(ctx, ST_ALIGN);
     stage_begin(ctx, ST_TRACE);
     CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
@@ -806,7 +806,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
   // recompute the codes of this one subject into a private buffer
   const int ks = ctx->inv[seq], kc = ctx->inv[ctx->center];
   const int Lc = ctx->Lc, Ls = ctx->len_sorted[ks];
-  const int R = kCodesR, G = kCodesG, nblk = (Lc + R - 1) / R, npass = (Lc + G * R - 1) / (G * R);
+  const int R = kCodesR, G = codes_group(Lc), nblk = (Lc + R - 1) / R, npass = (Lc + G * R - 1) / (G * R);
   const size_t bytes = (size_t)nblk * Ls * 8;
   DevBuf cb, ob, bb, ib, oc, sg, sc_;
   auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb, &ib, &oc, &sg, &sc_}) if (b->p) cudaFree(b->p); };
@@ -818,7 +818,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
     const int smem = codes_smem_bytes(ctx->K, npass * G * R);
     const int grid = 1;
-    if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(smem) * 8 * 2 * ctx->maxlen * sizeof(int2)));
+    if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, smem) * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
     CodesJob job;
     job.center = kc;
     job.sb = ks;
@@ -830,7 +830,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     job.counter = ctx->dcounter;
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
-    CK((++ctx->launches, launch_codes)(seqset(ctx), scoring(ctx), job, grid, ctx->st));
+    CK((++ctx->launches, launch_codes)(G, seqset(ctx), scoring(ctx), job, grid, ctx->st));
     std::vector<uint8_t> packed(bytes), out((size_t)Lc * Ls);
     CK(cudaMemcpyAsync(packed.data(), cb.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));

@@ -501,13 +501,14 @@ __global__ void __launch_bounds__(256) k_pairs(SeqSet ss, Scoring sc, PairJob jo
 // 1 diagonal, 2 F, 3 E; ties in that order), bit 2 "E extended", bit 3 "F
 // extended" (extension only when strictly better than opening).  Each lane
 // also keeps, per row, the first column reaching the row's maximum.
+template <int G>
 __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int stride,
-                                           const uint8_t *__restrict__ rs, int Ls, int t,
-                                           int blk, int nblk, int padc, int o, int e,
+                                           const uint8_t *__restrict__ rs, int Ls, int Lw, int t,
+                                           int base_lane, int blk, int nblk, int padc, int o, int e,
                                            const int2 *__restrict__ scr_in,
                                            int2 *__restrict__ scr_out, uint2 *__restrict__ cout,
                                            int &bv, int &bi, int &bj) {
-  constexpr int G = kCodesG, R = kCodesR;
+  constexpr int R = kCodesR;
   int H[R], E[R], rb[R], rj[R];
   uint32_t emask = 0;
 #pragma unroll
@@ -518,11 +519,11 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
   uint32_t cur = residue_at(rs, Ls, t, pc), nxt = residue_at(rs, Ls, G + t, pc);
   const int8_t *pb = prof + t * R;
   const bool wr = blk < nblk;
-  const int steps = Ls + G - 1;
+  const int steps = Lw + G - 1;  // warp-uniform; columns past Ls are padding
   for (int k = 0; k < steps; ++k) {
     const int kk = k & (G - 1);
     if (kk == 0 && k > 0) { cur = nxt; nxt = residue_at(rs, Ls, k + G + t, pc); }
-    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, kk);
+    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
     uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
     int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
     int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
@@ -580,8 +581,12 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
   }
 }
 
+// Groups of G lanes (G in {8, 16, 32}, chosen from the center length), each
+// aligning one subject at a time; the groups of a warp fetch their subjects
+// together and run the warp's longest subject's number of columns.
+template <int G>
 __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob job) {
-  constexpr int G = kCodesG, R = kCodesR, NT = 256, NW = NT / 32;
+  constexpr int R = kCodesR, NT = 256, NG = NT / G, GPW = 32 / G;
   extern __shared__ __align__(16) int8_t smem[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
   const int K = sc.K, padc = K;
@@ -598,38 +603,42 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
     smem[r * stride + i] = (int8_t)v;
   }
   __syncthreads();
-  const int t = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, t = threadIdx.x % G, g = threadIdx.x / G;
+  const int base_lane = lane - t;
   const int nblk = (Lc + R - 1) / R;
-  int2 *scr = job.scratch + ((size_t)blockIdx.x * NW + wid) * 2 * job.scratch_cols;
+  int2 *scr = job.scratch + ((size_t)blockIdx.x * NG + g) * 2 * job.scratch_cols;
   const int nsub = job.se - job.sb;
   for (;;) {
-    int x = 0;
-    if (t == 0) x = (int)atomicAdd(job.counter, 1ull);
-    x = __shfl_sync(MSA_FULL_MASK, x, 0);
-    if (x >= nsub) break;
-    const int k = job.se - 1 - x;  // longest first
-    const int Ls = ss.len[k];
+    int x0 = 0;
+    if (lane == 0) x0 = (int)atomicAdd(job.counter, (unsigned long long)GPW);
+    x0 = __shfl_sync(MSA_FULL_MASK, x0, 0);
+    if (x0 >= nsub) break;
+    const int x = x0 + lane / G;
+    const bool valid = x < nsub;
+    const int k = job.se - 1 - (valid ? x : 0);  // longest first
+    const int Ls = valid ? ss.len[k] : 0;
     const uint8_t *rs = ss.res + ss.pstart[k];
-    uint2 *cbase = reinterpret_cast<uint2 *>(job.codes + job.code_off[k - job.sb]);
+    uint2 *cbase = valid ? reinterpret_cast<uint2 *>(job.codes + job.code_off[k - job.sb]) : nullptr;
+    const int Lw = __reduce_max_sync(MSA_FULL_MASK, Ls);
     int bv = 0, bi = 0, bj = 0;
     for (int p = 0; p < job.npass; ++p) {
       const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
       int2 *sout = p + 1 < job.npass ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
       const int blk = p * G + t;
-      codes_pass(smem + p * G * R, stride, rs, Ls, t, blk, nblk, padc, sc.o, sc.e, sin, sout,
-                 cbase + (size_t)blk * Ls, bv, bi, bj);
+      codes_pass<G>(smem + p * G * R, stride, rs, Ls, Lw, t, base_lane, blk, nblk, padc, sc.o, sc.e,
+                    sin, sout, valid ? cbase + (size_t)blk * Ls : nullptr, bv, bi, bj);
       __syncwarp();
     }
     // best cell over the group: largest H, then smallest row, then smallest column
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = G / 2; off > 0; off >>= 1) {
       const int ov = __shfl_xor_sync(MSA_FULL_MASK, bv, off);
       const int oi = __shfl_xor_sync(MSA_FULL_MASK, bi, off);
       const int oj = __shfl_xor_sync(MSA_FULL_MASK, bj, off);
       const bool take = ov > bv || (ov == bv && (oi < bi || (oi == bi && oj < bj)));
       if (take) { bv = ov; bi = oi; bj = oj; }
     }
-    if (t == 0) {
+    if (t == 0 && valid) {
       int32_t *b = job.best + (size_t)(k - job.sb) * 3;
       b[0] = bv;
       b[1] = bv > 0 ? bi : 0;
@@ -743,14 +752,26 @@ int codes_smem_bytes(int K, int rows_alloc) {
   return (K + 1) * round_up_int(rows_alloc, MSA_PROF_ALIGN);
 }
 
-int codes_grid(int smem) { return occupancy_grid((const void *)k_codes, 256, smem); }
+typedef void (*codes_fn)(SeqSet, Scoring, CodesJob);
+static codes_fn codes_kernel(int G) {
+  return G == 8 ? k_codes<8> : (G == 16 ? k_codes<16> : (G == 32 ? k_codes<32> : nullptr));
+}
 
-cudaError_t launch_codes(const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
+int codes_group(int Lc) { return Lc <= 8 * kCodesR ? 8 : (Lc <= 16 * kCodesR ? 16 : 32); }
+
+int codes_grid(int G, int smem) {
+  codes_fn fn = codes_kernel(G);
+  return fn ? occupancy_grid((const void *)fn, 256, smem) : 0;
+}
+
+cudaError_t launch_codes(int G, const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
                          cudaStream_t st) {
-  const int smem = codes_smem_bytes(sc.K, job.npass * kCodesG * kCodesR);
+  codes_fn fn = codes_kernel(G);
+  if (!fn) return cudaErrorInvalidValue;
+  const int smem = codes_smem_bytes(sc.K, job.npass * G * kCodesR);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute((const void *)k_codes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_codes<<<grid, 256, smem, st>>>(ss, sc, job);
+    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  fn<<<grid, 256, smem, st>>>(ss, sc, job);
   return cudaGetLastError();
 }
 

@@ -73,10 +73,13 @@ cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJ
 int pairs_grid(int G);
 int pairs_rows(int G);
 
-cudaError_t launch_codes(const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
+// G = threads per subject group (8, 16 or 32; codes_group picks it from the
+// center length); 16 center rows per thread.
+cudaError_t launch_codes(int G, const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
                          cudaStream_t st);
 int codes_smem_bytes(int K, int rows_alloc);
-int codes_grid(int smem);
-constexpr int kCodesG = 32, kCodesR = 16;
+int codes_grid(int G, int smem);
+int codes_group(int Lc);
+constexpr int kCodesR = 16;
 constexpr int kPairsR = 16;
 constexpr int kCenterThreads = 256;
