@@ -165,6 +165,18 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out);
  * uint8[n][W] (ASCII letters and '-').  width_out: host int64. */
 int msa_merge_gaps(msa_ctx *ctx, uint8_t *msa_out, int64_t *width_out);
 
+/* The local part of Figure 3's reduce, for a set split across processes
+ * (each aligns its shard, plus the center, to the same center): G_out host
+ * or device int32[Lc+1] receives this context's per-slot maxima of the
+ * inserted-space rows; the elementwise maximum over processes is the
+ * global G. */
+int msa_insert_maxima(msa_ctx *ctx, int32_t *G_out);
+
+/* msa_merge_gaps with given slot widths G (host or device int32[Lc+1], e.g.
+ * the maximum over processes): width W = Lc + sum G.  EINVAL if some row
+ * inserts more residues in a slot than G allows. */
+int msa_merge_gaps_with(msa_ctx *ctx, const int32_t *G, uint8_t *msa_out, int64_t *width_out);
+
 /* Sum-of-pairs cost of the merged alignment (the paper's avg SP numerator:
  * +1 per differing residue pair, +2 per residue-gap pair, per column);
  * avg SP = cost / (n(n-1)/2).  sp_cost_out: host int64. */

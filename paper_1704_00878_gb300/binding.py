@@ -57,6 +57,8 @@ _SIGS = {
     "msa_debug_codes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "msa_merge_gaps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_sp_score": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_insert_maxima": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_merge_gaps_with": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
@@ -236,6 +238,24 @@ def msa_merge_gaps(ctx, out=None, want_rows=True):
     n = msa_dims(ctx)[0]
     res = np.zeros((n, W), np.uint8) if out is None else out
     _check(ctx, lib().msa_merge_gaps(ctx, _ptr(res), _ptr(w)))
+    return res, W
+
+
+def msa_insert_maxima(ctx):
+    lc = msa_dims(ctx)[2]
+    G = np.zeros(lc + 1, np.int32)
+    _check(ctx, lib().msa_insert_maxima(ctx, _ptr(G)))
+    return G
+
+
+def msa_merge_gaps_with(ctx, G, out=None):
+    """(rows uint8[n, W], W) merged with the given slot widths."""
+    g = np.ascontiguousarray(G, dtype=np.int32)
+    w = np.zeros(1, np.int64)
+    _check(ctx, lib().msa_merge_gaps_with(ctx, _ptr(g), None, _ptr(w)))
+    W = int(w[0])
+    res = np.zeros((msa_dims(ctx)[0], W), np.uint8) if out is None else out
+    _check(ctx, lib().msa_merge_gaps_with(ctx, _ptr(g), _ptr(res), _ptr(w)))
     return res, W
 
 

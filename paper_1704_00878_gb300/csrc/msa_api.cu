@@ -883,6 +883,54 @@ int msa_merge_gaps(msa_ctx *ctx, uint8_t *msa_out, int64_t *width_out) {
   return MSA_OK;
 }
 
+int msa_insert_maxima(msa_ctx *ctx, int32_t *G_out) {
+  if (!ctx || !G_out) return MSA_EINVAL;
+  if (!ctx->aligned) return fail(ctx, MSA_ESTATE, "align to a center first");
+  TRY(set_device(ctx));
+  const int Lc = ctx->Lc;
+  TRY(ensure(ctx, ctx->G, sizeof(int32_t) * (Lc + 1)));
+  CK(cudaMemsetAsync(ctx->G.p, 0, sizeof(int32_t) * (Lc + 1), ctx->st));
+  CK((++ctx->launches, launch_colmax)(P<uint16_t>(ctx->ins), ctx->n, Lc, P<int32_t>(ctx->G), ctx->st));
+  CK(cudaMemcpyAsync(G_out, ctx->G.p, sizeof(int32_t) * (Lc + 1), cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->merged = false;
+  return MSA_OK;
+}
+
+int msa_merge_gaps_with(msa_ctx *ctx, const int32_t *G, uint8_t *msa_out, int64_t *width_out) {
+  if (!ctx || !G || !width_out) return MSA_EINVAL;
+  if (!ctx->aligned) return fail(ctx, MSA_ESTATE, "align to a center first");
+  TRY(set_device(ctx));
+  const int n = ctx->n, Lc = ctx->Lc;
+  std::vector<int32_t> hg(Lc + 1), local(Lc + 1);
+  CK(cudaMemcpyAsync(hg.data(), G, sizeof(int32_t) * (Lc + 1), cudaMemcpyDefault, ctx->st));
+  TRY(ensure(ctx, ctx->G, sizeof(int32_t) * (Lc + 1)));
+  TRY(ensure(ctx, ctx->off, sizeof(int32_t) * (Lc + 1)));
+  CK(cudaMemsetAsync(ctx->G.p, 0, sizeof(int32_t) * (Lc + 1), ctx->st));
+  CK((++ctx->launches, launch_colmax)(P<uint16_t>(ctx->ins), n, Lc, P<int32_t>(ctx->G), ctx->st));
+  CK(cudaMemcpyAsync(local.data(), ctx->G.p, sizeof(int32_t) * (Lc + 1), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int j = 0; j <= Lc; ++j)
+    if (hg[j] < local[j]) return fail(ctx, MSA_EINVAL, "G[%d] = %d is below this set's %d", j, hg[j], local[j]);
+  CK(cudaMemcpyAsync(ctx->G.p, hg.data(), sizeof(int32_t) * (Lc + 1), cudaMemcpyHostToDevice, ctx->st));
+  stage_begin(ctx, ST_MERGE);
+  CK((++ctx->launches, launch_scan)(P<int32_t>(ctx->G), Lc, P<int32_t>(ctx->off), (int64_t *)(ctx->dsmall + 3), ctx->st));
+  stage_end(ctx, ST_MERGE);
+  long long W = 0;
+  CK(cudaMemcpyAsync(&W, ctx->dsmall + 3, sizeof W, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->W = W;
+  TRY(ensure(ctx, ctx->msa, (size_t)n * (size_t)W));
+  CK((++ctx->launches, launch_rows)(P<uint8_t>(ctx->res), P<int64_t>(ctx->d_pstart), P<int32_t>(ctx->d_inv),
+                                    P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->G),
+                                    P<int32_t>(ctx->off), n, Lc, W, ctx->dLetters, P<uint8_t>(ctx->msa), ctx->st));
+  ctx->merged = true;
+  *width_out = W;
+  if (msa_out) CK(cudaMemcpyAsync(msa_out, ctx->msa.p, (size_t)n * (size_t)W, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
+}
+
 int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out) {
   if (!ctx || !sp_cost_out) return MSA_EINVAL;
   if (!ctx->merged) return fail(ctx, MSA_ESTATE, "merge first");

@@ -290,3 +290,36 @@ def test_short_peptides_against_their_center():
         assert (b.msa_center_rowsums(h) == orow).all() and c == oc
         out = run_pipeline(b, h, letters, offsets, 0)
     check_against_oracle(prob, 0, *out)
+
+
+def test_split_set_merges_to_the_same_msa():
+    """Two halves aligned in separate contexts (each with the center), merged
+    with the elementwise maximum of their slot maxima, give the rows of the
+    single-context MSA (the sharded path's exchange, on one GPU)."""
+    b = binding()
+    from seqgen import split_sequences
+    letters, offsets, w, alph, M = workload("plain_protein_200", n=60, seed=13)
+    center = 17
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        b.msa_align_to_center(h, center)
+        full, W = b.msa_merge_gaps(h)
+    seqs = split_sequences(letters, offsets)
+    parts, Gs = [], []
+    for lo, hi in ((0, 31), (31, 60)):
+        sub = seqs[lo:hi] + [seqs[center]]
+        sl, so = pack_sequences(sub)
+        parts.append((lo, hi, sl, so))
+        with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+            b.msa_load(h, sl, so)
+            b.msa_align_to_center(h, len(sub) - 1)
+            Gs.append(b.msa_insert_maxima(h))
+    G = np.maximum(Gs[0], Gs[1])
+    for lo, hi, sl, so in parts:
+        with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+            b.msa_load(h, sl, so)
+            b.msa_align_to_center(h, hi - lo)
+            rows, W2 = b.msa_merge_gaps_with(h, G)
+            with pytest.raises(b.MSAError):
+                b.msa_merge_gaps_with(h, np.zeros_like(G) if G.any() else G - 1)
+        assert W2 == W and (rows[:hi - lo] == full[lo:hi]).all()
