@@ -190,6 +190,21 @@ int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
 // length Lq that stays below the overflow guard.
 int sat_thresh(msa_ctx *ctx) { return ctx->sat_limit - ctx->smax - ctx->o; }
 
+// int16 lanes hold every value of the alignment to a center of length Lc:
+// H <= Lc * smax, and the biased P = H + s + o never passes Lc * smax + smax + o.
+static bool codes_packed(msa_ctx *ctx, int Lc) {
+  if (ctx->precision == MSA_INT32 || ctx->smin + ctx->o < 0) return false;
+  const long long top = (long long)Lc * std::max(ctx->smax, 0) + std::max(ctx->smax, 0) + ctx->o;
+  return top <= std::min(ctx->sat_limit, 32767);
+}
+
+// group size of the alignment kernel for this set and a center of length Lc
+static int align_group(msa_ctx *ctx, int Lc, bool packed) {
+  double total = 0.0;
+  for (int L : ctx->len_sorted) total += L;
+  return codes_group(Lc, packed, ctx->K, ctx->n, ctx->n ? total / ctx->n : 0.0, ctx->maxlen);
+}
+
 bool use_packed(msa_ctx *ctx, int Lq) {
   if (ctx->precision == MSA_INT32 || ctx->smin + ctx->o < 0) return false;
   if (ctx->precision == MSA_INT16) return true;
@@ -694,7 +709,8 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   ctx->aligned = ctx->merged = false;
   ctx->center = center;
   ctx->Lc = Lc;
-  const int R = kCodesR, G = codes_group(Lc);
+  const bool packed = codes_packed(ctx, Lc);
+  const int R = kCodesR, G = align_group(ctx, Lc, packed);
   const int nblk = (Lc + R - 1) / R;
   const int npass = (Lc + G * R - 1) / (G * R);
   const size_t row = (size_t)Lc + 1;
@@ -739,7 +755,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   const SeqSet ss = seqset(ctx);
   const Scoring sc = scoring(ctx);
   const int smem = codes_smem_bytes(ctx->K, npass * G * R);
-  const int grid = codes_grid(G, smem);
+  const int grid = codes_grid(G, packed, smem);
   if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
   float ms_dp = 0.f, ms_tb = 0.f;
   int64_t cells = 0;
@@ -759,7 +775,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
     // offsets inside the batch are relative to the batch start
-    CK((++ctx->launches, launch_codes)(G, ss, sc, job, grid, ctx->st));
+    CK((++ctx->launches, launch_codes)(G, packed, ss, sc, job, grid, ctx->st));
     stage_end(ctx, ST_ALIGN);
     stage_begin(ctx, ST_TRACE);
     CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
@@ -803,26 +819,34 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
   if (!ctx->aligned) return fail(ctx, MSA_ESTATE, "no alignment yet");
   if (seq < 0 || seq >= ctx->n) return fail(ctx, MSA_EINVAL, "sequence index out of range");
   TRY(set_device(ctx));
-  // recompute the codes of this one subject into a private buffer
+  // Recompute the codes of this one subject into a private buffer.  On the
+  // packed path a subject at an odd sorted position is recomputed in the
+  // high lane, beside the next one, so both lanes are open to inspection.
   const int ks = ctx->inv[seq], kc = ctx->inv[ctx->center];
   const int Lc = ctx->Lc, Ls = ctx->len_sorted[ks];
-  const int R = kCodesR, G = codes_group(Lc), nblk = (Lc + R - 1) / R, npass = (Lc + G * R - 1) / (G * R);
+  const bool packed = codes_packed(ctx, Lc);
+  const int R = kCodesR, G = align_group(ctx, Lc, packed), nblk = (Lc + R - 1) / R;
+  const int npass = (Lc + G * R - 1) / (G * R);
+  const bool high = packed && (ks & 1) && ks + 1 < ctx->n;
+  const int se = high ? ks + 2 : ks + 1;
   const size_t bytes = (size_t)nblk * Ls * 8;
-  DevBuf cb, ob, bb, ib, oc, sg, sc_;
-  auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb, &ib, &oc, &sg, &sc_}) if (b->p) cudaFree(b->p); };
+  const size_t bytes_all = high ? bytes + (size_t)nblk * ctx->len_sorted[ks + 1] * 8 : bytes;
+  DevBuf cb, ob, bb;
+  auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb}) if (b->p) cudaFree(b->p); };
   int rc = [&]() -> int {
-    TRY(ensure(ctx, cb, bytes));
-    TRY(ensure(ctx, ob, sizeof(int64_t)));
-    TRY(ensure(ctx, bb, sizeof(int32_t) * 3));
-    CK(cudaMemsetAsync(ob.p, 0, sizeof(int64_t), ctx->st));
+    TRY(ensure(ctx, cb, bytes_all));
+    TRY(ensure(ctx, ob, 2 * sizeof(int64_t)));
+    TRY(ensure(ctx, bb, sizeof(int32_t) * 6));
+    const int64_t offs[2] = {0, (int64_t)bytes};
+    CK(cudaMemcpyAsync(ob.p, offs, sizeof(offs), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
     const int smem = codes_smem_bytes(ctx->K, npass * G * R);
     const int grid = 1;
-    if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, smem) * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
+    if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, packed, smem) * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
     CodesJob job;
     job.center = kc;
     job.sb = ks;
-    job.se = ks + 1;
+    job.se = se;
     job.code_off = P<int64_t>(ob);
     job.codes = P<uint8_t>(cb);
     job.best = P<int32_t>(bb);
@@ -830,14 +854,14 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     job.counter = ctx->dcounter;
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
-    CK((++ctx->launches, launch_codes)(G, seqset(ctx), scoring(ctx), job, grid, ctx->st));
-    std::vector<uint8_t> packed(bytes), out((size_t)Lc * Ls);
-    CK(cudaMemcpyAsync(packed.data(), cb.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
+    CK((++ctx->launches, launch_codes)(G, packed, seqset(ctx), scoring(ctx), job, grid, ctx->st));
+    std::vector<uint8_t> raw(bytes), out((size_t)Lc * Ls);
+    CK(cudaMemcpyAsync(raw.data(), cb.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     for (int i = 0; i < Lc; ++i)
       for (int j = 0; j < Ls; ++j) {
         const size_t at = ((size_t)(i >> 4) * Ls + j) * 8 + ((i & 15) >> 1);
-        out[(size_t)i * Ls + j] = (packed[at] >> ((i & 1) * 4)) & 15;
+        out[(size_t)i * Ls + j] = (raw[at] >> ((i & 1) * 4)) & 15;
       }
     CK(cudaMemcpyAsync(codes_out, out.data(), out.size(), cudaMemcpyDefault, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));

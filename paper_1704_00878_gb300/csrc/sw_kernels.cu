@@ -20,6 +20,7 @@
 // Packed mode keeps two subjects in the int16 halves of each register.
 #include "sw_kernels.cuh"
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -496,11 +497,21 @@ __global__ void __launch_bounds__(256) k_pairs(SeqSet ss, Scoring sc, PairJob jo
 }
 
 // ------------------------------------------------------------ codes
-// One pass of 32*16 center rows against one subject, int32 cells, writing
+// One pass of G*16 center rows against one subject, int32 cells, writing
 // the 4-bit traceback code of every cell: bits 0-1 the source of H (0 zero,
 // 1 diagonal, 2 F, 3 E; ties in that order), bit 2 "E extended", bit 3 "F
 // extended" (extension only when strictly better than opening).  Each lane
 // also keeps, per row, the first column reaching the row's maximum.
+//
+// Same biased form as the score kernels (profile s + o, E* = E + o,
+// F* = F + o).  Every comparison the codes need is the "a >= b" flag of a max
+// (__vibmax_s32 returns max(a, b) and whether a >= b):
+//   F* = vibmax(H_up, F*_up - e)   -> F extended   = !(H_up >= F*_up - e)
+//   T  = vibmax(P, F*)             -> P >= F*
+//   M  = vibmax(T, E*)             -> T >= E*   (source 1 / 2 / 3, in priority)
+//   H  = vibmax(0, M - o)          -> H == 0    (source 0, the stop)
+//   E*'= vibmax(H, E* - e)         -> E extended for the next column
+//   best row value = vibmax(best, H) -> a strictly larger H moves the column
 template <int G>
 __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int stride,
                                            const uint8_t *__restrict__ rs, int Ls, int Lw, int t,
@@ -512,8 +523,8 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
   int H[R], E[R], rb[R], rj[R];
   uint32_t emask = 0;
 #pragma unroll
-  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = -o; rb[r] = 0; rj[r] = 0; }
-  int hbot = 0, fbot = -o, htop_prev = 0;
+  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = 0; rb[r] = 0; rj[r] = 0; }
+  int hbot = 0, fbot = 0, htop_prev = 0;
   const uint32_t pc = (uint32_t)padc;
   uint32_t resv = pc;
   uint32_t cur = residue_at(rs, Ls, t, pc), nxt = residue_at(rs, Ls, G + t, pc);
@@ -533,7 +544,7 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
         const int2 v = scr_in[k];
         hin = v.x; fin = v.y;
       } else {
-        hin = 0; fin = -o;
+        hin = 0; fin = 0;
       }
     }
     resv = rin;
@@ -542,32 +553,30 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
     const int j = k - t;
     int hdiag = htop_prev;
     htop_prev = hin;
-    int xup = hin - o;
+    int hup = hin;
     int f = fin;
     uint32_t lo = 0, hi = 0;
     uint32_t enew = 0;
     Unroll<R>::run([&](auto ic) {
       constexpr int r = decltype(ic)::value;
-      const int s = Cell<false>::template score<r & 3>(pa.w[r >> 2], 0u);
-      const int dv = hdiag + s;
-      const int fe = f - e;
-      const int fv = max(fe, xup);
-      const uint32_t fext = fe > xup ? 1u : 0u;
-      const int ev = E[r];
-      const int hv = max(max(dv, 0), max(ev, fv));
-      const uint32_t src = hv == 0 ? 0u : (hv == dv ? 1u : (hv == fv ? 2u : 3u));
-      const uint32_t code = src | (((emask >> r) & 1u) << 2) | (fext << 3);
+      const int sp = Cell<false>::template score<r & 3>(pa.w[r >> 2], 0u);
+      bool pf, p1, p2, pz, pe, pk;
+      f = __vibmax_s32(hup, f - e, &pf);
+      const int tv = __vibmax_s32(hdiag + sp, f, &p1);
+      const int m = __vibmax_s32(tv, E[r], &p2);
+      const int hv = __vibmax_s32(0, m - o, &pz);
+      uint32_t src = p2 ? (p1 ? 1u : 2u) : 3u;
+      src = pz ? 0u : src;
+      const uint32_t code = src | (((emask >> r) & 1u) << 2) | ((pf ? 0u : 1u) << 3);
       if constexpr (r < 8) lo |= code << (4 * r);
       else hi |= code << (4 * (r - 8));
+      E[r] = __vibmax_s32(hv, E[r] - e, &pe);
+      enew |= (pe ? 0u : 1u) << r;
+      rb[r] = __vibmax_s32(rb[r], hv, &pk);
+      rj[r] = pk ? rj[r] : j;
       hdiag = H[r];
       H[r] = hv;
-      const int x = hv - o;
-      const int ee = ev - e;
-      E[r] = max(ee, x);
-      enew |= (ee > x ? 1u : 0u) << r;
-      if (hv > rb[r]) { rb[r] = hv; rj[r] = j; }
-      f = fv;
-      xup = x;
+      hup = hv;
     });
     emask = enew;
     hbot = H[R - 1];
@@ -598,8 +607,8 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
   const uint8_t *rc = ss.res + ss.pstart[job.center];
   for (int idx = threadIdx.x; idx < (K + 1) * rows; idx += NT) {
     const int r = idx / rows, i = idx - r * rows;
-    int v = MSA_PAD_SCORE;
-    if (r < K && i < Lc) v = sM[rc[i] * K + r];
+    int v = 0;  // padding: score -o
+    if (r < K && i < Lc) v = sM[rc[i] * K + r] + sc.o;
     smem[r * stride + i] = (int8_t)v;
   }
   __syncthreads();
@@ -643,6 +652,196 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
       b[0] = bv;
       b[1] = bv > 0 ? bi : 0;
       b[2] = bv > 0 ? bj : 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------ packed codes
+// Two length-adjacent subjects per group, A in the low int16 lane and B in the
+// high one, against the same G*16 center rows (the host takes this path only
+// while every cell value fits: Lc * smax + smax + o < 2^15 and s + o >= 0).
+// Every pair of values a flag compares is ordered (F* >= H_up, E* >= H_left,
+// M >= max(P, F*) >= P, a row's new best >= its old best), so each flag is one
+// 32-bit subtraction, which borrows across no lane, and a per-lane min with 1:
+//   F bit = min(F* - H_up, 1)          E bit = min(E* - H_left, 1)
+//   a     = min(M - P, 1)              (the diagonal is not a best source)
+//   x     = min(M - max(P, F*), 1)     (E is the only best source)
+//   src   = min(1 + a + x, H | 2H)    (0 for H = 0, else 1 + a + x)
+// and the first column reaching a row's best is max(column, d * j) with
+// d = min(best' - best, 1).
+// per-lane unsigned min of two int16 lanes: one instruction (the library's
+// three-operand form issues two)
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+template <int G>
+__device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int stride,
+                                            const uint8_t *__restrict__ rA, int LA,
+                                            const uint8_t *__restrict__ rB, int LB, int Lw, int t,
+                                            int base_lane, int blk, int nblk, int padc, int o,
+                                            int e, const int2 *__restrict__ scr_in,
+                                            int2 *__restrict__ scr_out,
+                                            uint2 *__restrict__ coutA, uint2 *__restrict__ coutB,
+                                            int (&bv)[2], int (&bi)[2], int (&bj)[2]) {
+  constexpr int R = kCodesR;
+  using C = Cell<true>;
+  constexpr uint32_t ONE = 0x00010001u;
+  const uint32_t negO = (uint32_t)C::splat(-o), negE = (uint32_t)C::splat(-e);
+  const uint32_t pc = (uint32_t)padc;
+  auto fetch = [&](int col) -> uint32_t {
+    return residue_at(rA, LA, col, pc) | (residue_at(rB, LB, col, pc) << 8);
+  };
+  uint32_t H[R], E[R], rb[R], rj[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = 0; rb[r] = 0; rj[r] = 0; }
+  uint32_t hbot = 0, fbot = 0, htop_prev = 0;
+  uint32_t resv = pc | (pc << 8);
+  uint32_t cur = fetch(t), nxt = fetch(G + t);
+  int2 sv0 = make_int2(0, 0), sv1 = make_int2(0, 0);
+  if (scr_in != nullptr) {
+    if (0 < Lw) sv0 = scr_in[0];
+    if (1 < Lw) sv1 = scr_in[1];
+  }
+  const int8_t *pb = prof + t * R;
+  const bool wr = blk < nblk;
+  const int steps = Lw + G - 1;
+  for (int k = 0; k < steps; ++k) {
+    const int kk = k & (G - 1);
+    if (kk == 0 && k > 0) { cur = nxt; nxt = fetch(k + G + t); }
+    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
+    uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
+    uint32_t hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
+    uint32_t fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    const int2 sv = sv0;
+    sv0 = sv1;
+    if (scr_in != nullptr && k + 2 < Lw) sv1 = scr_in[k + 2];
+    if (t == 0) {
+      rin = r0;
+      const bool above = scr_in != nullptr && k < Lw;
+      hin = above ? (uint32_t)sv.x : 0u;
+      fin = above ? (uint32_t)sv.y : 0u;
+    }
+    resv = rin;
+    ProfRow<R> pa, pq;
+    pa.load(pb + (int)(resv & 0xffu) * stride);
+    pq.load(pb + (int)(resv >> 8) * stride);
+    const int j = k - t;
+    const uint32_t jj = (uint32_t)j;  // multiplied only by d = 0 while j < 0
+    uint32_t hdiag = htop_prev;
+    htop_prev = hin;
+    uint32_t hup = hin, f = fin;
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    Unroll<R>::run([&](auto ic) {
+      constexpr int r = decltype(ic)::value;
+      const uint32_t p = hdiag + (uint32_t)C::template score<r & 3>(pa.w[r >> 2], pq.w[r >> 2]);
+      f = __viaddmax_s16x2(f, negE, hup);  // F*
+      const uint32_t bF = min_u16x2(f - hup, ONE);
+      const uint32_t tm = __vimax_s16x2_relu(p, f);
+      const uint32_t m = __vimax_s16x2_relu(tm, E[r]);
+      const uint32_t hn = __viaddmax_s16x2_relu(m, negO, 0u);
+      const uint32_t a = min_u16x2(m - p, ONE);
+      const uint32_t x = min_u16x2(m - tm, ONE);
+      // hn | hn << 1 is 0 for H = 0 and >= 3 otherwise (H < 2^15: nothing
+      // crosses into the other lane)
+      const uint32_t src = min_u16x2(a + x + ONE, hn | (hn << 1));
+      const uint32_t bE = min_u16x2(E[r] - H[r], ONE);
+      const uint32_t code = (bF << 3) + (bE << 2) + src;
+      acc[r >> 2] = (code << (4 * (r & 3))) + acc[r >> 2];
+      E[r] = __viaddmax_s16x2(E[r], negE, hn);  // E* of the next column
+      const uint32_t rbn = __vimax_s16x2_relu(rb[r], hn);
+      rj[r] = __vimax_s16x2_relu(rj[r], min_u16x2(rbn - rb[r], ONE) * jj);
+      rb[r] = rbn;
+      hdiag = H[r];
+      H[r] = hn;
+      hup = hn;
+    });
+    hbot = H[R - 1];
+    fbot = f;
+    if (wr && j >= 0) {
+      if (j < LA) coutA[j] = make_uint2(__byte_perm(acc[0], acc[1], 0x5410), __byte_perm(acc[2], acc[3], 0x5410));
+      if (j < LB) coutB[j] = make_uint2(__byte_perm(acc[0], acc[1], 0x7632), __byte_perm(acc[2], acc[3], 0x7632));
+    }
+    if (scr_out != nullptr && t == G - 1 && j >= 0 && j < Lw) scr_out[j] = make_int2((int)hbot, (int)fbot);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int va = C::lane0((int)rb[r]), vb = C::lane1((int)rb[r]);
+    if (va > bv[0]) { bv[0] = va; bi[0] = blk * R + r + 1; bj[0] = (int)(rj[r] & 0xffffu) + 1; }
+    if (vb > bv[1]) { bv[1] = vb; bi[1] = blk * R + r + 1; bj[1] = (int)(rj[r] >> 16) + 1; }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_codes2(SeqSet ss, Scoring sc, CodesJob job) {
+  constexpr int R = kCodesR, NT = 256, NG = NT / G, GPW = 32 / G;
+  extern __shared__ __align__(16) int8_t smem[];
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  const int K = sc.K, padc = K;
+  const int rows = job.npass * G * R;
+  const int stride = dround_up(rows, MSA_PROF_ALIGN);
+  for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = sc.M[i];
+  __syncthreads();
+  const int Lc = ss.len[job.center];
+  const uint8_t *rc = ss.res + ss.pstart[job.center];
+  for (int idx = threadIdx.x; idx < (K + 1) * rows; idx += NT) {
+    const int r = idx / rows, i = idx - r * rows;
+    int v = 0;  // padding: score -o
+    if (r < K && i < Lc) v = sM[rc[i] * K + r] + sc.o;
+    smem[r * stride + i] = (int8_t)v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, t = threadIdx.x % G, g = threadIdx.x / G;
+  const int base_lane = lane - t;
+  const int nblk = (Lc + R - 1) / R;
+  int2 *scr = job.scratch + ((size_t)blockIdx.x * NG + g) * 2 * job.scratch_cols;
+  const int nsub = job.se - job.sb, nitem = (nsub + 1) / 2;
+  for (;;) {
+    int x0 = 0;
+    if (lane == 0) x0 = (int)atomicAdd(job.counter, (unsigned long long)GPW);
+    x0 = __shfl_sync(MSA_FULL_MASK, x0, 0);
+    if (x0 >= nitem) break;
+    const int x = x0 + lane / G;
+    const bool valid = x < nitem;
+    const int ka = job.se - 1 - 2 * (valid ? x : 0);  // longest first
+    const int kb = ka - 1;
+    const bool hasb = valid && kb >= job.sb;
+    const int LA = valid ? ss.len[ka] : 0, LB = hasb ? ss.len[kb] : 0;
+    const uint8_t *rA = ss.res + ss.pstart[ka];
+    const uint8_t *rB = hasb ? ss.res + ss.pstart[kb] : rA;
+    uint2 *cA = valid ? reinterpret_cast<uint2 *>(job.codes + job.code_off[ka - job.sb]) : nullptr;
+    uint2 *cB = hasb ? reinterpret_cast<uint2 *>(job.codes + job.code_off[kb - job.sb]) : nullptr;
+    const int Lw = __reduce_max_sync(MSA_FULL_MASK, max(LA, LB));
+    int bv[2] = {0, 0}, bi[2] = {0, 0}, bj[2] = {0, 0};
+    for (int p = 0; p < job.npass; ++p) {
+      const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
+      int2 *sout = p + 1 < job.npass ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
+      const int blk = p * G + t;
+      codes_pass2<G>(smem + p * G * R, stride, rA, LA, rB, LB, Lw, t, base_lane, blk, nblk, padc,
+                     sc.o, sc.e, sin, sout, cA ? cA + (size_t)blk * LA : nullptr,
+                     cB ? cB + (size_t)blk * LB : nullptr, bv, bi, bj);
+      __syncwarp();
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      int v = bv[s2], bi2 = bi[s2], bj2 = bj[s2];
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) {
+        const int ov = __shfl_xor_sync(MSA_FULL_MASK, v, off);
+        const int oi = __shfl_xor_sync(MSA_FULL_MASK, bi2, off);
+        const int oj = __shfl_xor_sync(MSA_FULL_MASK, bj2, off);
+        const bool take = ov > v || (ov == v && (oi < bi2 || (oi == bi2 && oj < bj2)));
+        if (take) { v = ov; bi2 = oi; bj2 = oj; }
+      }
+      const int ks = s2 == 0 ? ka : kb;
+      if (t == 0 && (s2 == 0 ? valid : hasb)) {
+        int32_t *b = job.best + (size_t)(ks - job.sb) * 3;
+        b[0] = v;
+        b[1] = v > 0 ? bi2 : 0;
+        b[2] = v > 0 ? bj2 : 0;
+      }
     }
   }
 }
@@ -753,20 +952,40 @@ int codes_smem_bytes(int K, int rows_alloc) {
 }
 
 typedef void (*codes_fn)(SeqSet, Scoring, CodesJob);
-static codes_fn codes_kernel(int G) {
+static codes_fn codes_kernel(int G, bool packed) {
+  if (packed) return G == 8 ? k_codes2<8> : (G == 16 ? k_codes2<16> : (G == 32 ? k_codes2<32> : nullptr));
   return G == 8 ? k_codes<8> : (G == 16 ? k_codes<16> : (G == 32 ? k_codes<32> : nullptr));
 }
 
-int codes_group(int Lc) { return Lc <= 8 * kCodesR ? 8 : (Lc <= 16 * kCodesR ? 16 : 32); }
 
-int codes_grid(int G, int smem) {
-  codes_fn fn = codes_kernel(G);
+int codes_grid(int G, bool packed, int smem) {
+  codes_fn fn = codes_kernel(G, packed);
   return fn ? occupancy_grid((const void *)fn, 256, smem) : 0;
 }
 
-cudaError_t launch_codes(int G, const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
-                         cudaStream_t st) {
-  codes_fn fn = codes_kernel(G);
+// Group size for a center of length Lc.  A group of G lanes spends
+// npass * (L + G - 1) steps on a subject of length L (npass = ceil(Lc / 16G)),
+// and the groups share the resident warps, so the estimate is the larger of
+// the total steps spread over the warps and the longest subject's own steps.
+int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_len) {
+  int best_g = 32;
+  double best = 0.0;
+  for (int G : {32, 16, 8}) {
+    const int npass = (Lc + G * kCodesR - 1) / (G * kCodesR);
+    const int grid = codes_grid(G, packed, codes_smem_bytes(K, npass * G * kCodesR));
+    const double warps = (double)grid * 8;
+    const double units = packed ? (double)((n + 1) / 2) : (double)n;
+    const double tasks = std::ceil(units / (32 / G));
+    const double mean_steps = npass * (mean_len + G - 1), max_steps = npass * (max_len + G - 1.0);
+    const double est = std::max(tasks * mean_steps / warps, max_steps);
+    if (G == 32 || est < best) { best = est; best_g = G; }
+  }
+  return best_g;
+}
+
+cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc, const CodesJob &job,
+                         int grid, cudaStream_t st) {
+  codes_fn fn = codes_kernel(G, packed);
   if (!fn) return cudaErrorInvalidValue;
   const int smem = codes_smem_bytes(sc.K, job.npass * G * kCodesR);
   if (smem > 48 * 1024)

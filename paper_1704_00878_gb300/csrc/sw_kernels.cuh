@@ -45,7 +45,8 @@ struct PairJob {
   int2 *scratch; int scratch_cols;
 };
 
-// Alignment to the center with 4-bit traceback codes (int32 cells).
+// Alignment to the center with 4-bit traceback codes (int32 cells, or two
+// subjects per group in the int16 lanes when packed).
 struct CodesJob {
   int center;                     // sorted index
   int sb, se;                     // subjects: sorted indices [sb, se), longest first
@@ -74,12 +75,13 @@ int pairs_grid(int G);
 int pairs_rows(int G);
 
 // G = threads per subject group (8, 16 or 32; codes_group picks it from the
-// center length); 16 center rows per thread.
-cudaError_t launch_codes(int G, const SeqSet &ss, const Scoring &sc, const CodesJob &job, int grid,
-                         cudaStream_t st);
+// center length and the subject lengths); 16 center rows per thread.  packed: each group carries two
+// subjects in int16 lanes (the caller checks that every cell value fits).
+cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc, const CodesJob &job,
+                         int grid, cudaStream_t st);
 int codes_smem_bytes(int K, int rows_alloc);
-int codes_grid(int G, int smem);
-int codes_group(int Lc);
+int codes_grid(int G, bool packed, int smem);
+int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_len);
 constexpr int kCodesR = 16;
 constexpr int kPairsR = 16;
 constexpr int kCenterThreads = 256;

@@ -93,12 +93,16 @@ def test_sampled_center():
 
 # ------------------------------------------------------------- alignment + merge
 
-def test_codes_and_best_cells_bitexact():
+@pytest.mark.parametrize("precision", [0, 2])
+def test_codes_and_best_cells_bitexact(precision):
+    """Codes of every cell: int16 lanes carrying two subjects (automatic
+    precision; odd sorted positions are recomputed in the high lane) and
+    int32 cells."""
     b = binding()
-    letters, offsets, w, alph, M = workload("plain_protein_200", n=12, seed=2)
+    letters, offsets, w, alph, M = workload("plain_protein_200", n=13, seed=2)
     prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
     center = 4
-    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+    with make_ctx(alph, M, w.gap_open, w.gap_extend, precision=precision) as h:
         b.msa_load(h, letters, offsets)
         b.msa_align_to_center(h, center)
         seg, _, _ = b.msa_alignment_info(h)
