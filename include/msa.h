@@ -127,6 +127,8 @@ int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int
  *   them (nref x n alignments instead of n^2/2) and its argmin; refs unused;
  *   sum_dist_out gets the winner's exact row sum.
  * FIRST: 0.
+ * The exact modes run their length-bucketed kernels as one CUDA graph
+ * (captured on a stream private to the context, launched on its stream).
  * center_out: host int64; sum_dist_out (nullable, host int64): the winning
  * row sum (EXACT modes), else 0.  ESTATE for LEARNED without a selector. */
 int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,

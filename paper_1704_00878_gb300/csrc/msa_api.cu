@@ -216,13 +216,25 @@ struct CenterClass {
   int variant, ub, ue;  // item units [ub, ue): query pairs (paired) or queries
 };
 
-int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
-                 const std::vector<int> &qlen, float &center_ms, int sub_off = 0, int sub_n = -1) {
+// A class launch planned on the host: its slice of the item prefix, its
+// pass count, shared memory and grid.
+struct ClassPlan {
+  CenterClass cc;
+  int nq_list, npass, smem, grid;
+  size_t prefix_off;  // into the concatenated prefix of all planned classes
+  int64_t n_items;
+};
+
+ClassPlan plan_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
+                     const std::vector<int> &qlen, int sub_n, std::vector<int64_t> &prefix_all) {
   const CenterVariant &cv = kCenterVariants[cc.variant];
   const int NG = kCenterThreads / cv.G;
-  if (sub_n < 0) sub_n = ctx->n;
   const int n = mode == 0 ? ctx->n : sub_n;
-  std::vector<int64_t> prefix(cc.ue - cc.ub + 1, 0);
+  ClassPlan pl;
+  pl.cc = cc;
+  pl.nq_list = nq_list;
+  pl.prefix_off = prefix_all.size();
+  prefix_all.push_back(0);
   int maxlen = 0;
   for (int u = cc.ub; u < cc.ue; ++u) {
     int64_t items;
@@ -236,29 +248,30 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
       maxlen = std::max(maxlen, qlen[u]);
       items = mode == 0 ? (n - u + spi - 1) / spi : (n + spi - 1) / spi;
     }
-    prefix[u - cc.ub + 1] = prefix[u - cc.ub] + items;
+    prefix_all.push_back(prefix_all.back() + items);
   }
+  pl.n_items = prefix_all.back();
   const int rows = cv.G * cv.R;
-  const int npass = (maxlen + rows - 1) / rows;
-  TRY(ensure(ctx, ctx->prefix, sizeof(int64_t) * prefix.size()));
-  CK(cudaMemcpyAsync(ctx->prefix.p, prefix.data(), sizeof(int64_t) * prefix.size(),
-                     cudaMemcpyHostToDevice, ctx->st));
-  const int smem = center_smem_bytes(cc.variant, ctx->K, npass * rows);
-  const int grid = center_grid(cc.variant, smem);
-  if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * NG * 2 * ctx->maxlen * sizeof(int2)));
-  CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+  pl.npass = (maxlen + rows - 1) / rows;
+  pl.smem = center_smem_bytes(cc.variant, ctx->K, pl.npass * rows);
+  pl.grid = center_grid(cc.variant, pl.smem);
+  return pl;
+}
+
+CenterJob class_job(msa_ctx *ctx, int mode, const ClassPlan &pl, int sub_off, int sub_n,
+                    unsigned long long *counter) {
   CenterJob job;
   job.mode = mode;
   job.qlist = P<int32_t>(ctx->qlist);
-  job.nq = nq_list;
+  job.nq = pl.nq_list;
   job.sub_off = sub_off;
   job.sub_n = sub_n;
-  job.qb = cc.ub;
-  job.qe = cc.ue;
-  job.prefix = P<int64_t>(ctx->prefix);
-  job.n_items = prefix.back();
-  job.npass = npass;
-  job.counter = ctx->dcounter;
+  job.qb = pl.cc.ub;
+  job.qe = pl.cc.ue;
+  job.prefix = P<int64_t>(ctx->prefix) + pl.prefix_off;
+  job.n_items = pl.n_items;
+  job.npass = pl.npass;
+  job.counter = counter;
   job.pairsum = P<unsigned long long>(ctx->pairsum);
   job.self = P<int32_t>(ctx->self);
   job.sat_thresh = sat_thresh(ctx);
@@ -268,13 +281,80 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
   job.err = ctx->derr;
   job.scratch = P<int2>(ctx->scratch);
   job.scratch_cols = ctx->maxlen;
+  return job;
+}
+
+// Upload the plans' prefixes and size the scratch rows of multi-pass
+// classes (all classes run in stream order, so they share one scratch).
+int stage_plans(msa_ctx *ctx, const std::vector<ClassPlan> &plans,
+                const std::vector<int64_t> &prefix_all) {
+  size_t scratch = 0;
+  for (const ClassPlan &pl : plans)
+    if (pl.npass > 1)
+      scratch = std::max(scratch, (size_t)pl.grid * (kCenterThreads / kCenterVariants[pl.cc.variant].G) *
+                                      2 * ctx->maxlen * sizeof(int2));
+  if (scratch) TRY(ensure(ctx, ctx->scratch, scratch));
+  TRY(ensure(ctx, ctx->prefix, sizeof(int64_t) * prefix_all.size()));
+  TRY(ensure(ctx, ctx->counters, sizeof(unsigned long long) * std::max<size_t>(plans.size(), 1)));
+  CK(cudaMemcpyAsync(ctx->prefix.p, prefix_all.data(), sizeof(int64_t) * prefix_all.size(),
+                     cudaMemcpyHostToDevice, ctx->st));
+  return MSA_OK;
+}
+
+// One class, timed on its own (the autotuner's measurement).
+int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
+                 const std::vector<int> &qlen, float &center_ms, int sub_off = 0, int sub_n = -1) {
+  if (sub_n < 0) sub_n = ctx->n;
+  std::vector<int64_t> prefix_all;
+  const ClassPlan pl = plan_class(ctx, mode, nq_list, cc, qlen, sub_n, prefix_all);
+  TRY(stage_plans(ctx, {pl}, prefix_all));
+  CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->st));
+  const CenterJob job = class_job(ctx, mode, pl, sub_off, sub_n, P<unsigned long long>(ctx->counters));
   stage_begin(ctx, ST_CENTER_K);
-  CK((++ctx->launches, launch_center)(cc.variant, seqset(ctx), scoring(ctx), job, grid, ctx->st));
+  ++ctx->launches;
+  CK(launch_center(cc.variant, seqset(ctx), scoring(ctx), job, pl.grid, ctx->st, true));
   stage_end(ctx, ST_CENTER_K);
-  // the prefix buffer is reused by the next class: wait for this one
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_CENTER_K);
   center_ms += ctx->stage_ms[ST_CENTER_K];
+  return MSA_OK;
+}
+
+// All classes of a center selection as one CUDA graph: the per-class
+// counters are cleared by the graph's first node and the class kernels
+// follow one another in stream order, so the whole length-bucketed set is a
+// single submission with no host round trip between buckets.  The graph is
+// captured on the context's private capture stream and launched on its
+// stream (which may be the legacy default stream).
+int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, int sub_off,
+                 int sub_n, cudaGraphExec_t *exec_out) {
+  const SeqSet ss = seqset(ctx);
+  const Scoring sc = scoring(ctx);
+  std::vector<int> top(kNumCenterVariants, 0);
+  for (const ClassPlan &pl : plans) top[pl.cc.variant] = std::max(top[pl.cc.variant], pl.smem);
+  for (int v = 0; v < kNumCenterVariants; ++v)
+    if (top[v] > 0) CK(center_allow_smem(v, top[v]));
+  unsigned long long *cnt = P<unsigned long long>(ctx->counters);
+  CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * plans.size(), ctx->cap_st);
+  for (size_t c = 0; c < plans.size() && e == cudaSuccess; ++c) {
+    const CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c);
+    e = launch_center(plans[c].cc.variant, ss, sc, job, plans[c].grid, ctx->cap_st, false);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_st, &graph);
+  if (e == cudaSuccess) e = e_end;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  CK(e);
+  ctx->launches += (int64_t)plans.size();
+  stage_begin(ctx, ST_CENTER_K);
+  e = cudaGraphLaunch(exec, ctx->st);
+  stage_end(ctx, ST_CENTER_K);
+  if (e != cudaSuccess) cudaGraphExecDestroy(exec);
+  CK(e);
+  *exec_out = exec;  // destroyed by the caller once the stream has drained
   return MSA_OK;
 }
 
@@ -330,12 +410,21 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     classes.push_back({v, x, xe});
     x = xe;
   }
-  float center_ms = 0.f;
+  std::vector<ClassPlan> plans;
+  std::vector<int64_t> prefix_all;
   for (const CenterClass &cc : classes) {
     // a paired class may not pair across the packed / int32 boundary
     const int nq_list = kCenterVariants[cc.variant].paired ? x1 : nq;
-    TRY(launch_class(ctx, mode, nq_list, cc, qlen, center_ms));
+    plans.push_back(plan_class(ctx, mode, nq_list, cc, qlen, n, prefix_all));
   }
+  TRY(stage_plans(ctx, plans, prefix_all));
+  cudaGraphExec_t exec = nullptr;
+  TRY(launch_plans(ctx, mode, plans, 0, n, &exec));
+  const cudaError_t e_sync = cudaStreamSynchronize(ctx->st);
+  cudaGraphExecDestroy(exec);
+  CK(e_sync);
+  stage_collect(ctx, ST_CENTER_K);
+  const float center_ms = ctx->stage_ms[ST_CENTER_K];
   int64_t cells = 0;
   if (mode == 0) {
     for (int x = 0; x < nq; ++x) cells += (int64_t)ctx->len_sorted[x] * suffix[x];
@@ -491,6 +580,7 @@ int msa_create(msa_ctx **out, const msa_params *p, void *cuda_stream) {
     CK(cudaMalloc(&ctx->dSymLut, 256));
     CK(cudaMemcpy(ctx->dSymLut, sym, 256, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->dcounter, sizeof(unsigned long long)));
+    CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
     CK(cudaMalloc(&ctx->derr, 2 * sizeof(unsigned)));
     CK(cudaMemset(ctx->derr, 0, 2 * sizeof(unsigned)));
     CK(cudaMalloc(&ctx->dsmall, 8 * sizeof(long long)));
@@ -518,7 +608,7 @@ void msa_destroy(msa_ctx *ctx) {
                     &ctx->part_val, &ctx->part_idx, &ctx->pairs, &ctx->pair_dst,
                     &ctx->pair_out, &ctx->ins, &ctx->occ, &ctx->seg, &ctx->score,
                     &ctx->codes, &ctx->code_off, &ctx->best, &ctx->G, &ctx->off, &ctx->msa,
-                    &ctx->counts, &ctx->scratch};
+                    &ctx->counts, &ctx->scratch, &ctx->counters};
   for (DevBuf *b : bufs)
     if (b->p) cudaFree(b->p);
   cudaFree(ctx->dM);
@@ -526,6 +616,7 @@ void msa_destroy(msa_ctx *ctx) {
   cudaFree(ctx->dLut);
   cudaFree(ctx->dSymLut);
   cudaFree(ctx->dcounter);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   cudaFree(ctx->derr);
   cudaFree(ctx->dsmall);
   for (auto &ev : ctx->ev)

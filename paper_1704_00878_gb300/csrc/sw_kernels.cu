@@ -911,14 +911,23 @@ int center_grid(int variant, int smem) {
   return occupancy_grid((const void *)fn, kCenterThreads, smem);
 }
 
+cudaError_t center_allow_smem(int variant, int smem) {
+  center_fn fn = center_kernel(variant);
+  if (!fn) return cudaErrorInvalidValue;
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_center(int variant, const SeqSet &ss, const Scoring &sc, const CenterJob &job,
-                          int grid, cudaStream_t st) {
+                          int grid, cudaStream_t st, bool set_smem) {
   center_fn fn = center_kernel(variant);
   if (!fn) return cudaErrorInvalidValue;
   const CenterVariant &v = kCenterVariants[variant];
   const int smem = center_smem_bytes(variant, sc.K, job.npass * v.G * v.R);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (set_smem) {
+    const cudaError_t e = center_allow_smem(variant, smem);
+    if (e != cudaSuccess) return e;
+  }
   fn<<<grid, kCenterThreads, smem, st>>>(ss, sc, job);
   return cudaGetLastError();
 }

@@ -65,8 +65,12 @@ extern const CenterVariant kCenterVariants[];
 extern const int kNumCenterVariants;
 
 int center_smem_bytes(int variant, int K, int rows_alloc);
+// set_smem = false: the caller has already raised the kernel's dynamic
+// shared-memory limit with center_allow_smem (required while a stream is
+// being captured into a graph).
 cudaError_t launch_center(int variant, const SeqSet &ss, const Scoring &sc, const CenterJob &job,
-                          int grid, cudaStream_t st);
+                          int grid, cudaStream_t st, bool set_smem = true);
+cudaError_t center_allow_smem(int variant, int smem);
 int center_grid(int variant, int smem);
 
 cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJob &job,

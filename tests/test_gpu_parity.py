@@ -63,6 +63,25 @@ def test_exact_center_plain_protein_200():
     assert c == oc and s == orow[oc]
 
 
+def test_exact_center_graph_on_any_stream():
+    """The length-bucketed center kernels run as one captured CUDA graph
+    launched on the context's stream: on the legacy default stream and on a
+    side stream, twice in a row on one context, the row sums are the
+    oracle's."""
+    import torch
+    b = binding()
+    letters, offsets, w, alph, M = workload("batched_uneven_10k", n=150, seed=9)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    oc, orow = oracle.exact_center(prob)
+    for stream in (None, torch.cuda.Stream()):
+        with make_ctx(alph, M, w.gap_open, w.gap_extend, stream=stream) as h:
+            b.msa_load(h, letters, offsets)
+            for _ in range(2):
+                c, s = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+                assert c == oc and s == orow[oc]
+                assert (b.msa_center_rowsums(h) == orow).all()
+
+
 @pytest.mark.parametrize("precision,sat", [(2, 0), (1, 0), (1, 300)])
 def test_exact_center_precisions_and_overflow_recheck(precision, sat):
     """int32 cells, packed int16 cells, and packed cells with a low overflow
