@@ -89,6 +89,7 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int w) {
 #define MSA_DERR_LETTER   1u   // a letter outside the alphabet
 #define MSA_DERR_TRACE    2u   // inconsistent traceback codes
 #define MSA_DERR_OVERFLOW 4u   // overflow list full
+#define MSA_DERR_TIMEOUT_TC 8u // a tensor-core convolution gave up waiting on an mbarrier
 
 static inline int round_up_int(int x, int m) { return (x + m - 1) / m * m; }
 static inline int64_t round_up_i64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -100,6 +100,8 @@ int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector
 int selector_center(msa_ctx *ctx, int64_t *center_out);
 int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *sum_out);
 int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted);
+// the device error word -> an MSA_E* code (synchronises the stream)
+int check_derr(msa_ctx *ctx);
 
 }  // namespace msa_detail
 

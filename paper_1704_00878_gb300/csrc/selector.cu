@@ -150,13 +150,22 @@ int build_batch(msa_ctx *ctx, Selector *s, const std::vector<int32_t> &seqs, net
   return MSA_OK;
 }
 
+// One convolution: the tcgen05 kernel where it has the shape, else mma.sync.
+cudaError_t conv(msa_ctx *ctx, int cin, int cout, int mode, const bf16 *x, const bf16 *w,
+                 const float *bias, const int32_t *rowseq, const bf16 *prev, void *y, int T) {
+  ++ctx->launches;
+  if (net::conv_tc_supported(cin, cout, mode))
+    return net::conv_tc(cin, cout, mode, x, w, bias, rowseq, prev, y, T, ctx->derr, ctx->st);
+  return net::conv(cin, cout, mode, x, w, bias, rowseq, prev, y, T, ctx->st);
+}
+
 int forward(msa_ctx *ctx, Selector *s, const net::Batch &b) {
   const float *p = P<float>(s->params);
   const int T = b.T;
-  CK((++ctx->launches, net::conv)(net::KP, net::WD, 0, P<bf16>(s->x0), P<bf16>(s->w1t), p + net::B1_OFF, b.rowseq, nullptr, s->a1.p, T, ctx->st));
-  CK((++ctx->launches, net::conv)(net::WD, net::WD, 0, P<bf16>(s->a1), P<bf16>(s->w2t), p + net::B2_OFF, b.rowseq, nullptr, s->a2.p, T, ctx->st));
-  CK((++ctx->launches, net::conv)(net::WD, net::WD, 0, P<bf16>(s->a2), P<bf16>(s->w3t), p + net::B3_OFF, b.rowseq, nullptr, s->a3.p, T, ctx->st));
-  CK((++ctx->launches, net::conv)(net::WD, net::DIM, 1, P<bf16>(s->a3), P<bf16>(s->w4t), p + net::B4_OFF, b.rowseq, nullptr, s->y4.p, T, ctx->st));
+  CK(conv(ctx, net::KP, net::WD, 0, P<bf16>(s->x0), P<bf16>(s->w1t), p + net::B1_OFF, b.rowseq, nullptr, s->a1.p, T));
+  CK(conv(ctx, net::WD, net::WD, 0, P<bf16>(s->a1), P<bf16>(s->w2t), p + net::B2_OFF, b.rowseq, nullptr, s->a2.p, T));
+  CK(conv(ctx, net::WD, net::WD, 0, P<bf16>(s->a2), P<bf16>(s->w3t), p + net::B3_OFF, b.rowseq, nullptr, s->a3.p, T));
+  CK(conv(ctx, net::WD, net::DIM, 1, P<bf16>(s->a3), P<bf16>(s->w4t), p + net::B4_OFF, b.rowseq, nullptr, s->y4.p, T));
   CK((++ctx->launches, net::pool)(b, P<float>(s->y4), P<float>(s->emb), ctx->st));
   return MSA_OK;
 }
@@ -179,15 +188,15 @@ int forward_backward(msa_ctx *ctx, Selector *s, const net::Batch &b, int npairs)
   // layer 4 (linear)
   CK((++ctx->launches, net::wgrad)(net::WD, net::DIM, P<bf16>(s->a3), P<bf16>(s->dy4), g + net::W4_OFF, T, ctx->st));
   CK((++ctx->launches, net::colsum)(net::DIM, P<bf16>(s->dy4), g + net::B4_OFF, T, ctx->st));
-  CK((++ctx->launches, net::conv)(net::DIM, net::WD, 2, P<bf16>(s->dy4), P<bf16>(s->w4n), nullptr, b.rowseq, P<bf16>(s->a3), s->dz3.p, T, ctx->st));
+  CK(conv(ctx, net::DIM, net::WD, 2, P<bf16>(s->dy4), P<bf16>(s->w4n), nullptr, b.rowseq, P<bf16>(s->a3), s->dz3.p, T));
   // layer 3
   CK((++ctx->launches, net::wgrad)(net::WD, net::WD, P<bf16>(s->a2), P<bf16>(s->dz3), g + net::W3_OFF, T, ctx->st));
   CK((++ctx->launches, net::colsum)(net::WD, P<bf16>(s->dz3), g + net::B3_OFF, T, ctx->st));
-  CK((++ctx->launches, net::conv)(net::WD, net::WD, 2, P<bf16>(s->dz3), P<bf16>(s->w3n), nullptr, b.rowseq, P<bf16>(s->a2), s->dz2.p, T, ctx->st));
+  CK(conv(ctx, net::WD, net::WD, 2, P<bf16>(s->dz3), P<bf16>(s->w3n), nullptr, b.rowseq, P<bf16>(s->a2), s->dz2.p, T));
   // layer 2
   CK((++ctx->launches, net::wgrad)(net::WD, net::WD, P<bf16>(s->a1), P<bf16>(s->dz2), g + net::W2_OFF, T, ctx->st));
   CK((++ctx->launches, net::colsum)(net::WD, P<bf16>(s->dz2), g + net::B2_OFF, T, ctx->st));
-  CK((++ctx->launches, net::conv)(net::WD, net::WD, 2, P<bf16>(s->dz2), P<bf16>(s->w2n), nullptr, b.rowseq, P<bf16>(s->a1), s->dz1.p, T, ctx->st));
+  CK(conv(ctx, net::WD, net::WD, 2, P<bf16>(s->dz2), P<bf16>(s->w2n), nullptr, b.rowseq, P<bf16>(s->a1), s->dz1.p, T));
   // layer 1 (one-hot input: no data gradient)
   CK((++ctx->launches, net::wgrad)(net::KP, net::WD, P<bf16>(s->x0), P<bf16>(s->dz1), g + net::W1_OFF, T, ctx->st));
   CK((++ctx->launches, net::colsum)(net::WD, P<bf16>(s->dz1), g + net::B1_OFF, T, ctx->st));
@@ -306,6 +315,7 @@ int selector_center(msa_ctx *ctx, int64_t *center_out) {
   CK(cudaMemcpyAsync(&k, P<char>(s->small) + 768, sizeof k, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_SELECTOR);
+  TRY(check_derr(ctx));
   if (k < 0 || k >= ctx->n) return fail(ctx, MSA_ECUDA, "selector center out of range");
   *center_out = ctx->perm[k];
   return MSA_OK;
@@ -329,6 +339,7 @@ int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *s
   CK(cudaMemcpyAsync(dist.data(), s->dist.p, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_SELECTOR);
+  TRY(check_derr(ctx));
   std::vector<int32_t> idx(n);
   std::iota(idx.begin(), idx.end(), 0);
   std::partial_sort(idx.begin(), idx.begin() + k, idx.end(), [&](int32_t a, int32_t b) {
@@ -362,7 +373,7 @@ int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *s
   }
   *center_out = ctx->perm[bestq];
   if (sum_out) *sum_out = best;
-  return MSA_OK;
+  return check_derr(ctx);
 }
 
 }  // namespace msa_detail
@@ -426,7 +437,7 @@ int msa_selector_grad(msa_ctx *ctx, const int64_t *pairs, const float *targets, 
     CK(cudaMemcpyAsync(grad_out, s->grads.p, sizeof(float) * net::N_PARAMS, cudaMemcpyDefault, ctx->st));
   if (loss_out) CK(cudaMemcpyAsync(loss_out, s->loss.p, sizeof(float), cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  return MSA_OK;
+  return check_derr(ctx);
 }
 
 int msa_selector_train(msa_ctx *ctx, const int64_t *pairs, const float *targets, int64_t npairs,
@@ -495,7 +506,7 @@ int msa_selector_train(msa_ctx *ctx, const int64_t *pairs, const float *targets,
   stage_end(ctx, ST_SELECTOR);
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_SELECTOR);
-  return MSA_OK;
+  return check_derr(ctx);
 }
 
 int msa_selector_embed(msa_ctx *ctx, float *emb_out) {
@@ -512,7 +523,7 @@ int msa_selector_embed(msa_ctx *ctx, float *emb_out) {
     memcpy(&o[(size_t)ctx->perm[k] * net::DIM], &h[(size_t)k * net::DIM], sizeof(float) * net::DIM);
   CK(cudaMemcpyAsync(emb_out, o.data(), sizeof(float) * o.size(), cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  return MSA_OK;
+  return check_derr(ctx);
 }
 
 int msa_save_selector(msa_ctx *ctx, const char *path) {

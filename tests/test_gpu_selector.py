@@ -58,6 +58,24 @@ def test_embeddings_loss_and_gradients_match_oracle():
         at += size
 
 
+def test_embeddings_many_tiles_sampled():
+    """Enough rows that every persistent tensor-core CTA walks many 128-row
+    tiles through both of its input buffers: sampled embeddings against the
+    fp64 oracle."""
+    b = binding()
+    letters, offsets, w, alph, M = workload("learned_center_50k", n=1500, seed=9)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        b.msa_selector_init(h, seed=13)
+        params = net.unflatten(b.msa_selector_params(h).astype(np.float64))
+        emb = b.msa_selector_embed(h)
+    pick = np.random.default_rng(4).choice(prob.n, size=24, replace=False)
+    pick[:2] = [0, prob.n - 1]
+    oemb = np.stack([net.forward(params, prob.seq(int(i)))[0] for i in pick])
+    assert rel_err(emb[pick], oemb) < EMB_TOL
+
+
 def test_one_adam_step_matches_oracle():
     b = binding()
     letters, offsets, w, alph, M, prob, seqs = setup_small(seed=3)
