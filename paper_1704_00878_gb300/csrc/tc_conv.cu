@@ -1,25 +1,32 @@
-// tc_conv.cu -- the selector's 9-tap convolutions with 64 or 128 input
-// channels as implicit GEMMs on the fifth-generation tensor cores
-// (tcgen05.mma, bf16 operands, fp32 accumulators in tensor memory), with
-// every operand tile brought into shared memory by TMA.
+// tc_conv.cu -- the selector's 9-tap convolutions as implicit GEMMs on the
+// fifth-generation tensor cores (tcgen05.mma, bf16 operands, fp32
+// accumulators in tensor memory), every operand tile brought into shared
+// memory by TMA.
 //
 // Output tile: 128 positions (rows of the flat batch) x 64 output channels.
 // For tap t the A operand is rows r0 - 4 + t .. r0 + 123 + t of the input,
 // i.e. the same 136-row tile shifted by t rows, so a CTA loads the tile once
-// (TMA, 128-byte swizzle, rows outside the batch read as zeros) and points
-// the MMA's shared-memory descriptor t rows further for each tap.  The B
-// operand (the 64 output channels' weights of all 9 taps) stays resident in
-// shared memory for the CTA's whole life: CTAs are persistent, each owns one
-// 64-channel half of the output and walks the row tiles, the next tile's
-// TMA load overlapping the current tile's MMAs and epilogue.  One thread
-// issues the 9 x (CIN / 16) MMAs of a tile (M 128, N 64, K 16 each) and
-// commits them to an mbarrier; the four warps then read the accumulator
-// rows they own from tensor memory (tcgen05.ld 32x32b), add the bias, apply
-// the mode's activation or mask and store bf16 / fp32 rows.
+// (TMA, 128-byte swizzle for 64 or 128 channels, 64-byte swizzle for 32;
+// rows outside the batch read as zeros) and points the MMA's shared-memory
+// descriptor t rows further for each tap.  The B operand (the 64 output
+// channels' weights of all 9 taps) stays resident in shared memory for the
+// CTA's whole life.  CTAs are persistent, each owns one 64-channel slice of
+// the output and walks the row tiles with three roles:
+//   warp 0   TMA producer: input tiles into two buffers,
+//   warp 1   MMA issuer: 9 x (CIN / 16) MMAs (M 128, N 64, K 16) per tile
+//            into one of two accumulators in tensor memory, committed to
+//            mbarriers that free the input buffer and hand the accumulator
+//            to the epilogue,
+//   warps 2-5 epilogue: each reads the 32 accumulator rows its warp may
+//            address (tcgen05.ld 32x32b), adds the bias, applies the mode's
+//            activation or mask and stores bf16 / fp32 rows, then frees the
+//            accumulator,
+// so the epilogue of tile i runs under the MMAs of tile i + 1 and the load
+// of tile i + 2.
 //
 // Every wait on an mbarrier gives up after a bounded number of polls, sets
-// bit MSA_DERR_TIMEOUT_TC of the caller's error word and leaves the tile
-// loop; tensor memory is released on every path.
+// bit MSA_DERR_TIMEOUT_TC of the caller's error word and ends the role;
+// tensor memory is released on every path.
 #include <cuda.h>
 
 #include <cstring>
@@ -32,18 +39,25 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int TBM = 128;              // output rows per tile
-constexpr int TBN = 64;               // output channels per CTA
-constexpr int AROWS = TBM + 2 * HALF; // 136 staged input rows
-constexpr int KB_BYTES_A = AROWS * 128;  // one 64-channel block of the A tile
-constexpr int KB_BYTES_B = TBN * 128;    // one 64-channel block of one tap's weights
-constexpr int TC_THREADS = 128;
+constexpr int TBM = 128;               // output rows per tile
+constexpr int TBN = 64;                // output channels per CTA
+constexpr int AROWS = TBM + 2 * HALF;  // 136 staged input rows
+constexpr int TC_THREADS = 192;        // producer, MMA, 4 epilogue warps
 constexpr long long kSpinLimit = 1ll << 26;
 
-template <int CIN> __host__ __device__ constexpr int w_bytes() { return TAPS * (CIN / 64) * KB_BYTES_B; }
-template <int CIN> __host__ __device__ constexpr int a_bytes() { return (CIN / 64) * KB_BYTES_A; }
-// weights, two A buffers, 1 KB of slack to align the base to 1024 bytes
-template <int CIN> __host__ __device__ constexpr int tc_smem() { return w_bytes<CIN>() + 2 * a_bytes<CIN>() + 1024; }
+// Shared-memory geometry of one input width: rows of ROWB bytes (128 with
+// the 128-byte swizzle for 64 / 128 channels, 64 with the 64-byte swizzle
+// for 32), KB blocks of BLK channels across the reduction.
+template <int CIN> struct Geo {
+  static constexpr int ROWB = CIN >= 64 ? 128 : 64;
+  static constexpr int BLK = ROWB / 2;
+  static constexpr int KB = CIN / BLK;
+  static constexpr int A_BLOCK = AROWS * ROWB;         // one block of the A tile
+  static constexpr int B_BLOCK = TBN * ROWB;           // one block of one tap's weights
+  static constexpr int W_BYTES = TAPS * KB * B_BLOCK;  // resident weights
+  static constexpr int A_BYTES = (KB * A_BLOCK + 1023) / 1024 * 1024;
+  static constexpr int SMEM = W_BYTES + 2 * A_BYTES + 1024;  // + alignment slack
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -56,6 +70,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // true once the phase with the given parity has completed; false after the
@@ -81,21 +99,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
-// layout (rows of 128 bytes, 8-row groups 1024 bytes apart).  Fields: start
-// address >> 4 [0,14), leading-dimension offset >> 4 [16,30) (unused for this
-// layout, 1), stride-dimension offset >> 4 [32,46), descriptor version 1
-// [46,48), base offset [49,52) left 0, layout type [61,64) = 2 (128-byte
-// swizzle).  The swizzle phase of a row follows its shared-memory address
-// (as the TMA that wrote it), so a start address t rows into a 1024-byte
-// aligned tile reads rows t, t+1, ... as written.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand in a swizzled layout
+// (rows of ROWB bytes, 8-row groups 8 * ROWB bytes apart).  Fields: start
+// address >> 4 [0,14), leading-dimension offset >> 4 [16,30) (unused by
+// these layouts, 1), stride-dimension offset >> 4 [32,46), descriptor
+// version 1 [46,48), base offset [49,52) left 0, layout type [61,64) = 2
+// (128-byte swizzle) or 4 (64-byte swizzle).  The swizzle phase of a row
+// follows its shared-memory address (as for the TMA that wrote it), so a
+// start address t rows into an aligned tile reads rows t, t+1, ... as
+// written.
+template <int ROWB>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3fff);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((8 * ROWB) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(ROWB == 128 ? 2 : 4) << 61;
   return d;
 }
 
@@ -114,6 +134,7 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
       : "memory");
 }
 
+// arrive on the mbarrier once every MMA this thread issued before has completed
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -143,6 +164,9 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// barrier slots in shared memory
+enum { B_W = 0, B_AFULL = 1, B_AEMPTY = 3, B_CFULL = 5, B_CEMPTY = 7, NBARS = 9 };
+
 // mode 0: relu(x * W + b) -> bf16; mode 1: x * W + b -> fp32; mode 2: data
 // gradient (taps reversed, no bias) masked by prev > 0 -> bf16.  Rows whose
 // rowseq is negative (padding between sequences) are written as zero.
@@ -151,166 +175,173 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
           const float *__restrict__ bias, const int32_t *__restrict__ rowseq,
           const bf16 *__restrict__ prev, void *__restrict__ y, int T, unsigned *err) {
-  constexpr int KB = CIN / 64;          // 64-channel blocks of the reduction
-  constexpr int NH = COUT / TBN;        // output-channel halves
+  using Gm = Geo<CIN>;
+  constexpr int NH = COUT / TBN;  // output-channel slices
   extern __shared__ unsigned char tc_raw[];
-  __shared__ __align__(8) unsigned long long bars[4];  // W full, A full x2, MMA done
+  __shared__ __align__(8) unsigned long long bars[NBARS];
+  __shared__ float s_bias[TBN];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail;
   const uint32_t raw = smem_u32(tc_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   const uint32_t sW = base;
-  const uint32_t sA0 = base + w_bytes<CIN>();
+  const uint32_t sA0 = base + Gm::W_BYTES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int half = (int)(blockIdx.x % NH);
   const int stride = (int)(gridDim.x / NH);
+  const int first = (int)(blockIdx.x / NH);
   const int ntiles = (T + TBM - 1) / TBM;
-  const uint32_t barW = smem_u32(&bars[0]), barA0 = smem_u32(&bars[1]), barM = smem_u32(&bars[3]);
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
   if (tid == 0) {
-    mbar_init(barW, 1);
-    mbar_init(barA0, 1);
-    mbar_init(barA0 + 8, 1);
-    mbar_init(barM, 1);
-    s_fail = 0;
+    mbar_init(bar(B_W), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(B_AFULL + b), 1);
+      mbar_init(bar(B_AEMPTY + b), 1);
+      mbar_init(bar(B_CFULL + b), 1);
+      mbar_init(bar(B_CEMPTY + b), 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 0) {
+  if (tid < TBN) s_bias[tid] = MODE == 2 ? 0.f : bias[half * TBN + tid];
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(TBN));
+                 "r"(2 * TBN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-
-  int tile = (int)(blockIdx.x / NH);
-  if (tid == 0 && tile < ntiles) {
-    // this half's weights of every tap, and the first A tile
-    mbar_expect_tx(barW, (uint32_t)w_bytes<CIN>());
-    for (int t = 0; t < TAPS; ++t)
-      for (int kb = 0; kb < KB; ++kb)
-        tma_load_2d(sW + (uint32_t)((t * KB + kb) * KB_BYTES_B), &wmap, kb * 64, t * COUT + half * TBN, barW);
-    mbar_expect_tx(barA0, (uint32_t)a_bytes<CIN>());
-    for (int kb = 0; kb < KB; ++kb)
-      tma_load_2d(sA0 + (uint32_t)(kb * KB_BYTES_A), &xmap, kb * 64, tile * TBM - HALF, barA0);
-  }
   bool ok = true;
-  // copies and MMAs this CTA has in flight (tracked by thread 0, which
-  // issues them), drained on the failure path before shared memory is freed
-  bool pendW = tile < ntiles, pendA[2] = {tile < ntiles, false}, pendM = false;
-  if (tile < ntiles && !mbar_wait(barW, 0)) ok = false;
-  else pendW = false;
-  uint32_t phaseA[2] = {0u, 0u}, phaseM = 0u;
-  for (int it = 0; tile < ntiles; tile += stride, ++it) {
-    const int buf = it & 1;
-    const uint32_t sA = sA0 + (uint32_t)(buf * a_bytes<CIN>());
-    const uint32_t barA = barA0 + 8u * (uint32_t)buf;
-    // prefetch the next tile into the other buffer (its MMAs finished last round)
-    const int next = tile + stride;
-    if (tid == 0 && ok && next < ntiles) {
-      const uint32_t nb = barA0 + 8u * (uint32_t)(buf ^ 1);
-      const uint32_t nA = sA0 + (uint32_t)((buf ^ 1) * a_bytes<CIN>());
-      mbar_expect_tx(nb, (uint32_t)a_bytes<CIN>());
-      for (int kb = 0; kb < KB; ++kb)
-        tma_load_2d(nA + (uint32_t)(kb * KB_BYTES_A), &xmap, kb * 64, next * TBM - HALF, nb);
-      pendA[buf ^ 1] = true;
+
+  if (warp == 0) {
+    // ---- TMA producer
+    if (lane == 0 && first < ntiles) {
+      mbar_expect_tx(bar(B_W), (uint32_t)Gm::W_BYTES);
+      for (int t = 0; t < TAPS; ++t)
+        for (int kb = 0; kb < Gm::KB; ++kb)
+          tma_load_2d(sW + (uint32_t)((t * Gm::KB + kb) * Gm::B_BLOCK), &wmap, kb * Gm::BLK,
+                      t * COUT + half * TBN, bar(B_W));
+      int issued = 0;
+      for (int it = 0, tile = first; tile < ntiles && ok; tile += stride, ++it) {
+        const int b = it & 1, k = it >> 1;
+        if (k > 0 && !mbar_wait(bar(B_AEMPTY + b), (uint32_t)((k - 1) & 1))) { ok = false; break; }
+        const uint32_t sA = sA0 + (uint32_t)(b * Gm::A_BYTES);
+        mbar_expect_tx(bar(B_AFULL + b), (uint32_t)(Gm::KB * Gm::A_BLOCK));
+        for (int kb = 0; kb < Gm::KB; ++kb)
+          tma_load_2d(sA + (uint32_t)(kb * Gm::A_BLOCK), &xmap, kb * Gm::BLK, tile * TBM - HALF,
+                      bar(B_AFULL + b));
+        ++issued;
+      }
+      // no copy may still be landing when the CTA exits: wait (bounded) for
+      // the weights and the last load into each buffer (at once if landed)
+      mbar_wait(bar(B_W), 0);
+      for (int it = issued - 2; it < issued; ++it)
+        if (it >= 0) mbar_wait(bar(B_AFULL + (it & 1)), (uint32_t)((it >> 1) & 1));
     }
-    if (ok && !mbar_wait(barA, phaseA[buf])) ok = false;
-    if (ok) { phaseA[buf] ^= 1u; pendA[buf] = false; }
-    if (tid == 0 && ok) {
-      tc_fence_after();
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0 && first < ntiles) {
+      int last = -1;
+      if (!mbar_wait(bar(B_W), 0)) ok = false;
+      for (int it = 0, tile = first; ok && tile < ntiles; tile += stride, ++it) {
+        const int b = it & 1, k = it >> 1;
+        if (!mbar_wait(bar(B_AFULL + b), (uint32_t)(k & 1))) { ok = false; break; }
+        if (k > 0 && !mbar_wait(bar(B_CEMPTY + b), (uint32_t)((k - 1) & 1))) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sA = sA0 + (uint32_t)(b * Gm::A_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(b * TBN);
 #pragma unroll 1
-      for (int t = 0; t < TAPS; ++t) {
-        const int wt = MODE == 2 ? TAPS - 1 - t : t;
+        for (int t = 0; t < TAPS; ++t) {
+          const int wt = MODE == 2 ? TAPS - 1 - t : t;
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) {
+          for (int kb = 0; kb < Gm::KB; ++kb) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = sw128_desc(sA + (uint32_t)(kb * KB_BYTES_A + t * 128 + kk * 32));
-            const uint64_t bd = sw128_desc(sW + (uint32_t)((wt * KB + kb) * KB_BYTES_B + kk * 32));
-            umma_bf16(tmem, ad, bd, (t | kb | kk) != 0 ? 1u : 0u);
-          }
-        }
-      }
-      umma_commit(barM);
-      pendM = true;
-    }
-    if (ok && !mbar_wait(barM, phaseM)) ok = false;
-    if (ok) { phaseM ^= 1u; pendM = false; }
-    if (!ok) s_fail = 1;
-    __syncthreads();
-    if (s_fail) { ok = false; break; }
-    tc_fence_after();
-    // epilogue: warp w owns accumulator rows 32w .. 32w + 31
-    const int r = tile * TBM + warp * 32 + lane;
-    const bool inb = r < T;
-    const bool valid = inb && rowseq[r] >= 0;
-#pragma unroll
-    for (int c0 = 0; c0 < TBN; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      const int cb = half * TBN + c0;
-      if (!inb) continue;
-      if constexpr (MODE == 1) {
-        float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + (size_t)r * COUT + cb);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float4 o;
-          o.x = valid ? v[4 * q] + bias[cb + 4 * q] : 0.f;
-          o.y = valid ? v[4 * q + 1] + bias[cb + 4 * q + 1] : 0.f;
-          o.z = valid ? v[4 * q + 2] + bias[cb + 4 * q + 2] : 0.f;
-          o.w = valid ? v[4 * q + 3] + bias[cb + 4 * q + 3] : 0.f;
-          dst[q] = o;
-        }
-      } else {
-        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(y) + (size_t)r * COUT + cb);
-        const uint4 *pv = MODE == 2 ? reinterpret_cast<const uint4 *>(prev + (size_t)r * COUT + cb) : nullptr;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint32_t w[4];
-          uint4 pm = make_uint4(0u, 0u, 0u, 0u);
-          if constexpr (MODE == 2) pm = pv[q];
-          const uint32_t pw[4] = {pm.x, pm.y, pm.z, pm.w};
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const int c = 8 * q + 2 * h;
-            float a = v[c], b = v[c + 1];
-            if constexpr (MODE == 0) {
-              a = valid ? fmaxf(a + bias[cb + c], 0.f) : 0.f;
-              b = valid ? fmaxf(b + bias[cb + c + 1], 0.f) : 0.f;
-            } else {
-              const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162 *>(&pw[h]);
-              a = valid && __bfloat162float(p2.x) > 0.f ? a : 0.f;
-              b = valid && __bfloat162float(p2.y) > 0.f ? b : 0.f;
+            for (int kk = 0; kk < Gm::BLK / 16; ++kk) {
+              const uint64_t ad = smem_desc<Gm::ROWB>(sA + (uint32_t)(kb * Gm::A_BLOCK + t * Gm::ROWB + kk * 32));
+              const uint64_t bd = smem_desc<Gm::ROWB>(sW + (uint32_t)((wt * Gm::KB + kb) * Gm::B_BLOCK + kk * 32));
+              umma_bf16(acc, ad, bd, (t | kb | kk) != 0 ? 1u : 0u);
             }
-            const __nv_bfloat162 o2 = __floats2bfloat162_rn(a, b);
-            w[h] = *reinterpret_cast<const uint32_t *>(&o2);
           }
-          dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        umma_commit(bar(B_AEMPTY + b));
+        umma_commit(bar(B_CFULL + b));
+        last = it;
+      }
+      // and no MMA may still be running: the last commit's barrier (bounded)
+      if (last >= 0) mbar_wait(bar(B_AEMPTY + (last & 1)), (uint32_t)((last >> 1) & 1));
+    }
+  } else {
+    // ---- epilogue: warp w addresses accumulator rows 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    for (int it = 0, tile = first; tile < ntiles; tile += stride, ++it) {
+      const int b = it & 1, k = it >> 1;
+      if (!mbar_wait(bar(B_CFULL + b), (uint32_t)(k & 1))) { ok = false; break; }
+      tc_fence_after();
+      const int r = tile * TBM + q * 32 + lane;
+      const bool inb = r < T;
+      const bool valid = inb && rowseq[r] >= 0;
+#pragma unroll
+      for (int c0 = 0; c0 < TBN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TBN + c0), v);
+        const int cb = half * TBN + c0;
+        if (!inb) continue;
+        if constexpr (MODE == 1) {
+          float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + (size_t)r * COUT + cb);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float4 o;
+            o.x = valid ? v[4 * j] + s_bias[c0 + 4 * j] : 0.f;
+            o.y = valid ? v[4 * j + 1] + s_bias[c0 + 4 * j + 1] : 0.f;
+            o.z = valid ? v[4 * j + 2] + s_bias[c0 + 4 * j + 2] : 0.f;
+            o.w = valid ? v[4 * j + 3] + s_bias[c0 + 4 * j + 3] : 0.f;
+            dst[j] = o;
+          }
+        } else {
+          uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(y) + (size_t)r * COUT + cb);
+          const uint4 *pv = MODE == 2 ? reinterpret_cast<const uint4 *>(prev + (size_t)r * COUT + cb) : nullptr;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t w[4];
+            uint4 pm = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (MODE == 2) pm = pv[j];
+            const uint32_t pw[4] = {pm.x, pm.y, pm.z, pm.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int c = 8 * j + 2 * h;
+              float a = v[c], bb = v[c + 1];
+              if constexpr (MODE == 0) {
+                a = valid ? fmaxf(a + s_bias[c0 + c], 0.f) : 0.f;
+                bb = valid ? fmaxf(bb + s_bias[c0 + c + 1], 0.f) : 0.f;
+              } else {
+                const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162 *>(&pw[h]);
+                a = valid && __bfloat162float(p2.x) > 0.f ? a : 0.f;
+                bb = valid && __bfloat162float(p2.y) > 0.f ? bb : 0.f;
+              }
+              const __nv_bfloat162 o2 = __floats2bfloat162_rn(a, bb);
+              w[h] = *reinterpret_cast<const uint32_t *>(&o2);
+            }
+            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
         }
       }
+      // this warp's reads of the accumulator are done: hand it back
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_CEMPTY + b));
     }
-    // the next tile's MMAs overwrite the accumulator: every warp's loads first
-    tc_fence_before();
-    __syncthreads();
   }
-  if (!ok && tid == 0) {
-    atomicOr(err, MSA_DERR_TIMEOUT_TC);
-    // give what is still in flight one more bounded wait
-    if (pendW) mbar_wait(barW, 0);
-    for (int b = 0; b < 2; ++b)
-      if (pendA[b]) mbar_wait(barA0 + 8u * (uint32_t)b, phaseA[b]);
-    if (pendM) mbar_wait(barM, phaseM);
-  }
+  if (!ok) atomicOr(err, MSA_DERR_TIMEOUT_TC);
+  // every role has returned: the last MMAs and loads completed before the
+  // epilogue (or timed out above); free tensor memory
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
 }
 
 // ---------------------------------------------------------------- host side
@@ -333,17 +364,20 @@ encode_fn get_encode() {
   return fn;
 }
 
-// 2-D bf16 tensor [rows][cols] (cols contiguous), box of box_rows x 64
-// columns in the 128-byte swizzle; rows outside [0, rows) read as zeros
-bool make_map(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+// 2-D bf16 tensor [rows][cols] (cols contiguous), box of box_rows x blk
+// columns in the 128-byte (blk = 64) or 64-byte (blk = 32) swizzle; rows
+// outside [0, rows) read as zeros
+bool make_map(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
+              uint32_t blk) {
   encode_fn enc = get_encode();
   if (!enc) return false;
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {cols * sizeof(bf16)};
-  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint32_t box[2] = {blk, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE,
+             blk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -357,10 +391,12 @@ int sm_count() {
 template <int CIN, int COUT, int MODE>
 cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int32_t *rowseq,
                       const bf16 *prev, void *y, int T, unsigned *err, cudaStream_t st) {
+  using Gm = Geo<CIN>;
   CUtensorMap xm, wm;
-  if (!make_map(&xm, x, (uint64_t)T, CIN, AROWS) || !make_map(&wm, w, (uint64_t)TAPS * COUT, CIN, TBN))
+  if (!make_map(&xm, x, (uint64_t)T, CIN, AROWS, Gm::BLK) ||
+      !make_map(&wm, w, (uint64_t)TAPS * COUT, CIN, TBN, Gm::BLK))
     return cudaErrorInvalidValue;
-  constexpr int smem = tc_smem<CIN>();
+  constexpr int smem = Gm::SMEM;
   auto fn = k_conv_tc<CIN, COUT, MODE>;
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -375,7 +411,7 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int
 
 bool conv_tc_supported(int cin, int cout, int mode) {
   return (cin == 128 && cout == 128 && (mode == 0 || mode == 2)) || (cin == 128 && cout == 64 && mode == 1) ||
-         (cin == 64 && cout == 128 && mode == 2);
+         (cin == 64 && cout == 128 && mode == 2) || (cin == 32 && cout == 128 && mode == 0);
 }
 
 cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, const float *bias,
@@ -386,6 +422,7 @@ cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, c
   if (cin == 128 && cout == 128 && mode == 2) return launch_tc<128, 128, 2>(x, w, bias, rowseq, prev, y, T, err, st);
   if (cin == 128 && cout == 64 && mode == 1) return launch_tc<128, 64, 1>(x, w, bias, rowseq, prev, y, T, err, st);
   if (cin == 64 && cout == 128 && mode == 2) return launch_tc<64, 128, 2>(x, w, bias, rowseq, prev, y, T, err, st);
+  if (cin == 32 && cout == 128 && mode == 0) return launch_tc<32, 128, 0>(x, w, bias, rowseq, prev, y, T, err, st);
   return cudaErrorInvalidValue;
 }
 
