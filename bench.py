@@ -57,6 +57,12 @@ def parse():
                     help="override lengths, e.g. uniform:340:360 (profiling cases)")
     ap.add_argument("--only-center", action="store_true",
                     help="time the exact-center selection alone (profiling cases)")
+    ap.add_argument("--only-align", action="store_true",
+                    help="time the alignment to one center alone (profiling cases): the "
+                         "workload's own center if it has one, else the median-length sequence")
+    ap.add_argument("--only-embed", action="store_true",
+                    help="time the selector's embedding of every sequence alone, random "
+                         "network (profiling cases)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-center comparison")
     ap.add_argument("--autotune", action="store_true",
@@ -225,7 +231,7 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
             "speedup": exact_ms / float(np.mean(ms)),
             "avg_sp_exact": exact_sp / pairs_n, "avg_sp_learned": sp / pairs_n,
             "sp_loss_pct": 100.0 * (sp - exact_sp) / exact_sp, "learned_center": c,
-            "selector": "4-layer conv, width 128, k 9, 64-d, bf16 tensor cores",
+            "selector": "4-layer conv, width 128, k 9, 64-d, bf16 on tcgen05 tensor cores",
             "train": {"pairs": int(pairs.shape[0]), "steps": 6000, "batch_pairs": 256,
                       "seconds": train_s, "loss_first": float(losses[:10].mean()),
                       "loss_last": float(losses[-50:].mean())},
@@ -316,6 +322,34 @@ def run_ours(args):
         print(json.dumps({"only_center": True, "n": n, "center": c, "wall_s": dt,
                           "center_kernel_ms": ms["center_kernels"], "cells": cnt["center_cells"],
                           "gcups": cnt["center_cells"] / (ms["center_kernels"] * 1e-3) / 1e9}))
+        ctx.close()
+        return
+
+    if args.only_align:
+        lens = np.diff(offsets)
+        center = 0 if w.center_seq else int(np.argsort(lens, kind="stable")[len(lens) // 2])
+        b.msa_load(h, dlet, offsets)
+        for _ in range(max(1, args.warmup)):
+            b.msa_align_to_center(h, center)
+        ms, cnt = b.msa_stage_times(h)
+        print(json.dumps({"only_align": True, "n": n, "center": center, "Lc": int(lens[center]),
+                          "align_kernel_ms": ms["align_kernels"], "traceback_ms": ms["traceback"],
+                          "cells": cnt["align_cells"],
+                          "gcups": cnt["align_cells"] / (ms["align_kernels"] * 1e-3) / 1e9}))
+        ctx.close()
+        return
+    if args.only_embed:
+        lens = np.diff(offsets)
+        b.msa_load(h, dlet, offsets)
+        b.msa_selector_init(h, seed=1)
+        for _ in range(max(1, args.warmup)):
+            b.msa_select_center(h, b.MSA_CENTER_LEARNED)
+        ms = b.msa_stage_times(h)[0]["selector"]
+        # conv flops per row: 2 x 9 taps x (32x128 + 128x128 + 128x128 + 128x64)
+        rows = int(lens.sum()) + 4 * (n + 1)
+        flops = 2 * 9 * (32 * 128 + 2 * 128 * 128 + 128 * 64) * rows
+        print(json.dumps({"only_embed": True, "n": n, "rows": rows, "selector_ms": ms,
+                          "tflops": flops / (ms * 1e-3) / 1e12}))
         ctx.close()
         return
 

@@ -399,7 +399,7 @@ cudaError_t wgrad(int cin, int cout, const bf16 *x, const bf16 *dy, float *dw, i
 
 cudaError_t colsum(int cout, const bf16 *dy, float *db, int T, cudaStream_t st) {
   if (T <= 0) return cudaSuccess;
-  const int chunk = 1024;
+  const int chunk = 128;  // short serial sums, many CTAs
   k_colsum<<<(T + chunk - 1) / chunk, cout, 0, st>>>(cout, dy, db, T, chunk);
   return cudaGetLastError();
 }
