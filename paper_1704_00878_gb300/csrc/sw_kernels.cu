@@ -264,7 +264,9 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
 // add with no unpacking.  Lane t reads R words (R/4 16-byte loads) at word
 // offset t*R; with R/4 odd the eight lanes of a load phase hit eight
 // different 16-byte bank groups whatever residues they read.
-template <int G, int R>
+// IN / OUT: the pass reads the row above from scr_in / writes its bottom row
+// to scr_out (compile-time, so a single-pass query carries no test for them).
+template <int G, int R, bool IN, bool OUT>
 __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, int stride,
                                             const uint8_t *__restrict__ rs, int Ls, int Lw, int t,
                                             int base_lane, int padc, int o, int e,
@@ -281,7 +283,7 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
   uint32_t resv = pc;
   uint32_t cur = residue_at(rs, Ls, t, pc), nxt = residue_at(rs, Ls, G + t, pc);
   int2 sv0 = make_int2(0, 0), sv1 = make_int2(0, 0);
-  if (scr_in != nullptr) {
+  if (IN) {
     if (0 < Lw) sv0 = scr_in[0];
     if (1 < Lw) sv1 = scr_in[1];
   }
@@ -295,11 +297,13 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
     int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
     int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
     const int2 sv = sv0;
-    sv0 = sv1;
-    if (scr_in != nullptr && k + 2 < Lw) sv1 = scr_in[k + 2];
+    if (IN) {
+      sv0 = sv1;
+      if (k + 2 < Lw) sv1 = scr_in[k + 2];
+    }
     if (t == 0) {
       rin = r0;
-      const bool above = scr_in != nullptr && k < Lw;
+      const bool above = IN && k < Lw;
       hin = above ? sv.x : 0;
       fin = above ? sv.y : 0;
     }
@@ -329,7 +333,7 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
     }
     hbot = H[R - 1];
     fbot = f;
-    if (scr_out != nullptr && t == G - 1) {
+    if (OUT && t == G - 1) {
       const int j = k - (G - 1);
       if (j >= 0 && j < Lw) scr_out[j] = make_int2(hbot, fbot);
     }
@@ -338,8 +342,10 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
 }
 
 // Work item = (query pair p, block of NG consecutive subjects, one per group).
+// three CTAs per SM for the 12-row variants (their registers fit 85 per
+// thread without spilling); two otherwise
 template <int G, int R>
-__global__ void __launch_bounds__(kCenterThreads)
+__global__ void __launch_bounds__(kCenterThreads, R <= 12 ? 3 : 2)
 k_center2(SeqSet ss, Scoring sc, CenterJob job) {
   extern __shared__ __align__(16) uint32_t smem32[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
@@ -398,8 +404,16 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
       for (int p = 0; p < np; ++p) {
         const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
         int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
-        const int b = wave_pass_pp<G, R>(smem32 + p * G * R, stride, rs, Ls, Lw, t, base_lane,
-                                         padc, o, sc.e, sin, sout);
+        const uint32_t *pp = smem32 + p * G * R;
+        int b;
+        if (np == 1)
+          b = wave_pass_pp<G, R, false, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
+        else if (p == 0)
+          b = wave_pass_pp<G, R, false, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
+        else if (p + 1 == np)
+          b = wave_pass_pp<G, R, true, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
+        else
+          b = wave_pass_pp<G, R, true, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
         best = Cell<true>::vmax(best, b);
         __syncwarp();
       }
