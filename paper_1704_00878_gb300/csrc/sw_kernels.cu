@@ -289,7 +289,7 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
   }
   const uint32_t *pb = prof + t * R;
   const int steps = Lw + G - 1;
-#pragma unroll 2
+#pragma unroll 4
   for (int k = 0; k < steps; ++k) {
     const int kk = k & (G - 1);
     if (kk == 0 && k > 0) { cur = nxt; nxt = residue_at(rs, Ls, k + G + t, pc); }
