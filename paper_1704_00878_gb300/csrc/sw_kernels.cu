@@ -110,6 +110,7 @@ __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int st
   const int8_t *pb = prof + t * R;
   const int steps = Lw + G - 1;
 
+#pragma unroll 4
   for (int k = 0; k < steps; ++k) {
     const int kk = k & (G - 1);
     if (kk == 0 && k > 0) { cur = nxt; nxt = fetch(k + G + t); }
@@ -723,6 +724,7 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
   const int8_t *pb = prof + t * R;
   const bool wr = blk < nblk;
   const int steps = Lw + G - 1;
+#pragma unroll 2
   for (int k = 0; k < steps; ++k) {
     const int kk = k & (G - 1);
     if (kk == 0 && k > 0) { cur = nxt; nxt = fetch(k + G + t); }
