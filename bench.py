@@ -65,6 +65,9 @@ def parse():
                          "network (profiling cases)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-center comparison")
+    ap.add_argument("--center", default="exact", choices=["exact", "sampled"],
+                    help="exact all-pairs center, or the sampled exact center over 1,000 "
+                         "seeded references (the larger workloads)")
     ap.add_argument("--autotune", action="store_true",
                     help="correct the center planner's cost model with measured rates first")
     return ap.parse_args()
@@ -195,6 +198,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def workload_text(w, n, center, length=None):
+    """The workload of a bench line, from its generator parameters."""
+    ln = length or w.length
+    if ln[0] == "lognormal":
+        lens = "lognormal lengths median %d sigma %.1f clipped %d-%d" % ln[1:]
+    else:
+        lens = "lengths uniform %d-%d" % ln[1:]
+    kind = "proteins (BLOSUM62)" if w.kind == "protein" else "DNA sequences (+2/-3)"
+    return ("%s: %d %s per GPU, %s, %d families at %.0f%% substitutions, %.1f%% indels, gap "
+            "open %d / extend %d, %s center" % (w.name, n, kind, lens, w.families, 100 * w.p_sub,
+                                                100 * w.p_indel, w.gap_open, w.gap_extend,
+                                                "exact all-pairs" if center == "exact"
+                                                else "sampled exact (1,000 references)"))
+
+
 def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp):
     """Train the selector on exact-kernel distances (untimed), then time the
     whole step with the learned center (network embedding + exact row sums of
@@ -265,9 +283,16 @@ def run_ours(args):
     ctx = b.Context(M, alph, w.gap_open, w.gap_extend, stream=stream)
     h = ctx.h
 
+    from seqgen import reference_sample
+    refs = reference_sample(n, 1000, 8) if args.center == "sampled" else None
+    center_mode = b.MSA_CENTER_EXACT_SAMPLED if refs is not None else b.MSA_CENTER_EXACT
+
+    def select_exact():
+        return b.msa_select_center(h, center_mode, refs)
+
     def step_device():
         b.msa_load(h, dlet, offsets)
-        c, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        c, _ = select_exact()
         b.msa_align_to_center(h, c)
         _, W = b.msa_merge_gaps(h, want_rows=False)
         sp = b.msa_sp_score(h)
@@ -277,7 +302,7 @@ def run_ours(args):
 
     def step_e2e():
         b.msa_load(h, hlet, offsets)
-        c, _ = b.msa_select_center(h, b.MSA_CENTER_EXACT)
+        c, _ = select_exact()
         b.msa_align_to_center(h, c)
         _, W = b.msa_merge_gaps(h, want_rows=False)
         buf = host_rows.get(W)
@@ -403,10 +428,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
-        "config": {"workload": "%s: %d proteins per GPU, lognormal lengths median 350 sigma 0.6 "
-                               "clipped 50-2000, 5 families at 40%% divergence, 5%% indels, "
-                               "BLOSUM62 gap 11/1, exact all-pairs center" % (w.name, n),
-                   "step": "encode + exact center + align with traceback + merge + rows + SP",
+        "config": {"workload": workload_text(w, n, args.center, length),
+                   "step": "encode + %s center + align with traceback + merge + rows + SP"
+                           % ("exact all-pairs" if refs is None else "sampled exact"),
                    "l2": "flushed (512 MB write) before every timed step",
                    "cells_per_step": cells / args.steps, "center": c, "msa_width": W,
                    "avg_sp": sp / (n * (n - 1) / 2)},
