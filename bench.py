@@ -446,6 +446,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(letters.nbytes + offsets.nbytes),
                 "d2h_bytes_per_step": int(n * W + 8 * 4)},
         "gpu_launches": launches,
+        "device_mem_gb": b.msa_memory(h)[1] / 1e9,
         "autotune": {"seconds": tune_s, "buckets_timed": int((tune > 0).any(axis=1).sum()),
                      "variants_timed": int((tune > 0).sum())},
     }

@@ -274,6 +274,29 @@ int msa_dims(msa_ctx *ctx, int64_t *dims_out);
  * this context since msa_create. */
 int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_out);
 
+/* Device memory the context holds for its working buffers (the paper has no
+ * counterpart; its analogue is the per-machine peak memory it reports):
+ * bytes_out / peak_out (nullable, host int64) = bytes held now and the most
+ * held at once since msa_create.  A few hundred bytes of fixed scalars and
+ * tables are not counted. */
+int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out);
+
+/* Cap on that memory (no counterpart in the paper): with limit_bytes > 0 a
+ * call that would grow the context's buffers beyond it fails with
+ * MSA_ENOMEM and "device memory limit" in msa_last_error, leaving the
+ * context usable (a later call after raising the cap succeeds); 0 removes
+ * the cap.  EINVAL for a negative limit. */
+int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes);
+
+/* Self-test of the bounded waits of the tensor-core convolution (no
+ * counterpart in the paper): runs one small convolution whose loads are
+ * never issued, with a short poll limit, so every mbarrier wait runs out.
+ * *timed_out (host int32) = 1 when the kernel reported the timeout through
+ * the device error word (the expected outcome), 0 otherwise; the error word
+ * is cleared afterwards and the context stays usable.  Returns MSA_OK, or
+ * MSA_ECUDA / MSA_ENOMEM if the probe could not run. */
+int msa_debug_wait_timeout(msa_ctx *ctx, int32_t *timed_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,9 @@ _SIGS = {
     "msa_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "msa_memory": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_set_memory_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "msa_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
     "msa_selector_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -263,6 +266,25 @@ def msa_sp_score(ctx):
     v = np.zeros(1, np.int64)
     _check(ctx, lib().msa_sp_score(ctx, _ptr(v)))
     return int(v[0])
+
+
+def msa_memory(ctx):
+    """(bytes held now, peak bytes) of the context's device buffers."""
+    cur = np.zeros(1, np.int64)
+    peak = np.zeros(1, np.int64)
+    _check(ctx, lib().msa_memory(ctx, _ptr(cur), _ptr(peak)))
+    return int(cur[0]), int(peak[0])
+
+
+def msa_set_memory_limit(ctx, limit_bytes):
+    _check(ctx, lib().msa_set_memory_limit(ctx, int(limit_bytes)))
+
+
+def msa_debug_wait_timeout(ctx):
+    """True when the tensor-core convolution reported its bounded waits running out."""
+    out = np.zeros(1, np.int32)
+    _check(ctx, lib().msa_debug_wait_timeout(ctx, _ptr(out)))
+    return bool(out[0])
 
 
 def msa_stage_times(ctx):

@@ -21,7 +21,7 @@ enum Stage {
 };
 
 struct Selector;  // the learned center selector (selector.cu)
-void selector_free(Selector *s);
+void selector_free(msa_ctx *ctx, Selector *s);
 
 }  // namespace msa_detail
 
@@ -73,6 +73,8 @@ struct msa_ctx {
   float stage_ms[msa_detail::ST_N] = {};
   int64_t cells[2] = {0, 0};
   int64_t launches = 0;
+  // device memory held through ensure(): current, peak, optional cap (0 = none)
+  size_t dev_bytes = 0, dev_peak = 0, dev_limit = 0;
   size_t codes_budget = (size_t)4 << 30;
 
   msa_detail::Selector *sel = nullptr;
@@ -87,6 +89,7 @@ namespace msa_detail {
 
 int fail(msa_ctx *c, int code, const char *fmt, ...);
 int ensure(msa_ctx *ctx, DevBuf &b, size_t bytes);
+void release(msa_ctx *ctx, DevBuf &b);  // frees a buffer taken with ensure()
 template <class T> T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
 bool is_device_ptr(const void *p);
 int set_device(msa_ctx *ctx);

@@ -33,13 +33,27 @@ int ensure(msa_ctx *ctx, DevBuf &b, size_t bytes) {
   if (b.p) {
     CK(cudaStreamSynchronize(ctx->st));
     CK(cudaFree(b.p));
+    ctx->dev_bytes -= b.cap;
     b.p = nullptr;
     b.cap = 0;
   }
   bytes = (bytes + 255) / 256 * 256;
+  if (ctx->dev_limit && ctx->dev_bytes + bytes > ctx->dev_limit)
+    return fail(ctx, MSA_ENOMEM, "device memory limit: %zu bytes held, %zu more wanted, limit %zu",
+                ctx->dev_bytes, bytes, ctx->dev_limit);
   CK(cudaMalloc(&b.p, bytes));
   b.cap = bytes;
+  ctx->dev_bytes += bytes;
+  ctx->dev_peak = std::max(ctx->dev_peak, ctx->dev_bytes);
   return MSA_OK;
+}
+
+void release(msa_ctx *ctx, DevBuf &b) {
+  if (!b.p) return;
+  cudaFree(b.p);
+  ctx->dev_bytes -= b.cap;
+  b.p = nullptr;
+  b.cap = 0;
 }
 
 
@@ -601,7 +615,7 @@ int msa_create(msa_ctx **out, const msa_params *p, void *cuda_stream) {
 void msa_destroy(msa_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
-  selector_free(ctx->sel);
+  selector_free(ctx, ctx->sel);
   ctx->sel = nullptr;
   DevBuf *bufs[] = {&ctx->res, &ctx->d_pstart, &ctx->d_len, &ctx->d_perm, &ctx->d_inv,
                     &ctx->d_srcoff, &ctx->staging, &ctx->pairsum, &ctx->self, &ctx->rowsum,
@@ -924,7 +938,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
   const size_t bytes = (size_t)nblk * Ls * 8;
   const size_t bytes_all = high ? bytes + (size_t)nblk * ctx->len_sorted[ks + 1] * 8 : bytes;
   DevBuf cb, ob, bb;
-  auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb}) if (b->p) cudaFree(b->p); };
+  auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb}) release(ctx, *b); };
   int rc = [&]() -> int {
     TRY(ensure(ctx, cb, bytes_all));
     TRY(ensure(ctx, ob, 2 * sizeof(int64_t)));
@@ -1101,6 +1115,19 @@ int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_ou
     counters_out[1] = ctx->cells[1];
     counters_out[2] = ctx->launches;
   }
+  return MSA_OK;
+}
+
+int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (bytes_out) *bytes_out = (int64_t)ctx->dev_bytes;
+  if (peak_out) *peak_out = (int64_t)ctx->dev_peak;
+  return MSA_OK;
+}
+
+int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes) {
+  if (!ctx || limit_bytes < 0) return MSA_EINVAL;
+  ctx->dev_limit = (size_t)limit_bytes;
   return MSA_OK;
 }
 

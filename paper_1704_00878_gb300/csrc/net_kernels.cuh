@@ -46,14 +46,17 @@ cudaError_t onehot(const Batch &b, const uint8_t *res, const int64_t *pstart, __
 cudaError_t conv(int cin, int cout, int mode, const __nv_bfloat16 *x, const __nv_bfloat16 *w,
                  const float *bias, const int32_t *rowseq, const __nv_bfloat16 *prev, void *y,
                  int T, cudaStream_t st);
-// The same convolutions on the tcgen05 tensor cores (tc_conv.cu) for the
-// shapes with 64 or 128 input channels: (128, 128) modes 0 and 2, (128, 64)
-// mode 1, (64, 128) mode 2.  w as above; err: device error word
-// (MSA_DERR_TIMEOUT_TC).
+// The same convolutions on the tcgen05 tensor cores (tc_conv.cu): (32, 128)
+// and (128, 128) mode 0, (128, 128) and (64, 128) mode 2, (128, 64) mode 1.
+// w as above; err: device error word (MSA_DERR_TIMEOUT_TC).  spins: polls
+// before an mbarrier wait gives up (<= 0: the default, seconds); no_loads:
+// the TMA warp issues nothing, so every wait runs out (the self-test of the
+// bounded waits).
 bool conv_tc_supported(int cin, int cout, int mode);
 cudaError_t conv_tc(int cin, int cout, int mode, const __nv_bfloat16 *x, const __nv_bfloat16 *w,
                     const float *bias, const int32_t *rowseq, const __nv_bfloat16 *prev, void *y,
-                    int T, unsigned *err, cudaStream_t st);
+                    int T, unsigned *err, cudaStream_t st, long long spins = 0,
+                    bool no_loads = false);
 // dW[tap][ci][co] += sum_r x[r + tap - 4][ci] * dy[r][co]   (fp32 atomics)
 cudaError_t wgrad(int cin, int cout, const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw,
                   int T, cudaStream_t st);

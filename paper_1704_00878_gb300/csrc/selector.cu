@@ -30,11 +30,6 @@ struct Selector {
 
 namespace {
 
-void free_buf(DevBuf &b) {
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.cap = 0;
-}
 
 // splitmix64 (Steele, Lea & Flood 2014) as a counter-based generator.
 uint64_t splitmix64(uint64_t x) {
@@ -291,14 +286,14 @@ int embed_all(msa_ctx *ctx, Selector *s) {
 
 }  // namespace
 
-void selector_free(Selector *s) {
+void selector_free(msa_ctx *ctx, Selector *s) {
   if (!s) return;
   DevBuf *bufs[] = {&s->params, &s->grads, &s->m, &s->v, &s->w1t, &s->w2t, &s->w2n, &s->w3t,
                     &s->w3n, &s->w4t, &s->w4n, &s->seq, &s->base, &s->len, &s->rowseq, &s->x0,
                     &s->a1, &s->a2, &s->a3, &s->y4, &s->emb, &s->demb, &s->dy4, &s->dz3,
                     &s->dz2, &s->dz1, &s->bpairs, &s->btargets, &s->loss, &s->small, &s->allemb,
                     &s->dist};
-  for (DevBuf *b : bufs) free_buf(*b);
+  for (DevBuf *b : bufs) release(ctx, *b);
   delete s;
 }
 
@@ -553,6 +548,41 @@ int msa_load_selector(msa_ctx *ctx, const char *path) {
   fclose(f);
   if (!ok) return fail(ctx, MSA_EINVAL, "%s is not a selector file", path);
   return msa_selector_init(ctx, 0, p.data(), count);
+}
+
+// One 128-row (128 -> 128 channel) convolution with its loads suppressed and
+// a poll limit of 4,096: every wait runs out and the kernel reports it.
+int msa_debug_wait_timeout(msa_ctx *ctx, int32_t *timed_out) {
+  if (!ctx || !timed_out) return MSA_EINVAL;
+  TRY(set_device(ctx));
+  *timed_out = 0;
+  const int T = 128, C = net::WD;
+  DevBuf x, w, bias, rows, y;
+  auto cleanup = [&]() { for (DevBuf *b : {&x, &w, &bias, &rows, &y}) release(ctx, *b); };
+  int rc = [&]() -> int {
+    TRY(ensure(ctx, x, sizeof(bf16) * T * C));
+    TRY(ensure(ctx, w, sizeof(bf16) * net::TAPS * C * C));
+    TRY(ensure(ctx, bias, sizeof(float) * C));
+    TRY(ensure(ctx, rows, sizeof(int32_t) * T));
+    TRY(ensure(ctx, y, sizeof(bf16) * T * C));
+    CK(cudaMemsetAsync(x.p, 0, x.cap, ctx->st));
+    CK(cudaMemsetAsync(w.p, 0, w.cap, ctx->st));
+    CK(cudaMemsetAsync(bias.p, 0, bias.cap, ctx->st));
+    CK(cudaMemsetAsync(rows.p, 0, rows.cap, ctx->st));
+    CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+    ++ctx->launches;
+    CK(net::conv_tc(C, C, 0, P<bf16>(x), P<bf16>(w), P<float>(bias), P<int32_t>(rows), nullptr, y.p, T,
+                    ctx->derr, ctx->st, 4096, true));
+    unsigned h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, ctx->derr, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *timed_out = (h[0] & MSA_DERR_TIMEOUT_TC) ? 1 : 0;
+    CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MSA_OK;
+  }();
+  cleanup();
+  return rc;
 }
 
 }  // extern "C"

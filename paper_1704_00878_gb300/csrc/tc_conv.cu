@@ -43,7 +43,7 @@ constexpr int TBM = 128;               // output rows per tile
 constexpr int TBN = 64;                // output channels per CTA
 constexpr int AROWS = TBM + 2 * HALF;  // 136 staged input rows
 constexpr int TC_THREADS = 192;        // producer, MMA, 4 epilogue warps
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kSpinLimit = 1ll << 26;  // polls before a wait gives up
 
 // Shared-memory geometry of one input width: rows of ROWB bytes (128 with
 // the 128-byte swizzle for 64 / 128 channels, 64 with the 64-byte swizzle
@@ -76,10 +76,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// true once the phase with the given parity has completed; false after the
-// poll limit
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+// true once the phase with the given parity has completed; false after
+// `spins` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long spins) {
+  for (long long i = 0; i < spins; ++i) {
     uint32_t done;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -174,7 +174,8 @@ template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
           const float *__restrict__ bias, const int32_t *__restrict__ rowseq,
-          const bf16 *__restrict__ prev, void *__restrict__ y, int T, unsigned *err) {
+          const bf16 *__restrict__ prev, void *__restrict__ y, int T, unsigned *err,
+          long long spins, int no_loads) {
   using Gm = Geo<CIN>;
   constexpr int NH = COUT / TBN;  // output-channel slices
   extern __shared__ unsigned char tc_raw[];
@@ -218,7 +219,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
 
   if (warp == 0) {
     // ---- TMA producer
-    if (lane == 0 && first < ntiles) {
+    if (lane == 0 && first < ntiles && !no_loads) {
       mbar_expect_tx(bar(B_W), (uint32_t)Gm::W_BYTES);
       for (int t = 0; t < TAPS; ++t)
         for (int kb = 0; kb < Gm::KB; ++kb)
@@ -227,7 +228,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
       int issued = 0;
       for (int it = 0, tile = first; tile < ntiles && ok; tile += stride, ++it) {
         const int b = it & 1, k = it >> 1;
-        if (k > 0 && !mbar_wait(bar(B_AEMPTY + b), (uint32_t)((k - 1) & 1))) { ok = false; break; }
+        if (k > 0 && !mbar_wait(bar(B_AEMPTY + b), (uint32_t)((k - 1) & 1), spins)) { ok = false; break; }
         const uint32_t sA = sA0 + (uint32_t)(b * Gm::A_BYTES);
         mbar_expect_tx(bar(B_AFULL + b), (uint32_t)(Gm::KB * Gm::A_BLOCK));
         for (int kb = 0; kb < Gm::KB; ++kb)
@@ -237,19 +238,19 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
       }
       // no copy may still be landing when the CTA exits: wait (bounded) for
       // the weights and the last load into each buffer (at once if landed)
-      mbar_wait(bar(B_W), 0);
+      mbar_wait(bar(B_W), 0, spins);
       for (int it = issued - 2; it < issued; ++it)
-        if (it >= 0) mbar_wait(bar(B_AFULL + (it & 1)), (uint32_t)((it >> 1) & 1));
+        if (it >= 0) mbar_wait(bar(B_AFULL + (it & 1)), (uint32_t)((it >> 1) & 1), spins);
     }
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0 && first < ntiles) {
       int last = -1;
-      if (!mbar_wait(bar(B_W), 0)) ok = false;
+      if (!mbar_wait(bar(B_W), 0, spins)) ok = false;
       for (int it = 0, tile = first; ok && tile < ntiles; tile += stride, ++it) {
         const int b = it & 1, k = it >> 1;
-        if (!mbar_wait(bar(B_AFULL + b), (uint32_t)(k & 1))) { ok = false; break; }
-        if (k > 0 && !mbar_wait(bar(B_CEMPTY + b), (uint32_t)((k - 1) & 1))) { ok = false; break; }
+        if (!mbar_wait(bar(B_AFULL + b), (uint32_t)(k & 1), spins)) { ok = false; break; }
+        if (k > 0 && !mbar_wait(bar(B_CEMPTY + b), (uint32_t)((k - 1) & 1), spins)) { ok = false; break; }
         tc_fence_after();
         const uint32_t sA = sA0 + (uint32_t)(b * Gm::A_BYTES);
         const uint32_t acc = tmem + (uint32_t)(b * TBN);
@@ -271,14 +272,14 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
         last = it;
       }
       // and no MMA may still be running: the last commit's barrier (bounded)
-      if (last >= 0) mbar_wait(bar(B_AEMPTY + (last & 1)), (uint32_t)((last >> 1) & 1));
+      if (last >= 0) mbar_wait(bar(B_AEMPTY + (last & 1)), (uint32_t)((last >> 1) & 1), spins);
     }
   } else {
     // ---- epilogue: warp w addresses accumulator rows 32 (w % 4) .. + 31
     const int q = warp & 3;
     for (int it = 0, tile = first; tile < ntiles; tile += stride, ++it) {
       const int b = it & 1, k = it >> 1;
-      if (!mbar_wait(bar(B_CFULL + b), (uint32_t)(k & 1))) { ok = false; break; }
+      if (!mbar_wait(bar(B_CFULL + b), (uint32_t)(k & 1), spins)) { ok = false; break; }
       tc_fence_after();
       const int r = tile * TBM + q * 32 + lane;
       const bool inb = r < T;
@@ -390,7 +391,8 @@ int sm_count() {
 
 template <int CIN, int COUT, int MODE>
 cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int32_t *rowseq,
-                      const bf16 *prev, void *y, int T, unsigned *err, cudaStream_t st) {
+                      const bf16 *prev, void *y, int T, unsigned *err, cudaStream_t st,
+                      long long spins, int no_loads) {
   using Gm = Geo<CIN>;
   CUtensorMap xm, wm;
   if (!make_map(&xm, x, (uint64_t)T, CIN, AROWS, Gm::BLK) ||
@@ -403,7 +405,7 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int
   constexpr int NH = COUT / TBN;
   const int ntiles = (T + TBM - 1) / TBM;
   const int per_half = std::min(ntiles, std::max(1, sm_count() / NH));
-  fn<<<per_half * NH, TC_THREADS, smem, st>>>(xm, wm, bias, rowseq, prev, y, T, err);
+  fn<<<per_half * NH, TC_THREADS, smem, st>>>(xm, wm, bias, rowseq, prev, y, T, err, spins, no_loads);
   return cudaGetLastError();
 }
 
@@ -416,13 +418,19 @@ bool conv_tc_supported(int cin, int cout, int mode) {
 
 cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, const float *bias,
                     const int32_t *rowseq, const bf16 *prev, void *y, int T, unsigned *err,
-                    cudaStream_t st) {
+                    cudaStream_t st, long long spins, bool no_loads) {
   if (T <= 0) return cudaSuccess;
-  if (cin == 128 && cout == 128 && mode == 0) return launch_tc<128, 128, 0>(x, w, bias, rowseq, prev, y, T, err, st);
-  if (cin == 128 && cout == 128 && mode == 2) return launch_tc<128, 128, 2>(x, w, bias, rowseq, prev, y, T, err, st);
-  if (cin == 128 && cout == 64 && mode == 1) return launch_tc<128, 64, 1>(x, w, bias, rowseq, prev, y, T, err, st);
-  if (cin == 64 && cout == 128 && mode == 2) return launch_tc<64, 128, 2>(x, w, bias, rowseq, prev, y, T, err, st);
-  if (cin == 32 && cout == 128 && mode == 0) return launch_tc<32, 128, 0>(x, w, bias, rowseq, prev, y, T, err, st);
+  if (spins <= 0) spins = kSpinLimit;
+  const int nl = no_loads ? 1 : 0;
+#define NET_TC(CI, CO, MD) \
+  if (cin == CI && cout == CO && mode == MD) \
+    return launch_tc<CI, CO, MD>(x, w, bias, rowseq, prev, y, T, err, st, spins, nl);
+  NET_TC(128, 128, 0)
+  NET_TC(128, 128, 2)
+  NET_TC(128, 64, 1)
+  NET_TC(64, 128, 2)
+  NET_TC(32, 128, 0)
+#undef NET_TC
   return cudaErrorInvalidValue;
 }
 
