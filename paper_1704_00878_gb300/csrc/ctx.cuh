@@ -48,7 +48,7 @@ struct msa_ctx {
 
   // center selection
   DevBuf pairsum, self, rowsum, prefix, qlist, ovf, ovf_scores, ovf_dst, part_val, part_idx,
-      pairs, pair_dst, pair_out, counters;
+      pairs, pair_dst, pair_out, counters, streams;
   cudaStream_t cap_st = nullptr;  // private stream the center graph is captured on
   bool have_rowsum = false;
 

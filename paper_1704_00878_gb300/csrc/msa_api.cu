@@ -174,7 +174,8 @@ bool variant_fits(msa_ctx *ctx, int v, int Lq) {
   const int rows = cv.G * cv.R;
   const int np = (Lq + rows - 1) / rows;
   const int smem = center_smem_bytes(v, ctx->K, np * rows);
-  return !(cv.paired && smem > kMaxPairedProfile) && smem <= 200 * 1024;
+  return !(cv.paired && center_profile_bytes(v, ctx->K, np * rows) > kMaxPairedProfile) &&
+         smem <= 200 * 1024;
 }
 
 int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
@@ -191,7 +192,7 @@ int choose_variant(msa_ctx *ctx, int Lq, int Ls_est, bool packed) {
     const int rows = cv.G * cv.R;
     const int np = (Lq + rows - 1) / rows;
     const int smem = center_smem_bytes(v, ctx->K, np * rows);
-    if (cv.paired && smem > kMaxPairedProfile) continue;
+    if (cv.paired && center_profile_bytes(v, ctx->K, np * rows) > kMaxPairedProfile) continue;
     if (smem > 200 * 1024) continue;
     double c = variant_cost(v, Lq, Ls_est);
     if (corr && (*corr)[v] > 0) c /= (*corr)[v];
@@ -240,8 +241,16 @@ struct ClassPlan {
   int64_t n_items;
 };
 
+// rows of query pair p in a stream of R-row blocks: the longer of its two
+// queries, rounded up to R
+static int pair_rows(const std::vector<int> &qlen, int nq_list, int p, int R) {
+  const int xa = 2 * p, xb = std::min(2 * p + 1, nq_list - 1);
+  return round_up_int(std::max(qlen[xa], qlen[xb]), R);
+}
+
 ClassPlan plan_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
-                     const std::vector<int> &qlen, int sub_n, std::vector<int64_t> &prefix_all) {
+                     const std::vector<int> &qlen, int sub_n, std::vector<int64_t> &prefix_all,
+                     const std::vector<int2> &streams) {
   const CenterVariant &cv = kCenterVariants[cc.variant];
   const int NG = kCenterThreads / cv.G;
   const int n = mode == 0 ? ctx->n : sub_n;
@@ -250,24 +259,27 @@ ClassPlan plan_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
   pl.nq_list = nq_list;
   pl.prefix_off = prefix_all.size();
   prefix_all.push_back(0);
-  int maxlen = 0;
+  int maxrows = 0;
   for (int u = cc.ub; u < cc.ue; ++u) {
     int64_t items;
     if (cv.paired) {
-      const int xa = 2 * u;
-      const int xb = std::min(2 * u + 1, nq_list - 1);
-      maxlen = std::max(maxlen, std::max(qlen[xa], qlen[xb]));
+      // unit = stream u of consecutive pairs, subjects from its first query on
+      const int2 st = streams[u];
+      int rows = 0;
+      for (int q = st.x; q < st.x + st.y; ++q) rows += pair_rows(qlen, nq_list, q, cv.R);
+      maxrows = std::max(maxrows, rows);
+      const int xa = 2 * st.x;
       items = mode == 0 ? (n - xa + NG - 1) / NG : (n + NG - 1) / NG;
     } else {
       const int spi = NG * (cv.packed ? 2 : 1);
-      maxlen = std::max(maxlen, qlen[u]);
+      maxrows = std::max(maxrows, qlen[u]);
       items = mode == 0 ? (n - u + spi - 1) / spi : (n + spi - 1) / spi;
     }
     prefix_all.push_back(prefix_all.back() + items);
   }
   pl.n_items = prefix_all.back();
   const int rows = cv.G * cv.R;
-  pl.npass = (maxlen + rows - 1) / rows;
+  pl.npass = (maxrows + rows - 1) / rows;
   pl.smem = center_smem_bytes(cc.variant, ctx->K, pl.npass * rows);
   pl.grid = center_grid(cc.variant, pl.smem);
   return pl;
@@ -296,13 +308,18 @@ CenterJob class_job(msa_ctx *ctx, int mode, const ClassPlan &pl, int sub_off, in
   job.err = ctx->derr;
   job.scratch = P<int2>(ctx->scratch);
   job.scratch_cols = ctx->maxlen;
+  job.streams = P<int2>(ctx->streams);
   return job;
 }
 
 // Upload the plans' prefixes and size the scratch rows of multi-pass
 // classes (all classes run in stream order, so they share one scratch).
 int stage_plans(msa_ctx *ctx, const std::vector<ClassPlan> &plans,
-                const std::vector<int64_t> &prefix_all) {
+                const std::vector<int64_t> &prefix_all, const std::vector<int2> &streams) {
+  TRY(ensure(ctx, ctx->streams, sizeof(int2) * std::max<size_t>(streams.size(), 1)));
+  if (!streams.empty())
+    CK(cudaMemcpyAsync(ctx->streams.p, streams.data(), sizeof(int2) * streams.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
   size_t scratch = 0;
   for (const ClassPlan &pl : plans)
     if (pl.npass > 1)
@@ -321,8 +338,11 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
                  const std::vector<int> &qlen, float &center_ms, int sub_off = 0, int sub_n = -1) {
   if (sub_n < 0) sub_n = ctx->n;
   std::vector<int64_t> prefix_all;
-  const ClassPlan pl = plan_class(ctx, mode, nq_list, cc, qlen, sub_n, prefix_all);
-  TRY(stage_plans(ctx, {pl}, prefix_all));
+  std::vector<int2> streams;  // paired: one pair per stream
+  if (kCenterVariants[cc.variant].paired)
+    for (int u = 0; u < cc.ue; ++u) streams.push_back(make_int2(u, 1));
+  const ClassPlan pl = plan_class(ctx, mode, nq_list, cc, qlen, sub_n, prefix_all, streams);
+  TRY(stage_plans(ctx, {pl}, prefix_all, streams));
   CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->st));
   const CenterJob job = class_job(ctx, mode, pl, sub_off, sub_n, P<unsigned long long>(ctx->counters));
   stage_begin(ctx, ST_CENTER_K);
@@ -352,12 +372,20 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
   unsigned long long *cnt = P<unsigned long long>(ctx->counters);
   CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * plans.size(), ctx->cap_st);
+  int failed = -1;
   for (size_t c = 0; c < plans.size() && e == cudaSuccess; ++c) {
     const CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c);
     e = launch_center(plans[c].cc.variant, ss, sc, job, plans[c].grid, ctx->cap_st, false);
+    if (e != cudaSuccess) failed = (int)c;
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_st, &graph);
+  if (failed >= 0) {
+    if (graph) cudaGraphDestroy(graph);
+    const ClassPlan &pl = plans[failed];
+    return fail(ctx, MSA_ECUDA, "center kernel variant %d (grid %d, %d B shared, %d passes): %s",
+                pl.cc.variant, pl.grid, pl.smem, pl.npass, cudaGetErrorString(e));
+  }
   if (e == cudaSuccess) e = e_end;
   cudaGraphExec_t exec = nullptr;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -400,21 +428,63 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   };
 
   std::vector<CenterClass> classes;
-  // packed part: query pairs [0, ceil(x1/2))
+  std::vector<int2> streams;
+  // Packed part: query pairs [0, ceil(x1/2)).  Consecutive pairs are stacked
+  // into streams (each pair's rows rounded up to R, not to a whole pass) when
+  // that lowers the modelled cost per real cell; mode 0 streams see the
+  // subjects from their first query on.
   const int npairs = (x1 + 1) / 2;
+  const double total_len = (double)suffix[0];
+  auto partner_cells = [&](int x) { return mode == 0 ? (double)suffix[x] : total_len; };
+  auto partners = [&](int x) { return mode == 0 ? (double)(n - x) : (double)n; };
+  auto add_class = [&](int v, int ub, int ue) {
+    if (!classes.empty() && classes.back().variant == v && classes.back().ue == ub) classes.back().ue = ue;
+    else classes.push_back({v, ub, ue});
+  };
   for (int p = 0; p < npairs;) {
-    const int xq = std::min(2 * p + 1, x1 - 1);
-    const int v = choose_variant(ctx, qlen[xq], est_at(xq), true);
-    if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", qlen[xq]);
-    int pe = p + 1;
-    while (pe < npairs) {
-      const int xe = std::min(2 * pe + 1, x1 - 1);
-      if (choose_variant(ctx, qlen[xe], est_at(xe), true) != v) break;
-      ++pe;
+    int bv = -1, bm = 0;
+    double bcost = 1e300;
+    for (int v = 0; v < kNumCenterVariants; ++v) {
+      const CenterVariant &cv = kCenterVariants[v];
+      if (!cv.paired || !cv.packed) continue;
+      const int GR = cv.G * cv.R;
+      double corr = 1.0;
+      if (!ctx->tune_corr.empty())
+        for (size_t b = 0; b + 1 < ctx->tune_edges.size(); ++b)
+          if (qlen[2 * p] >= ctx->tune_edges[b] && qlen[2 * p] < ctx->tune_edges[b + 1] &&
+              ctx->tune_corr[b][v] > 0)
+            corr = ctx->tune_corr[b][v];
+      int rows = 0;
+      double real = 0;
+      for (int q = p; q < npairs && q - p < kMaxSeg; ++q) {
+        const int rq = pair_rows(qlen, x1, q, cv.R);
+        if (center_profile_bytes(v, ctx->K, round_up_int(rows + rq, GR)) > kMaxPairedProfile) break;
+        rows += rq;
+        const int xa = 2 * q, xb = 2 * q + 1;
+        real += (double)qlen[xa] * partner_cells(xa) + (xb < x1 ? (double)qlen[xb] * partner_cells(xb) : 0.0);
+        const int np = (rows + GR - 1) / GR;
+        const double cost = (double)np * GR * (1.0 + 3.0 / cv.R) *
+                            (partner_cells(2 * p) + partners(2 * p) * (cv.G - 1 + (np > 1 ? 48 : 0))) / corr;
+        if (cost / real < bcost) { bcost = cost / real; bv = v; bm = q - p + 1; }
+      }
     }
-    if (kCenterVariants[v].paired) classes.push_back({v, p, pe});
-    else classes.push_back({v, 2 * p, std::min(2 * pe, x1)});
-    p = pe;
+    if (bv < 0) {
+      // no paired profile fits: the single-query packed kernels
+      const int xq = std::min(2 * p + 1, x1 - 1);
+      const int v = choose_variant(ctx, qlen[xq], est_at(xq), true);
+      if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", qlen[xq]);
+      if (kCenterVariants[v].paired) {
+        streams.push_back(make_int2(p, 1));
+        add_class(v, (int)streams.size() - 1, (int)streams.size());
+      } else {
+        add_class(v, 2 * p, std::min(2 * p + 2, x1));
+      }
+      p += 1;
+      continue;
+    }
+    streams.push_back(make_int2(p, bm));
+    add_class(bv, (int)streams.size() - 1, (int)streams.size());
+    p += bm;
   }
   // int32 part: single queries [x1, nq)
   for (int x = x1; x < nq;) {
@@ -430,9 +500,9 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
   for (const CenterClass &cc : classes) {
     // a paired class may not pair across the packed / int32 boundary
     const int nq_list = kCenterVariants[cc.variant].paired ? x1 : nq;
-    plans.push_back(plan_class(ctx, mode, nq_list, cc, qlen, n, prefix_all));
+    plans.push_back(plan_class(ctx, mode, nq_list, cc, qlen, n, prefix_all, streams));
   }
-  TRY(stage_plans(ctx, plans, prefix_all));
+  TRY(stage_plans(ctx, plans, prefix_all, streams));
   cudaGraphExec_t exec = nullptr;
   TRY(launch_plans(ctx, mode, plans, 0, n, &exec));
   const cudaError_t e_sync = cudaStreamSynchronize(ctx->st);
@@ -623,7 +693,7 @@ void msa_destroy(msa_ctx *ctx) {
                     &ctx->part_val, &ctx->part_idx, &ctx->pairs, &ctx->pair_dst,
                     &ctx->pair_out, &ctx->ins, &ctx->occ, &ctx->seg, &ctx->score,
                     &ctx->codes, &ctx->code_off, &ctx->best, &ctx->G, &ctx->off, &ctx->msa,
-                    &ctx->counts, &ctx->scratch, &ctx->counters};
+                    &ctx->counts, &ctx->scratch, &ctx->counters, &ctx->streams};
   for (DevBuf *b : bufs)
     if (b->p) cudaFree(b->p);
   cudaFree(ctx->dM);

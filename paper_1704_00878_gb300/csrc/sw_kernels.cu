@@ -270,7 +270,7 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
 template <int G, int R, bool IN, bool OUT>
 __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, int stride,
                                             const uint8_t *__restrict__ rs, int Ls, int Lw, int t,
-                                            int base_lane, int padc, int o, int e,
+                                            int base_lane, int padc, int o, int e, bool top,
                                             const int2 *__restrict__ scr_in,
                                             int2 *__restrict__ scr_out) {
   using C = Cell<true>;
@@ -308,6 +308,10 @@ __device__ __forceinline__ int wave_pass_pp(const uint32_t *__restrict__ prof, i
       const bool above = IN && k < Lw;
       hin = above ? sv.x : 0;
       fin = above ? sv.y : 0;
+    }
+    if (top) {  // the lane's first row starts a query (pair): the matrix top
+      hin = 0;
+      fin = 0;
     }
     resv = rin;
     const uint4 *pr = reinterpret_cast<const uint4 *>(pb + resv * stride);
@@ -352,19 +356,23 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
   extern __shared__ __align__(16) uint32_t smem32[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
   __shared__ long long s_item;
-  __shared__ unsigned long long s_qsum[2];
+  __shared__ int s_q[kMaxSeg][2], s_len[kMaxSeg][2], s_start[kMaxSeg + 1];
+  __shared__ const uint8_t *s_res[kMaxSeg][2];
+  __shared__ unsigned long long s_qsum[kMaxSeg][2];
   constexpr int NT = kCenterThreads, NG = NT / G;
   const int K = sc.K, padc = K, o = sc.o;
   const int stride = dround_up(job.npass * G * R, 32);
+  // after the profile: the segment of every R-row block, then the best score
+  // of every segment per group (two int16 lanes kept as two ints)
+  int *s_blk = reinterpret_cast<int *>(smem32 + (K + 1) * stride);
+  int *s_best = s_blk + ((stride / R + 1 + 3) & ~3);
   for (int i = threadIdx.x; i < K * K; i += NT) sM[i] = sc.M[i];
   const int g = threadIdx.x / G, t = threadIdx.x % G;
   const int base_lane = (threadIdx.x & 31) - t;
   int2 *scr = job.scratch + ((size_t)blockIdx.x * NG + g) * 2 * job.scratch_cols;
+  int *gbest = s_best + g * kMaxSeg * 2;
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_item = (long long)atomicAdd(job.counter, 1ull);
-      s_qsum[0] = s_qsum[1] = 0ull;
-    }
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(job.counter, 1ull);
     __syncthreads();
     long long item = s_item;
     if (item >= job.n_items) break;
@@ -374,86 +382,122 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
       const int mid = (lo + hi + 1) >> 1;
       if (job.prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
-    const int pidx = job.qb + lo;  // pair index: queries 2*pidx, 2*pidx+1 of the query list
-    const int xa = 2 * pidx, xb = 2 * pidx + 1;
-    const int qA = job.mode == 0 ? xa : job.qlist[xa];
-    const int qB = xb < job.nq ? (job.mode == 0 ? xb : job.qlist[xb]) : -1;
-    const int s0 = (job.mode == 0 ? xa : job.sub_off) + (int)(item - job.prefix[lo]) * NG;
-    const int send = job.mode == 0 ? ss.n : job.sub_off + job.sub_n;
-    const int LqA = ss.len[qA], LqB = qB >= 0 ? ss.len[qB] : 0;
-    const uint8_t *ra = ss.res + ss.pstart[qA];
-    const uint8_t *rb = ss.res + ss.pstart[qB >= 0 ? qB : qA];
-    const int np = (max(LqA, LqB) + G * R - 1) / (G * R);
+    const int2 st = job.streams[job.qb + lo];  // pairs [st.x, st.x + st.y)
+    const int m = st.y;
+    // segment k = pair st.x + k: queries of the two lanes, lengths, first row
+    if (threadIdx.x < m) {
+      const int k = threadIdx.x, xa = 2 * (st.x + k), xb = xa + 1;
+      const int qa = job.mode == 0 ? xa : job.qlist[xa];
+      const int qb = xb < job.nq ? (job.mode == 0 ? xb : job.qlist[xb]) : -1;
+      s_q[k][0] = qa;
+      s_q[k][1] = qb;
+      s_len[k][0] = ss.len[qa];
+      s_len[k][1] = qb >= 0 ? ss.len[qb] : 0;
+      s_res[k][0] = ss.res + ss.pstart[qa];
+      s_res[k][1] = ss.res + ss.pstart[qb >= 0 ? qb : qa];
+      s_qsum[k][0] = s_qsum[k][1] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int r = 0;
+      for (int k = 0; k < m; ++k) {
+        s_start[k] = r;
+        r += dround_up(max(s_len[k][0], s_len[k][1]), R);
+      }
+      s_start[m] = r;
+    }
+    __syncthreads();
+    const int rows = s_start[m];
+    const int np = (rows + G * R - 1) / (G * R);
     const int prow = np * G * R;
+    for (int b = threadIdx.x; b < prow / R; b += NT) {
+      int k = -1;
+      if (b * R < rows)
+        for (k = m - 1; s_start[k] > b * R; --k) {}
+      s_blk[b] = k;
+    }
+    for (int i = threadIdx.x; i < NG * kMaxSeg * 2; i += NT) s_best[i] = 0;
+    __syncthreads();
     for (int idx = threadIdx.x; idx < (K + 1) * prow; idx += NT) {
       const int r = idx / prow, i = idx - r * prow;
       uint32_t a = 0, b = 0;  // padding: score -o
-      if (r < K) {
-        if (i < LqA) a = (uint32_t)(sM[ra[i] * K + r] + o);
-        if (i < LqB) b = (uint32_t)(sM[rb[i] * K + r] + o);
+      const int k = s_blk[i / R];
+      if (r < K && k >= 0) {
+        const int li = i - s_start[k];
+        if (li < s_len[k][0]) a = (uint32_t)(sM[s_res[k][0][li] * K + r] + o);
+        if (li < s_len[k][1]) b = (uint32_t)(sM[s_res[k][1][li] * K + r] + o);
       }
       smem32[r * stride + i] = a | (b << 16);
     }
     __syncthreads();
 
+    const int xf = 2 * st.x;  // mode 0: the stream's subjects start at its first query
+    const int s0 = (job.mode == 0 ? xf : job.sub_off) + (int)(item - job.prefix[lo]) * NG;
+    const int send = job.mode == 0 ? ss.n : job.sub_off + job.sub_n;
     const int s = s0 + g;
     const bool valid = s < send;
     const int Ls = valid ? ss.len[s] : 0;
     const uint8_t *rs = ss.res + (valid ? ss.pstart[s] : 0);
     const int Lw = __reduce_max_sync(MSA_FULL_MASK, Ls);
-    int best = 0;
     if (Lw > 0) {
       for (int p = 0; p < np; ++p) {
         const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
         int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
         const uint32_t *pp = smem32 + p * G * R;
+        const int blk = p * G + t, kseg = s_blk[blk];
+        const bool top = kseg >= 0 && blk * R == s_start[kseg];
         int b;
         if (np == 1)
-          b = wave_pass_pp<G, R, false, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
+          b = wave_pass_pp<G, R, false, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, top, sin, sout);
         else if (p == 0)
-          b = wave_pass_pp<G, R, false, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
+          b = wave_pass_pp<G, R, false, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, top, sin, sout);
         else if (p + 1 == np)
-          b = wave_pass_pp<G, R, true, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
+          b = wave_pass_pp<G, R, true, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, top, sin, sout);
         else
-          b = wave_pass_pp<G, R, true, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, sin, sout);
-        best = Cell<true>::vmax(best, b);
+          b = wave_pass_pp<G, R, true, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, top, sin, sout);
+        if (kseg >= 0) {
+          atomicMax(&gbest[2 * kseg], Cell<true>::lane0(b));
+          atomicMax(&gbest[2 * kseg + 1], Cell<true>::lane1(b));
+        }
         __syncwarp();
       }
     }
+    __syncwarp();
+    // every query of the stream against this group's subject
+    if (valid) {
+      unsigned long long sub = 0ull;
+      for (int k = t; k < m; k += G) {
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1)
-      best = Cell<true>::vmax(best, __shfl_xor_sync(MSA_FULL_MASK, best, off));
-    if (t == 0 && valid) {
-#pragma unroll
-      for (int l = 0; l < 2; ++l) {
-        const int q = l ? qB : qA;
-        if (q < 0) continue;
-        // all pairs: lane B's first subject (the lane-A query) is counted by lane A
-        if (job.mode == 0 && l == 1 && s < qB) continue;
-        const int S = l ? Cell<true>::lane1(best) : Cell<true>::lane0(best);
-        if (S > job.sat_thresh) {
-          const unsigned slot = atomicAdd(job.ovf_count, 1u);
-          if (slot < (unsigned)job.ovf_cap) job.ovf[slot] = make_int2(q, s);
-          else atomicOr(job.err, MSA_DERR_OVERFLOW);
-          continue;
-        }
-        if (job.mode == 0) {
-          if (s == q) job.self[q] = S;
-          else {
-            atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
-            atomicAdd(&s_qsum[l], (unsigned long long)(long long)S);
+        for (int l = 0; l < 2; ++l) {
+          const int q = s_q[k][l];
+          if (q < 0) continue;
+          if (job.mode == 0 && s < q) continue;  // counted as (s, q) by the earlier query
+          const int S = gbest[2 * k + l];
+          if (S > job.sat_thresh) {
+            const unsigned slot = atomicAdd(job.ovf_count, 1u);
+            if (slot < (unsigned)job.ovf_cap) job.ovf[slot] = make_int2(q, s);
+            else atomicOr(job.err, MSA_DERR_OVERFLOW);
+            continue;
           }
-        } else if (job.mode == 1) {
-          atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
-        } else {
-          atomicAdd(&s_qsum[l], (unsigned long long)(long long)S);
+          if (job.mode == 0) {
+            if (s == q) job.self[q] = S;
+            else {
+              sub += (unsigned long long)(long long)S;
+              atomicAdd(&s_qsum[k][l], (unsigned long long)(long long)S);
+            }
+          } else if (job.mode == 1) {
+            sub += (unsigned long long)(long long)S;
+          } else {
+            atomicAdd(&s_qsum[k][l], (unsigned long long)(long long)S);
+          }
         }
       }
+      if (sub) atomicAdd(&job.pairsum[s], sub);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && job.mode != 1) {
-      if (s_qsum[0]) atomicAdd(&job.pairsum[qA], s_qsum[0]);
-      if (qB >= 0 && s_qsum[1]) atomicAdd(&job.pairsum[qB], s_qsum[1]);
+    if (job.mode != 1 && threadIdx.x < 2 * m) {
+      const int k = threadIdx.x >> 1, l = threadIdx.x & 1;
+      if (s_q[k][l] >= 0 && s_qsum[k][l]) atomicAdd(&job.pairsum[s_q[k][l]], s_qsum[k][l]);
     }
   }
 }
@@ -878,10 +922,21 @@ const CenterVariant kCenterVariants[] = {
     {0, 16, 16, false}, {0, 32, 16, false}};
 const int kNumCenterVariants = sizeof(kCenterVariants) / sizeof(kCenterVariants[0]);
 
-int center_smem_bytes(int variant, int K, int rows_alloc) {
+int center_profile_bytes(int variant, int K, int rows_alloc) {
   const CenterVariant &v = kCenterVariants[variant];
   if (v.paired) return (K + 1) * round_up_int(rows_alloc, 32) * 4;
   return (K + 1) * round_up_int(rows_alloc, MSA_PROF_ALIGN);
+}
+
+// paired: the profile, then the segment of every R-row block and the
+// per-group best scores of every segment
+int center_smem_bytes(int variant, int K, int rows_alloc) {
+  const CenterVariant &v = kCenterVariants[variant];
+  int b = center_profile_bytes(variant, K, rows_alloc);
+  if (v.paired)
+    b += round_up_int(round_up_int(rows_alloc, 32) / v.R + 1, 4) * 4 +
+         (kCenterThreads / v.G) * kMaxSeg * 8;
+  return b;
 }
 
 typedef void (*center_fn)(SeqSet, Scoring, CenterJob);
@@ -914,8 +969,7 @@ static int sm_count() {
 }
 
 static int occupancy_grid(const void *fn, int threads, int smem) {
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (per_sm < 1) per_sm = 1;
@@ -928,10 +982,11 @@ int center_grid(int variant, int smem) {
   return occupancy_grid((const void *)fn, kCenterThreads, smem);
 }
 
+// (static shared memory counts against the 48 KB default too, so the limit
+// is raised whatever the dynamic size)
 cudaError_t center_allow_smem(int variant, int smem) {
   center_fn fn = center_kernel(variant);
   if (!fn) return cudaErrorInvalidValue;
-  if (smem <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
@@ -967,7 +1022,7 @@ cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJ
   pairs_fn fn = pairs_kernel(G);
   if (!fn) return cudaErrorInvalidValue;
   const int smem = pairs_smem(G, sc.K);
-  if (smem > 48 * 1024)
+  if (smem > 40 * 1024)  // static shared memory counts too
     cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   fn<<<grid, 256, smem, st>>>(ss, sc, job);
   return cudaGetLastError();
@@ -1014,7 +1069,7 @@ cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc
   codes_fn fn = codes_kernel(G, packed);
   if (!fn) return cudaErrorInvalidValue;
   const int smem = codes_smem_bytes(sc.K, job.npass * G * kCodesR);
-  if (smem > 48 * 1024)
+  if (smem > 40 * 1024)  // static shared memory counts too
     cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   fn<<<grid, 256, smem, st>>>(ss, sc, job);
   return cudaGetLastError();

@@ -33,7 +33,13 @@ struct CenterJob {
   int sat_thresh;                 // packed cells: lanes whose best exceeds this are re-run in int32
   int2 *ovf; unsigned *ovf_count; int ovf_cap; unsigned *err;
   int2 *scratch; int scratch_cols;
+  // paired classes: the unit is a stream of consecutive query pairs stacked
+  // in one row range, streams[u] = {first pair, pair count <= kMaxSeg}
+  const int2 *streams;
 };
+
+// Query pairs one stream of the paired center kernel may stack.
+constexpr int kMaxSeg = 32;
 
 // Arbitrary pair list (int32 cells).
 struct PairJob {
@@ -64,7 +70,10 @@ struct CenterVariant { int paired, G, R; bool packed; };
 extern const CenterVariant kCenterVariants[];
 extern const int kNumCenterVariants;
 
+// dynamic shared memory of a center launch whose units need rows_alloc
+// profile rows; center_profile_bytes: the profile part alone
 int center_smem_bytes(int variant, int K, int rows_alloc);
+int center_profile_bytes(int variant, int K, int rows_alloc);
 // set_smem = false: the caller has already raised the kernel's dynamic
 // shared-memory limit with center_allow_smem (required while a stream is
 // being captured into a graph).
