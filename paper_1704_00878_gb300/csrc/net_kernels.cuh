@@ -57,6 +57,11 @@ cudaError_t conv_tc(int cin, int cout, int mode, const __nv_bfloat16 *x, const _
                     const float *bias, const int32_t *rowseq, const __nv_bfloat16 *prev, void *y,
                     int T, unsigned *err, cudaStream_t st, long long spins = 0,
                     bool no_loads = false);
+// The weight gradient below on the tcgen05 tensor cores (tc_conv.cu) for 128
+// input channels and 128 or 64 output channels (fp32 atomics into dw).
+bool wgrad_tc_supported(int cin, int cout);
+cudaError_t wgrad_tc(int cin, int cout, const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw,
+                     int T, unsigned *err, cudaStream_t st, long long spins = 0);
 // dW[tap][ci][co] += sum_r x[r + tap - 4][ci] * dy[r][co]   (fp32 atomics)
 cudaError_t wgrad(int cin, int cout, const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw,
                   int T, cudaStream_t st);

@@ -145,6 +145,13 @@ int build_batch(msa_ctx *ctx, Selector *s, const std::vector<int32_t> &seqs, net
   return MSA_OK;
 }
 
+// One weight gradient: the tcgen05 kernel where it has the shape, else mma.sync.
+cudaError_t wgrad(msa_ctx *ctx, int cin, int cout, const bf16 *x, const bf16 *dy, float *dw, int T) {
+  ++ctx->launches;
+  if (net::wgrad_tc_supported(cin, cout)) return net::wgrad_tc(cin, cout, x, dy, dw, T, ctx->derr, ctx->st);
+  return net::wgrad(cin, cout, x, dy, dw, T, ctx->st);
+}
+
 // One convolution: the tcgen05 kernel where it has the shape, else mma.sync.
 cudaError_t conv(msa_ctx *ctx, int cin, int cout, int mode, const bf16 *x, const bf16 *w,
                  const float *bias, const int32_t *rowseq, const bf16 *prev, void *y, int T) {
@@ -181,19 +188,19 @@ int forward_backward(msa_ctx *ctx, Selector *s, const net::Batch &b, int npairs)
   CK((++ctx->launches, net::pair_loss)(P<int2>(s->bpairs), P<float>(s->btargets), npairs, P<float>(s->emb), P<float>(s->demb), P<float>(s->loss), ctx->st));
   CK((++ctx->launches, net::pool_backward)(b, P<float>(s->demb), P<bf16>(s->dy4), ctx->st));
   // layer 4 (linear)
-  CK((++ctx->launches, net::wgrad)(net::WD, net::DIM, P<bf16>(s->a3), P<bf16>(s->dy4), g + net::W4_OFF, T, ctx->st));
+  CK(wgrad(ctx, net::WD, net::DIM, P<bf16>(s->a3), P<bf16>(s->dy4), g + net::W4_OFF, T));
   CK((++ctx->launches, net::colsum)(net::DIM, P<bf16>(s->dy4), g + net::B4_OFF, T, ctx->st));
   CK(conv(ctx, net::DIM, net::WD, 2, P<bf16>(s->dy4), P<bf16>(s->w4n), nullptr, b.rowseq, P<bf16>(s->a3), s->dz3.p, T));
   // layer 3
-  CK((++ctx->launches, net::wgrad)(net::WD, net::WD, P<bf16>(s->a2), P<bf16>(s->dz3), g + net::W3_OFF, T, ctx->st));
+  CK(wgrad(ctx, net::WD, net::WD, P<bf16>(s->a2), P<bf16>(s->dz3), g + net::W3_OFF, T));
   CK((++ctx->launches, net::colsum)(net::WD, P<bf16>(s->dz3), g + net::B3_OFF, T, ctx->st));
   CK(conv(ctx, net::WD, net::WD, 2, P<bf16>(s->dz3), P<bf16>(s->w3n), nullptr, b.rowseq, P<bf16>(s->a2), s->dz2.p, T));
   // layer 2
-  CK((++ctx->launches, net::wgrad)(net::WD, net::WD, P<bf16>(s->a1), P<bf16>(s->dz2), g + net::W2_OFF, T, ctx->st));
+  CK(wgrad(ctx, net::WD, net::WD, P<bf16>(s->a1), P<bf16>(s->dz2), g + net::W2_OFF, T));
   CK((++ctx->launches, net::colsum)(net::WD, P<bf16>(s->dz2), g + net::B2_OFF, T, ctx->st));
   CK(conv(ctx, net::WD, net::WD, 2, P<bf16>(s->dz2), P<bf16>(s->w2n), nullptr, b.rowseq, P<bf16>(s->a1), s->dz1.p, T));
   // layer 1 (one-hot input: no data gradient)
-  CK((++ctx->launches, net::wgrad)(net::KP, net::WD, P<bf16>(s->x0), P<bf16>(s->dz1), g + net::W1_OFF, T, ctx->st));
+  CK(wgrad(ctx, net::KP, net::WD, P<bf16>(s->x0), P<bf16>(s->dz1), g + net::W1_OFF, T));
   CK((++ctx->launches, net::colsum)(net::WD, P<bf16>(s->dz1), g + net::B1_OFF, T, ctx->st));
   return MSA_OK;
 }

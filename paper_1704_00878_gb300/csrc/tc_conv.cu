@@ -345,6 +345,170 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
 }
 
+// ---------------------------------------------------------------- weight gradient
+// dW[t][ci][co] += sum_r x[r + t - 4][ci] * dy[r][co] for 128 input channels.
+// Per tap a GEMM with M = ci (128), N = co (COUT), K = the rows.  Both
+// operands come straight from the row-major activations, so both are
+// MN-major (channels contiguous, rows the reduction): TMA loads a chunk of
+// 64 rows of dy and the same rows of x plus the halo of the CTA's taps, in
+// the 128-byte swizzle, and tap t is again a start address t rows further.
+// A CTA owns 3 taps (3 x COUT fp32 accumulator columns in TMEM) and a
+// contiguous, 64-aligned range of rows, pipelined over 4 stages by a TMA
+// warp and an MMA warp; at the end its four epilogue warps add the partial
+// dW to global memory with fp32 atomics.
+constexpr int WG_TAPS = 3;    // taps per CTA
+constexpr int WG_KR = 64;     // rows per chunk
+constexpr int WG_AROWS = 72;  // chunk + halo of 3 taps (66), rounded up to 8
+constexpr int WG_STAGES = 4;
+
+template <int COUT> struct WGeo {
+  static constexpr int A_BLOCK = WG_AROWS * 128;  // one 64-channel block of x
+  static constexpr int A_BYTES = 2 * A_BLOCK;     // 128 channels
+  static constexpr int B_BLOCK = WG_KR * 128;     // one 64-channel block of dy
+  static constexpr int B_BYTES = (COUT / 64) * B_BLOCK;
+  static constexpr int STAGE = (A_BYTES + B_BYTES + 1023) / 1024 * 1024;
+  static constexpr int SMEM = WG_STAGES * STAGE + 1024;
+  static constexpr int TMEM_COLS = WG_TAPS * COUT <= 256 ? 256 : 512;
+};
+
+// MN-major operand in the 128-byte swizzle: 64-element MN blocks `lbo` bytes
+// apart (leading-dimension offset), 8-row K groups 1024 bytes apart
+// (stride-dimension offset), version 1, layout type 2.
+__device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3fff);
+  d |= (uint64_t)((lbo >> 4) & 0x3fff) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// kind::f16, fp32 accumulator, bf16 A and B, both MN-major (bits 15, 16),
+// N = COUT, M = 128
+template <int COUT>
+__host__ __device__ constexpr uint32_t wg_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(COUT >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int COUT>
+__device__ __forceinline__ void umma_wg(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(wg_idesc<COUT>()), "r"(accumulate)
+      : "memory");
+}
+
+// grid: (row splits, 3 tap groups); rows [split * per, min(T, (split + 1) * per)), per % 64 == 0
+template <int COUT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dymap,
+           float *__restrict__ dw, int T, int per, unsigned *err, long long spins) {
+  using Gm = WGeo<COUT>;
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) unsigned long long bars[2 * WG_STAGES + 1];
+  __shared__ uint32_t tmem_slot;
+  const uint32_t raw = smem_u32(tc_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int t0 = (int)blockIdx.y * WG_TAPS;
+  const int r_begin = (int)blockIdx.x * per, r_end = min(T, r_begin + per);
+  const int nchunks = r_end > r_begin ? (r_end - r_begin + WG_KR - 1) / WG_KR : 0;
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[WG_STAGES + s]); };
+  const uint32_t done = smem_u32(&bars[2 * WG_STAGES]);
+  if (tid == 0) {
+    for (int s = 0; s < WG_STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(Gm::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int s = c % WG_STAGES, k = c / WG_STAGES;
+        if (k > 0 && !mbar_wait(empty(s), (uint32_t)((k - 1) & 1), spins)) { ok = false; break; }
+        const uint32_t sA = base + (uint32_t)(s * Gm::STAGE), sB = sA + Gm::A_BYTES;
+        const int r0 = r_begin + c * WG_KR;
+        mbar_expect_tx(full(s), (uint32_t)(Gm::A_BYTES + Gm::B_BYTES));
+        for (int h = 0; h < 2; ++h)
+          tma_load_2d(sA + (uint32_t)(h * Gm::A_BLOCK), &xmap, h * 64, r0 - HALF + t0, full(s));
+        for (int h = 0; h < COUT / 64; ++h)
+          tma_load_2d(sB + (uint32_t)(h * Gm::B_BLOCK), &dymap, h * 64, r0, full(s));
+      }
+      // the last loads of each stage land before the CTA may exit
+      for (int c = max(0, nchunks - WG_STAGES); c < nchunks; ++c)
+        mbar_wait(full(c % WG_STAGES), (uint32_t)((c / WG_STAGES) & 1), spins);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % WG_STAGES, k = c / WG_STAGES;
+        if (!mbar_wait(full(s), (uint32_t)(k & 1), spins)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sA = base + (uint32_t)(s * Gm::STAGE), sB = sA + Gm::A_BYTES;
+#pragma unroll
+        for (int tl = 0; tl < WG_TAPS; ++tl) {
+#pragma unroll
+          for (int kk = 0; kk < WG_KR / 16; ++kk) {
+            const uint64_t ad = mn_desc(sA + (uint32_t)((tl + 16 * kk) * 128), (uint32_t)Gm::A_BLOCK);
+            const uint64_t bd = mn_desc(sB + (uint32_t)(16 * kk * 128), (uint32_t)Gm::B_BLOCK);
+            umma_wg<COUT>(tmem + (uint32_t)(tl * COUT), ad, bd, (c | kk) != 0 ? 1u : 0u);
+          }
+        }
+        umma_commit(empty(s));
+      }
+      if (ok && nchunks > 0) umma_commit(done);
+      // no MMA may still run at exit: the last chunk's release (bounded)
+      if (nchunks > 0)
+        mbar_wait(empty((nchunks - 1) % WG_STAGES), (uint32_t)(((nchunks - 1) / WG_STAGES) & 1), spins);
+    }
+  } else if (nchunks > 0) {
+    // epilogue: warp w holds ci = 32 (w % 4) + lane of every tap's accumulator
+    const int q = warp & 3;
+    if (!mbar_wait(done, 0, spins)) {
+      ok = false;
+    } else {
+      tc_fence_after();
+      const int ci = q * 32 + lane;
+#pragma unroll 1
+      for (int tl = 0; tl < WG_TAPS; ++tl) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < COUT; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tl * COUT + c0), v);
+          float *d = dw + ((size_t)(t0 + tl) * 128 + ci) * COUT + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) atomicAdd(d + j, v[j]);
+        }
+      }
+    }
+  }
+  if (!ok) atomicOr(err, MSA_DERR_TIMEOUT_TC);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Gm::TMEM_COLS));
+}
+
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -409,7 +573,38 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int
   return cudaGetLastError();
 }
 
+template <int COUT>
+cudaError_t launch_wgrad_tc(const bf16 *x, const bf16 *dy, float *dw, int T, unsigned *err,
+                            cudaStream_t st, long long spins) {
+  using Gm = WGeo<COUT>;
+  CUtensorMap xm, dm;
+  if (!make_map(&xm, x, (uint64_t)T, 128, WG_AROWS, 64) || !make_map(&dm, dy, (uint64_t)T, COUT, WG_KR, 64))
+    return cudaErrorInvalidValue;
+  auto fn = k_wgrad_tc<COUT>;
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
+  if (e != cudaSuccess) return e;
+  // about 8 chunks per CTA at least, one CTA per SM at most
+  const int chunks = (T + WG_KR - 1) / WG_KR;
+  const int groups = TAPS / WG_TAPS;
+  const int splits = std::max(1, std::min(sm_count() / groups, (chunks + 7) / 8));
+  const int per = (chunks + splits - 1) / splits * WG_KR;
+  const dim3 grid((T + per - 1) / per, groups);
+  fn<<<grid, TC_THREADS, Gm::SMEM, st>>>(xm, dm, dw, T, per, err, spins);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool wgrad_tc_supported(int cin, int cout) { return cin == 128 && (cout == 128 || cout == 64); }
+
+cudaError_t wgrad_tc(int cin, int cout, const bf16 *x, const bf16 *dy, float *dw, int T,
+                     unsigned *err, cudaStream_t st, long long spins) {
+  if (T <= 0) return cudaSuccess;
+  if (spins <= 0) spins = kSpinLimit;
+  if (cin == 128 && cout == 128) return launch_wgrad_tc<128>(x, dy, dw, T, err, st, spins);
+  if (cin == 128 && cout == 64) return launch_wgrad_tc<64>(x, dy, dw, T, err, st, spins);
+  return cudaErrorInvalidValue;
+}
 
 bool conv_tc_supported(int cin, int cout, int mode) {
   return (cin == 128 && cout == 128 && (mode == 0 || mode == 2)) || (cin == 128 && cout == 64 && mode == 1) ||
