@@ -1,12 +1,7 @@
-// net_kernels.cu -- kernels of the learned center selector.
-//
-// The 9-tap 1-D convolutions are implicit GEMMs on the tensor cores
-// (mma.sync m16n8k16, bf16 operands, fp32 accumulation): rows = positions of
-// the flat batch, reduction = taps x input channels.  A CTA stages 128 output
-// rows plus the 8 halo rows of its input tile once, then streams one tap of
-// weights at a time; each of its 8 warps owns 16 rows and every output
-// channel.  The weight gradient is the same contraction with the positions as
-// the reduction (both operands read transposed with ldmatrix.trans).
+// net_kernels.cu -- the selector's small kernels: batch layout, one-hot
+// input, bias gradients, pooling, the pair loss, Adam, weight refresh and the
+// embedding-space center.  The convolutions and weight gradients run on the
+// tensor cores in tc_conv.cu.
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -17,175 +12,6 @@ namespace net {
 namespace {
 
 typedef __nv_bfloat16 bf16;
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-// d += a (16x16, row) * b (16x8, col)
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-constexpr int BM = 128;  // output rows per CTA
-
-template <int CIN, int COUT>
-constexpr int conv_smem() { return ((BM + 2 * HALF) * (CIN + 8) + COUT * (CIN + 8)) * 2; }
-
-template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(256) k_conv(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
-                                              const float *__restrict__ bias,
-                                              const int32_t *__restrict__ rowseq,
-                                              const bf16 *__restrict__ prev, void *__restrict__ y,
-                                              int T) {
-  constexpr int SA = CIN + 8, SB = CIN + 8, CH = CIN / 8;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  bf16 *sA = reinterpret_cast<bf16 *>(smraw);
-  bf16 *sB = sA + (BM + 2 * HALF) * SA;
-  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  const int r0 = blockIdx.x * BM;
-  for (int idx = tid; idx < (BM + 2 * HALF) * CH; idx += 256) {
-    const int i = idx / CH, c = idx - i * CH;
-    const int r = r0 - HALF + i;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (r >= 0 && r < T) v = *reinterpret_cast<const uint4 *>(x + (size_t)r * CIN + c * 8);
-    *reinterpret_cast<uint4 *>(sA + i * SA + c * 8) = v;
-  }
-  float acc[COUT / 8][4];
-#pragma unroll
-  for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-
-  for (int tap = 0; tap < TAPS; ++tap) {
-    const int wt = MODE == 2 ? TAPS - 1 - tap : tap;
-    __syncthreads();
-    for (int idx = tid; idx < COUT * CH; idx += 256) {
-      const int n = idx / CH, c = idx - n * CH;
-      *reinterpret_cast<uint4 *>(sB + n * SB + c * 8) =
-          *reinterpret_cast<const uint4 *>(w + ((size_t)wt * COUT + n) * CIN + c * 8);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kc = 0; kc < CIN / 16; ++kc) {
-      uint32_t a[4];
-      ldsm_x4(a, sA + (wp * 16 + tap + (lane & 15)) * SA + kc * 16 + (lane >> 4) * 8);
-#pragma unroll
-      for (int j = 0; j < COUT / 16; ++j) {
-        uint32_t b[4];
-        ldsm_x4(b, sB + ((2 * j + (lane >> 4)) * 8 + (lane & 7)) * SB + kc * 16 + ((lane >> 3) & 1) * 8);
-        mma16816(acc[2 * j], a, b[0], b[1]);
-        mma16816(acc[2 * j + 1], a, b[2], b[3]);
-      }
-    }
-  }
-  const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = r0 + wp * 16 + gid + 8 * h;
-    if (r >= T) continue;
-    const bool valid = rowseq[r] >= 0;
-#pragma unroll
-    for (int nt = 0; nt < COUT / 8; ++nt) {
-      const int c = nt * 8 + tig * 2;
-      float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
-      if constexpr (MODE == 0) {
-        v0 = valid ? fmaxf(v0 + bias[c], 0.f) : 0.f;
-        v1 = valid ? fmaxf(v1 + bias[c + 1], 0.f) : 0.f;
-        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(y) + (size_t)r * COUT + c) =
-            __floats2bfloat162_rn(v0, v1);
-      } else if constexpr (MODE == 1) {
-        v0 = valid ? v0 + bias[c] : 0.f;
-        v1 = valid ? v1 + bias[c + 1] : 0.f;
-        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(y) + (size_t)r * COUT + c) =
-            make_float2(v0, v1);
-      } else {
-        const __nv_bfloat162 pv =
-            *reinterpret_cast<const __nv_bfloat162 *>(prev + (size_t)r * COUT + c);
-        v0 = valid && __bfloat162float(pv.x) > 0.f ? v0 : 0.f;
-        v1 = valid && __bfloat162float(pv.y) > 0.f ? v1 : 0.f;
-        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(y) + (size_t)r * COUT + c) =
-            __floats2bfloat162_rn(v0, v1);
-      }
-    }
-  }
-}
-
-// dW[tap][ci][co] += sum over rows r of x[r + tap - 4][ci] * dy[r][co].
-// CTA = (chunk of rows, tap); warps tile ci x co; partials meet in fp32
-// atomics.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_wgrad(const bf16 *__restrict__ x, const bf16 *__restrict__ dy,
-                                               float *__restrict__ dw, int T, int chunk) {
-  constexpr int KS = 64, SX = CIN + 8, SD = COUT + 8;
-  constexpr int WM = CIN / 16, WN = 8 / WM, NT = COUT / (8 * WN);
-  static_assert(WM * WN == 8 && NT % 2 == 0, "warp tiling");
-  __shared__ __align__(16) bf16 sX[KS * SX];
-  __shared__ __align__(16) bf16 sD[KS * SD];
-  const int tap = blockIdx.y;
-  const int c0 = blockIdx.x * chunk, c1 = min(T, c0 + chunk);
-  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  const int wm = wp % WM, wn = wp / WM;
-  float acc[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  for (int p0 = c0; p0 < c1; p0 += KS) {
-    __syncthreads();
-    for (int idx = tid; idx < KS * (CIN / 8); idx += 256) {
-      const int i = idx / (CIN / 8), c = idx - i * (CIN / 8);
-      const int r = p0 + i + tap - HALF;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (r >= 0 && r < T) v = *reinterpret_cast<const uint4 *>(x + (size_t)r * CIN + c * 8);
-      *reinterpret_cast<uint4 *>(sX + i * SX + c * 8) = v;
-    }
-    for (int idx = tid; idx < KS * (COUT / 8); idx += 256) {
-      const int i = idx / (COUT / 8), c = idx - i * (COUT / 8);
-      const int r = p0 + i;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (r < c1) v = *reinterpret_cast<const uint4 *>(dy + (size_t)r * COUT + c * 8);
-      *reinterpret_cast<uint4 *>(sD + i * SD + c * 8) = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < KS / 16; ++kk) {
-      uint32_t a[4];
-      ldsm_x4_t(a, sX + (kk * 16 + (lane >> 4) * 8 + (lane & 7)) * SX + wm * 16 + ((lane >> 3) & 1) * 8);
-#pragma unroll
-      for (int j = 0; j < NT / 2; ++j) {
-        uint32_t b[4];
-        ldsm_x4_t(b, sD + (kk * 16 + ((lane >> 3) & 1) * 8 + (lane & 7)) * SD +
-                         (wn * NT + 2 * j + (lane >> 4)) * 8);
-        mma16816(acc[2 * j], a, b[0], b[1]);
-        mma16816(acc[2 * j + 1], a, b[2], b[3]);
-      }
-    }
-  }
-  const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int ci = wm * 16 + gid + 8 * h;
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const int co = (wn * NT + nt) * 8 + tig * 2;
-      float *d = dw + ((size_t)tap * CIN + ci) * COUT + co;
-      atomicAdd(d, acc[nt][2 * h]);
-      atomicAdd(d + 1, acc[nt][2 * h + 1]);
-    }
-  }
-}
 
 __global__ void k_colsum(int cout, const bf16 *__restrict__ dy, float *__restrict__ db, int T,
                          int chunk) {
@@ -342,19 +168,6 @@ __global__ void k_key_to_idx(const unsigned long long *key, long long *out) {
   *out = (long long)(*key & 0xffffffffull);
 }
 
-template <int CIN, int COUT, int MODE>
-cudaError_t launch_conv(const bf16 *x, const bf16 *w, const float *bias, const int32_t *rowseq,
-                        const bf16 *prev, void *y, int T, cudaStream_t st) {
-  constexpr int smem = conv_smem<CIN, COUT>();
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_conv<CIN, COUT, MODE><<<(T + BM - 1) / BM, 256, smem, st>>>(x, w, bias, rowseq, prev, y, T);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t fill_rows(const Batch &b, cudaStream_t st) {
@@ -368,32 +181,6 @@ cudaError_t fill_rows(const Batch &b, cudaStream_t st) {
 cudaError_t onehot(const Batch &b, const uint8_t *res, const int64_t *pstart, bf16 *x0,
                    cudaStream_t st) {
   k_onehot<<<(b.T + 255) / 256, 256, 0, st>>>(b, res, pstart, x0);
-  return cudaGetLastError();
-}
-
-cudaError_t conv(int cin, int cout, int mode, const bf16 *x, const bf16 *w, const float *bias,
-                 const int32_t *rowseq, const bf16 *prev, void *y, int T, cudaStream_t st) {
-  if (T <= 0) return cudaSuccess;
-#define NET_CONV(CI, CO, MD) \
-  if (cin == CI && cout == CO && mode == MD) return launch_conv<CI, CO, MD>(x, w, bias, rowseq, prev, y, T, st);
-  NET_CONV(32, 128, 0)
-  NET_CONV(128, 128, 0)
-  NET_CONV(128, 64, 1)
-  NET_CONV(64, 128, 2)
-  NET_CONV(128, 128, 2)
-#undef NET_CONV
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t wgrad(int cin, int cout, const bf16 *x, const bf16 *dy, float *dw, int T,
-                  cudaStream_t st) {
-  if (T <= 0) return cudaSuccess;
-  const int chunk = 2048;
-  dim3 grid((T + chunk - 1) / chunk, TAPS);
-  if (cin == 32 && cout == 128) k_wgrad<32, 128><<<grid, 256, 0, st>>>(x, dy, dw, T, chunk);
-  else if (cin == 128 && cout == 128) k_wgrad<128, 128><<<grid, 256, 0, st>>>(x, dy, dw, T, chunk);
-  else if (cin == 128 && cout == 64) k_wgrad<128, 64><<<grid, 256, 0, st>>>(x, dy, dw, T, chunk);
-  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

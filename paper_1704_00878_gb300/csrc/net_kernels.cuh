@@ -40,31 +40,24 @@ cudaError_t fill_rows(const Batch &b, cudaStream_t st);
 cudaError_t onehot(const Batch &b, const uint8_t *res, const int64_t *pstart, __nv_bfloat16 *x0,
                    cudaStream_t st);
 
-// mode 0: relu(x * W + b) -> bf16; mode 1: x * W + b -> fp32; mode 2 (data
-// gradient): (dy * W^T, taps reversed) masked by prev > 0 -> bf16.  Padding
-// rows are written as zero.  w: bf16 [9][cout][cin] ([tap][n][k]).
-cudaError_t conv(int cin, int cout, int mode, const __nv_bfloat16 *x, const __nv_bfloat16 *w,
-                 const float *bias, const int32_t *rowseq, const __nv_bfloat16 *prev, void *y,
-                 int T, cudaStream_t st);
-// The same convolutions on the tcgen05 tensor cores (tc_conv.cu): (32, 128)
-// and (128, 128) mode 0, (128, 128) and (64, 128) mode 2, (128, 64) mode 1.
-// w as above; err: device error word (MSA_DERR_TIMEOUT_TC).  spins: polls
+// The 9-tap convolutions on the tcgen05 tensor cores (tc_conv.cu): (cin,
+// cout) = (32, 128) and (128, 128) mode 0, (128, 128) and (64, 128) mode 2,
+// (128, 64) mode 1.  mode 0: relu(x * W + b) -> bf16; mode 1: x * W + b ->
+// fp32; mode 2 (data gradient): (dy * W^T, taps reversed) masked by prev >
+// 0 -> bf16.  Padding rows are written as zero.  w: bf16 [9][cout][cin]
+// ([tap][n][k]).  err: device error word (MSA_DERR_TIMEOUT_TC).  spins: polls
 // before an mbarrier wait gives up (<= 0: the default, seconds); no_loads:
 // the TMA warp issues nothing, so every wait runs out (the self-test of the
 // bounded waits).
-bool conv_tc_supported(int cin, int cout, int mode);
 cudaError_t conv_tc(int cin, int cout, int mode, const __nv_bfloat16 *x, const __nv_bfloat16 *w,
                     const float *bias, const int32_t *rowseq, const __nv_bfloat16 *prev, void *y,
                     int T, unsigned *err, cudaStream_t st, long long spins = 0,
                     bool no_loads = false);
-// The weight gradient below on the tcgen05 tensor cores (tc_conv.cu) for 128
-// input channels and 128 or 64 output channels (fp32 atomics into dw).
-bool wgrad_tc_supported(int cin, int cout);
+// dW[tap][ci][co] += sum_r x[r + tap - 4][ci] * dy[r][co] on the tcgen05
+// tensor cores (tc_conv.cu): 128 input channels with 128 or 64 output
+// channels, and 32 with 128 (fp32 atomics into dw).
 cudaError_t wgrad_tc(int cin, int cout, const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw,
                      int T, unsigned *err, cudaStream_t st, long long spins = 0);
-// dW[tap][ci][co] += sum_r x[r + tap - 4][ci] * dy[r][co]   (fp32 atomics)
-cudaError_t wgrad(int cin, int cout, const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw,
-                  int T, cudaStream_t st);
 // db[c] += sum_r dy[r][c]
 cudaError_t colsum(int cout, const __nv_bfloat16 *dy, float *db, int T, cudaStream_t st);
 

@@ -145,20 +145,17 @@ int build_batch(msa_ctx *ctx, Selector *s, const std::vector<int32_t> &seqs, net
   return MSA_OK;
 }
 
-// One weight gradient: the tcgen05 kernel where it has the shape, else mma.sync.
+// One weight gradient / convolution on the tensor cores (every shape of the
+// network has its tcgen05 kernel).
 cudaError_t wgrad(msa_ctx *ctx, int cin, int cout, const bf16 *x, const bf16 *dy, float *dw, int T) {
   ++ctx->launches;
-  if (net::wgrad_tc_supported(cin, cout)) return net::wgrad_tc(cin, cout, x, dy, dw, T, ctx->derr, ctx->st);
-  return net::wgrad(cin, cout, x, dy, dw, T, ctx->st);
+  return net::wgrad_tc(cin, cout, x, dy, dw, T, ctx->derr, ctx->st);
 }
 
-// One convolution: the tcgen05 kernel where it has the shape, else mma.sync.
 cudaError_t conv(msa_ctx *ctx, int cin, int cout, int mode, const bf16 *x, const bf16 *w,
                  const float *bias, const int32_t *rowseq, const bf16 *prev, void *y, int T) {
   ++ctx->launches;
-  if (net::conv_tc_supported(cin, cout, mode))
-    return net::conv_tc(cin, cout, mode, x, w, bias, rowseq, prev, y, T, ctx->derr, ctx->st);
-  return net::conv(cin, cout, mode, x, w, bias, rowseq, prev, y, T, ctx->st);
+  return net::conv_tc(cin, cout, mode, x, w, bias, rowseq, prev, y, T, ctx->derr, ctx->st);
 }
 
 int forward(msa_ctx *ctx, Selector *s, const net::Batch &b) {

@@ -402,8 +402,10 @@ __device__ __forceinline__ void umma_wg(uint32_t tmem_d, uint64_t adesc, uint64_
       : "memory");
 }
 
-// grid: (row splits, 3 tap groups); rows [split * per, min(T, (split + 1) * per)), per % 64 == 0
-template <int COUT>
+// grid: (row splits, 3 tap groups); rows [split * per, min(T, (split + 1) * per)), per % 64 == 0.
+// CIN < 128 (the 32-channel one-hot input): the channels past CIN load as
+// zeros (outside the tensor) and their accumulator rows are not written.
+template <int CIN, int COUT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dymap,
            float *__restrict__ dw, int T, int per, unsigned *err, long long spins) {
@@ -494,7 +496,8 @@ k_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
         for (int c0 = 0; c0 < COUT; c0 += 32) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tl * COUT + c0), v);
-          float *d = dw + ((size_t)(t0 + tl) * 128 + ci) * COUT + c0;
+          if (ci >= CIN) continue;
+          float *d = dw + ((size_t)(t0 + tl) * CIN + ci) * COUT + c0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) atomicAdd(d + j, v[j]);
         }
@@ -573,14 +576,14 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int
   return cudaGetLastError();
 }
 
-template <int COUT>
+template <int CIN, int COUT>
 cudaError_t launch_wgrad_tc(const bf16 *x, const bf16 *dy, float *dw, int T, unsigned *err,
                             cudaStream_t st, long long spins) {
   using Gm = WGeo<COUT>;
   CUtensorMap xm, dm;
-  if (!make_map(&xm, x, (uint64_t)T, 128, WG_AROWS, 64) || !make_map(&dm, dy, (uint64_t)T, COUT, WG_KR, 64))
+  if (!make_map(&xm, x, (uint64_t)T, CIN, WG_AROWS, 64) || !make_map(&dm, dy, (uint64_t)T, COUT, WG_KR, 64))
     return cudaErrorInvalidValue;
-  auto fn = k_wgrad_tc<COUT>;
+  auto fn = k_wgrad_tc<CIN, COUT>;
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
   if (e != cudaSuccess) return e;
   // about 8 chunks per CTA at least, one CTA per SM at most
@@ -595,21 +598,17 @@ cudaError_t launch_wgrad_tc(const bf16 *x, const bf16 *dy, float *dw, int T, uns
 
 }  // namespace
 
-bool wgrad_tc_supported(int cin, int cout) { return cin == 128 && (cout == 128 || cout == 64); }
 
 cudaError_t wgrad_tc(int cin, int cout, const bf16 *x, const bf16 *dy, float *dw, int T,
                      unsigned *err, cudaStream_t st, long long spins) {
   if (T <= 0) return cudaSuccess;
   if (spins <= 0) spins = kSpinLimit;
-  if (cin == 128 && cout == 128) return launch_wgrad_tc<128>(x, dy, dw, T, err, st, spins);
-  if (cin == 128 && cout == 64) return launch_wgrad_tc<64>(x, dy, dw, T, err, st, spins);
+  if (cin == 128 && cout == 128) return launch_wgrad_tc<128, 128>(x, dy, dw, T, err, st, spins);
+  if (cin == 128 && cout == 64) return launch_wgrad_tc<128, 64>(x, dy, dw, T, err, st, spins);
+  if (cin == 32 && cout == 128) return launch_wgrad_tc<32, 128>(x, dy, dw, T, err, st, spins);
   return cudaErrorInvalidValue;
 }
 
-bool conv_tc_supported(int cin, int cout, int mode) {
-  return (cin == 128 && cout == 128 && (mode == 0 || mode == 2)) || (cin == 128 && cout == 64 && mode == 1) ||
-         (cin == 64 && cout == 128 && mode == 2) || (cin == 32 && cout == 128 && mode == 0);
-}
 
 cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, const float *bias,
                     const int32_t *rowseq, const bf16 *prev, void *y, int T, unsigned *err,
