@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--only-embed", action="store_true",
                     help="time the selector's embedding of every sequence alone, random "
                          "network (profiling cases)")
+    ap.add_argument("--only-train", action="store_true",
+                    help="time selector training steps alone (256 pairs per step; profiling cases)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-center comparison")
     ap.add_argument("--center", default="exact", choices=["exact", "sampled"],
@@ -374,6 +376,26 @@ def run_ours(args):
         rows = int(lens.sum()) + 4 * (n + 1)
         flops = 2 * 9 * (32 * 128 + 2 * 128 * 128 + 128 * 64) * rows
         print(json.dumps({"only_embed": True, "n": n, "rows": rows, "selector_ms": ms,
+                          "tflops": flops / (ms * 1e-3) / 1e12}))
+        ctx.close()
+        return
+
+    if args.only_train:
+        from seqgen import training_pairs
+        lens = np.diff(offsets)
+        b.msa_load(h, dlet, offsets)
+        b.msa_selector_init(h, seed=1)
+        pairs = training_pairs(n, 4096, fam, seed=3)
+        targets = b.msa_selector_targets(h, pairs, scale=1e-3)
+        steps = 20
+        b.msa_selector_train(h, pairs, targets, steps=max(1, args.warmup), batch_pairs=256)
+        b.msa_selector_train(h, pairs, targets, steps=steps, batch_pairs=256)
+        ms = b.msa_stage_times(h)[0]["selector"] / steps
+        # forward + data gradient + weight gradient: 3x the forward flops of
+        # 512 sequences of the set's mean length (+ 4 zero rows each)
+        rows = 512 * (float(lens.mean()) + 4)
+        flops = 3 * 2 * 9 * (32 * 128 + 2 * 128 * 128 + 128 * 64) * rows
+        print(json.dumps({"only_train": True, "n": n, "ms_per_step": ms,
                           "tflops": flops / (ms * 1e-3) / 1e12}))
         ctx.close()
         return

@@ -50,6 +50,8 @@ struct msa_ctx {
   DevBuf pairsum, self, rowsum, prefix, qlist, ovf, ovf_scores, ovf_dst, part_val, part_idx,
       pairs, pair_dst, pair_out, counters, streams;
   cudaStream_t cap_st = nullptr;  // private stream the center graph is captured on
+  cudaGraphExec_t center_exec = nullptr;  // the last center graph and what it bakes in
+  std::vector<int64_t> center_key;
   bool have_rowsum = false;
 
   // alignment

@@ -362,7 +362,7 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
 // captured on the context's private capture stream and launched on its
 // stream (which may be the legacy default stream).
 int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, int sub_off,
-                 int sub_n, cudaGraphExec_t *exec_out) {
+                 int sub_n) {
   const SeqSet ss = seqset(ctx);
   const Scoring sc = scoring(ctx);
   std::vector<int> top(kNumCenterVariants, 0);
@@ -370,34 +370,57 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
   for (int v = 0; v < kNumCenterVariants; ++v)
     if (top[v] > 0) CK(center_allow_smem(v, top[v]));
   unsigned long long *cnt = P<unsigned long long>(ctx->counters);
-  CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * plans.size(), ctx->cap_st);
-  int failed = -1;
-  for (size_t c = 0; c < plans.size() && e == cudaSuccess; ++c) {
+  // Everything the graph bakes in; a selection with the same key (the same
+  // set and buffers, e.g. a repeated step) relaunches the cached graph.
+  std::vector<CenterJob> jobs;
+  std::vector<int64_t> key = {mode, sub_off, sub_n, (int64_t)ss.res, (int64_t)ss.pstart,
+                              (int64_t)ss.len, ss.n, (int64_t)sc.M, sc.K, sc.o, sc.e,
+                              (int64_t)cnt, (int64_t)plans.size()};
+  for (size_t c = 0; c < plans.size(); ++c) {
     const CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c);
-    e = launch_center(plans[c].cc.variant, ss, sc, job, plans[c].grid, ctx->cap_st, false);
-    if (e != cudaSuccess) failed = (int)c;
+    jobs.push_back(job);
+    const int64_t f[] = {plans[c].cc.variant, plans[c].grid, plans[c].smem, job.mode,
+                         (int64_t)job.qlist, job.nq, job.qb, job.qe, job.sub_off, job.sub_n,
+                         (int64_t)job.prefix, job.n_items, job.npass, (int64_t)job.counter,
+                         (int64_t)job.pairsum, (int64_t)job.self, job.sat_thresh,
+                         (int64_t)job.ovf, (int64_t)job.ovf_count, job.ovf_cap, (int64_t)job.err,
+                         (int64_t)job.scratch, job.scratch_cols, (int64_t)job.streams};
+    key.insert(key.end(), f, f + sizeof(f) / sizeof(f[0]));
   }
-  cudaGraph_t graph = nullptr;
-  const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_st, &graph);
-  if (failed >= 0) {
+  if (!ctx->center_exec || key != ctx->center_key) {
+    if (ctx->center_exec) {
+      CK(cudaStreamSynchronize(ctx->st));
+      cudaGraphExecDestroy(ctx->center_exec);
+      ctx->center_exec = nullptr;
+      ctx->center_key.clear();
+    }
+    CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * plans.size(), ctx->cap_st);
+    int failed = -1;
+    for (size_t c = 0; c < plans.size() && e == cudaSuccess; ++c) {
+      e = launch_center(plans[c].cc.variant, ss, sc, jobs[c], plans[c].grid, ctx->cap_st, false);
+      if (e != cudaSuccess) failed = (int)c;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_st, &graph);
+    if (failed >= 0) {
+      if (graph) cudaGraphDestroy(graph);
+      const ClassPlan &pl = plans[failed];
+      return fail(ctx, MSA_ECUDA, "center kernel variant %d (grid %d, %d B shared, %d passes): %s",
+                  pl.cc.variant, pl.grid, pl.smem, pl.npass, cudaGetErrorString(e));
+    }
+    if (e == cudaSuccess) e = e_end;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    const ClassPlan &pl = plans[failed];
-    return fail(ctx, MSA_ECUDA, "center kernel variant %d (grid %d, %d B shared, %d passes): %s",
-                pl.cc.variant, pl.grid, pl.smem, pl.npass, cudaGetErrorString(e));
+    CK(e);
+    ctx->center_exec = exec;
+    ctx->center_key = key;
   }
-  if (e == cudaSuccess) e = e_end;
-  cudaGraphExec_t exec = nullptr;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
-  CK(e);
   ctx->launches += (int64_t)plans.size();
   stage_begin(ctx, ST_CENTER_K);
-  e = cudaGraphLaunch(exec, ctx->st);
+  CK(cudaGraphLaunch(ctx->center_exec, ctx->st));
   stage_end(ctx, ST_CENTER_K);
-  if (e != cudaSuccess) cudaGraphExecDestroy(exec);
-  CK(e);
-  *exec_out = exec;  // destroyed by the caller once the stream has drained
   return MSA_OK;
 }
 
@@ -441,6 +464,16 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     if (!classes.empty() && classes.back().variant == v && classes.back().ue == ub) classes.back().ue = ue;
     else classes.push_back({v, ub, ue});
   };
+  // Stacking shortens the item list by the stack height; it is only worth
+  // it while the queries' own items fill the GPU many times over, in the
+  // all-pairs and reference modes (not for a short candidate list), and
+  // within one pass (a stack over several passes pays boundary rows the
+  // model does not see).
+  int64_t items_single = 0;
+  for (int p = 0; p < npairs; ++p) items_single += (int64_t)(mode == 0 ? n - 2 * p : n) / 8;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
+  const bool stack = mode != 2 && items_single >= 16 * 2 * 3 * (int64_t)std::max(sms, 1);
   for (int p = 0; p < npairs;) {
     int bv = -1, bm = 0;
     double bcost = 1e300;
@@ -456,8 +489,9 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
             corr = ctx->tune_corr[b][v];
       int rows = 0;
       double real = 0;
-      for (int q = p; q < npairs && q - p < kMaxSeg; ++q) {
+      for (int q = p; q < npairs && q - p < (stack ? kMaxSeg : 1); ++q) {
         const int rq = pair_rows(qlen, x1, q, cv.R);
+        if (q > p && rows + rq > GR) break;  // stacks stay within one pass
         if (center_profile_bytes(v, ctx->K, round_up_int(rows + rq, GR)) > kMaxPairedProfile) break;
         rows += rq;
         const int xa = 2 * q, xb = 2 * q + 1;
@@ -503,11 +537,8 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     plans.push_back(plan_class(ctx, mode, nq_list, cc, qlen, n, prefix_all, streams));
   }
   TRY(stage_plans(ctx, plans, prefix_all, streams));
-  cudaGraphExec_t exec = nullptr;
-  TRY(launch_plans(ctx, mode, plans, 0, n, &exec));
-  const cudaError_t e_sync = cudaStreamSynchronize(ctx->st);
-  cudaGraphExecDestroy(exec);
-  CK(e_sync);
+  TRY(launch_plans(ctx, mode, plans, 0, n));
+  CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_CENTER_K);
   const float center_ms = ctx->stage_ms[ST_CENTER_K];
   int64_t cells = 0;
@@ -701,6 +732,7 @@ void msa_destroy(msa_ctx *ctx) {
   cudaFree(ctx->dLut);
   cudaFree(ctx->dSymLut);
   cudaFree(ctx->dcounter);
+  if (ctx->center_exec) cudaGraphExecDestroy(ctx->center_exec);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   cudaFree(ctx->derr);
   cudaFree(ctx->dsmall);

@@ -384,6 +384,90 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
     }
     const int2 st = job.streams[job.qb + lo];  // pairs [st.x, st.x + st.y)
     const int m = st.y;
+    if (m == 1) {
+      // a single pair: its rows start at the first pass, so the lanes keep
+      // their best in registers and no segment table is needed
+      const int xa = 2 * st.x, xb = xa + 1;
+      const int qA = job.mode == 0 ? xa : job.qlist[xa];
+      const int qB = xb < job.nq ? (job.mode == 0 ? xb : job.qlist[xb]) : -1;
+      const int LqA = ss.len[qA], LqB = qB >= 0 ? ss.len[qB] : 0;
+      const uint8_t *ra = ss.res + ss.pstart[qA];
+      const uint8_t *rb = ss.res + ss.pstart[qB >= 0 ? qB : qA];
+      const int np = (max(LqA, LqB) + G * R - 1) / (G * R);
+      const int prow = np * G * R;
+      if (threadIdx.x < 2) s_qsum[0][threadIdx.x] = 0ull;
+      for (int idx = threadIdx.x; idx < (K + 1) * prow; idx += NT) {
+        const int r = idx / prow, i = idx - r * prow;
+        uint32_t a = 0, b = 0;  // padding: score -o
+        if (r < K) {
+          if (i < LqA) a = (uint32_t)(sM[ra[i] * K + r] + o);
+          if (i < LqB) b = (uint32_t)(sM[rb[i] * K + r] + o);
+        }
+        smem32[r * stride + i] = a | (b << 16);
+      }
+      __syncthreads();
+      const int s0 = (job.mode == 0 ? xa : job.sub_off) + (int)(item - job.prefix[lo]) * NG;
+      const int send = job.mode == 0 ? ss.n : job.sub_off + job.sub_n;
+      const int s = s0 + g;
+      const bool valid = s < send;
+      const int Ls = valid ? ss.len[s] : 0;
+      const uint8_t *rs = ss.res + (valid ? ss.pstart[s] : 0);
+      const int Lw = __reduce_max_sync(MSA_FULL_MASK, Ls);
+      int best = 0;
+      if (Lw > 0) {
+        for (int p = 0; p < np; ++p) {
+          const int2 *sin = p > 0 ? scr + (size_t)((p - 1) & 1) * job.scratch_cols : nullptr;
+          int2 *sout = p + 1 < np ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
+          const uint32_t *pp = smem32 + p * G * R;
+          int b;
+          if (np == 1)
+            b = wave_pass_pp<G, R, false, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, false, sin, sout);
+          else if (p == 0)
+            b = wave_pass_pp<G, R, false, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, false, sin, sout);
+          else if (p + 1 == np)
+            b = wave_pass_pp<G, R, true, false>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, false, sin, sout);
+          else
+            b = wave_pass_pp<G, R, true, true>(pp, stride, rs, Ls, Lw, t, base_lane, padc, o, sc.e, false, sin, sout);
+          best = Cell<true>::vmax(best, b);
+          __syncwarp();
+        }
+      }
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1)
+        best = Cell<true>::vmax(best, __shfl_xor_sync(MSA_FULL_MASK, best, off));
+      if (t == 0 && valid) {
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const int q = l ? qB : qA;
+          if (q < 0) continue;
+          if (job.mode == 0 && s < q) continue;  // counted as (s, q) by the earlier query
+          const int S = l ? Cell<true>::lane1(best) : Cell<true>::lane0(best);
+          if (S > job.sat_thresh) {
+            const unsigned slot = atomicAdd(job.ovf_count, 1u);
+            if (slot < (unsigned)job.ovf_cap) job.ovf[slot] = make_int2(q, s);
+            else atomicOr(job.err, MSA_DERR_OVERFLOW);
+            continue;
+          }
+          if (job.mode == 0) {
+            if (s == q) job.self[q] = S;
+            else {
+              atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+              atomicAdd(&s_qsum[0][l], (unsigned long long)(long long)S);
+            }
+          } else if (job.mode == 1) {
+            atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+          } else {
+            atomicAdd(&s_qsum[0][l], (unsigned long long)(long long)S);
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && job.mode != 1) {
+        if (s_qsum[0][0]) atomicAdd(&job.pairsum[qA], s_qsum[0][0]);
+        if (qB >= 0 && s_qsum[0][1]) atomicAdd(&job.pairsum[qB], s_qsum[0][1]);
+      }
+      continue;
+    }
     // segment k = pair st.x + k: queries of the two lanes, lengths, first row
     if (threadIdx.x < m) {
       const int k = threadIdx.x, xa = 2 * (st.x + k), xb = xa + 1;
