@@ -262,7 +262,9 @@ def test_batched_uneven_10k_full_size_sampled():
         sp = b.msa_sp_score(h)
     assert c == int(np.argmin(rowsum)) and s == rowsum[c]
     rng = np.random.default_rng(1)
-    sample = [c] + list(rng.choice(n, 2, replace=False))
+    # the shortest sequences are the queries stacked several to a pass
+    order = np.argsort(np.diff(offsets), kind="stable")
+    sample = [c] + list(rng.choice(n, 2, replace=False)) + [int(order[0]), int(order[5])]
     for i in sample:
         pairs = np.stack([np.full(n, i), np.arange(n)], 1)
         S = oracle.pair_scores(prob, pairs).astype(np.int64)
@@ -301,11 +303,13 @@ def test_autotuned_selection_is_unchanged():
 
 def test_short_peptides_against_their_center():
     """Peptides cut from a 500-residue ancestor (which is sequence 0):
-    sampled exact center and the whole MSA, bit-exact."""
+    sampled exact center (240 references: enough work that the short
+    reference queries are stacked several to a pass) and the whole MSA,
+    bit-exact."""
     b = binding()
     letters, offsets, w, alph, M = workload("short_peptides_1m", n=1500, seed=5)
     prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
-    refs = reference_sample(prob.n, 100, seed=3)
+    refs = reference_sample(prob.n, 240, seed=3)
     oc, orow = oracle.exact_center(prob, refs=refs)
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
         b.msa_load(h, letters, offsets)
