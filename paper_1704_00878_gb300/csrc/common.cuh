@@ -7,12 +7,6 @@
 
 #define MSA_FULL_MASK 0xffffffffu
 
-// Score given to padding rows (query positions past the end) and to the
-// padding residue code (subject positions past the end).  Any negative value
-// keeps every padded cell strictly below the best real cell: each padded H is
-// a real or padded neighbour minus a positive amount, or zero.
-#define MSA_PAD_SCORE (-100)
-
 // Residues of every loaded sequence sit at 16-byte aligned offsets followed by
 // at least MSA_SEQ_TAIL bytes of the padding code, so 16-byte loads that start
 // inside a sequence stay inside its allocation.
