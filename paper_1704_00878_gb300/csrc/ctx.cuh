@@ -49,7 +49,9 @@ struct msa_ctx {
   // center selection
   DevBuf pairsum, self, rowsum, prefix, qlist, ovf, ovf_scores, ovf_dst, part_val, part_idx,
       pairs, pair_dst, pair_out, counters, streams;
-  cudaStream_t cap_st = nullptr;  // private stream the center graph is captured on
+  cudaStream_t cap_st = nullptr;  // private streams the center graph is captured on
+  cudaStream_t cap_st2 = nullptr;
+  cudaEvent_t cap_fork = nullptr, cap_join = nullptr;
   cudaGraphExec_t center_exec = nullptr;  // the last center graph and what it bakes in
   std::vector<int64_t> center_key;
   bool have_rowsum = false;
@@ -70,6 +72,7 @@ struct msa_ctx {
   unsigned *derr = nullptr;     // derr[0] error bits, derr[1] overflow count
   long long *dsmall = nullptr;  // [0] total, [1] argmin val, [2] argmin idx, [3] width, [4] sp
   DevBuf scratch;
+  size_t scratch_half = 0;  // int2 offset of the second stream's boundary rows (center graph)
 
   cudaEvent_t ev[2 * msa_detail::ST_N] = {};
   float stage_ms[msa_detail::ST_N] = {};

@@ -325,7 +325,9 @@ int stage_plans(msa_ctx *ctx, const std::vector<ClassPlan> &plans,
     if (pl.npass > 1)
       scratch = std::max(scratch, (size_t)pl.grid * (kCenterThreads / kCenterVariants[pl.cc.variant].G) *
                                       2 * ctx->maxlen * sizeof(int2));
-  if (scratch) TRY(ensure(ctx, ctx->scratch, scratch));
+  // the graph runs its classes on two streams: one boundary-row area each
+  if (scratch) TRY(ensure(ctx, ctx->scratch, 2 * scratch));
+  ctx->scratch_half = scratch / sizeof(int2);
   TRY(ensure(ctx, ctx->prefix, sizeof(int64_t) * prefix_all.size()));
   TRY(ensure(ctx, ctx->counters, sizeof(unsigned long long) * std::max<size_t>(plans.size(), 1)));
   CK(cudaMemcpyAsync(ctx->prefix.p, prefix_all.data(), sizeof(int64_t) * prefix_all.size(),
@@ -372,12 +374,18 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
   unsigned long long *cnt = P<unsigned long long>(ctx->counters);
   // Everything the graph bakes in; a selection with the same key (the same
   // set and buffers, e.g. a repeated step) relaunches the cached graph.
+  // The classes run longest queries first, alternating between two streams
+  // (a fork and a join in the graph), so a class's tail of long items
+  // overlaps the next class instead of idling the GPU; each stream has its
+  // own boundary-row area.
   std::vector<CenterJob> jobs;
   std::vector<int64_t> key = {mode, sub_off, sub_n, (int64_t)ss.res, (int64_t)ss.pstart,
                               (int64_t)ss.len, ss.n, (int64_t)sc.M, sc.K, sc.o, sc.e,
                               (int64_t)cnt, (int64_t)plans.size()};
   for (size_t c = 0; c < plans.size(); ++c) {
-    const CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c);
+    CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c);
+    const size_t order = plans.size() - 1 - c;  // launch position
+    if (order & 1) job.scratch += ctx->scratch_half;
     jobs.push_back(job);
     const int64_t f[] = {plans[c].cc.variant, plans[c].grid, plans[c].smem, job.mode,
                          (int64_t)job.qlist, job.nq, job.qb, job.qe, job.sub_off, job.sub_n,
@@ -396,10 +404,19 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
     }
     CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * plans.size(), ctx->cap_st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->cap_fork, ctx->cap_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap_st2, ctx->cap_fork, 0);
     int failed = -1;
-    for (size_t c = 0; c < plans.size() && e == cudaSuccess; ++c) {
-      e = launch_center(plans[c].cc.variant, ss, sc, jobs[c], plans[c].grid, ctx->cap_st, false);
+    for (size_t k = 0; k < plans.size() && e == cudaSuccess; ++k) {
+      const size_t c = plans.size() - 1 - k;
+      e = launch_center(plans[c].cc.variant, ss, sc, jobs[c], plans[c].grid,
+                        (k & 1) ? ctx->cap_st2 : ctx->cap_st, false);
       if (e != cudaSuccess) failed = (int)c;
+    }
+    {
+      const cudaError_t e2 = cudaEventRecord(ctx->cap_join, ctx->cap_st2);
+      const cudaError_t e3 = cudaStreamWaitEvent(ctx->cap_st, ctx->cap_join, 0);
+      if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_st, &graph);
@@ -697,6 +714,9 @@ int msa_create(msa_ctx **out, const msa_params *p, void *cuda_stream) {
     CK(cudaMemcpy(ctx->dSymLut, sym, 256, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->dcounter, sizeof(unsigned long long)));
     CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->cap_st2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->cap_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->cap_join, cudaEventDisableTiming));
     CK(cudaMalloc(&ctx->derr, 2 * sizeof(unsigned)));
     CK(cudaMemset(ctx->derr, 0, 2 * sizeof(unsigned)));
     CK(cudaMalloc(&ctx->dsmall, 8 * sizeof(long long)));
@@ -734,6 +754,9 @@ void msa_destroy(msa_ctx *ctx) {
   cudaFree(ctx->dcounter);
   if (ctx->center_exec) cudaGraphExecDestroy(ctx->center_exec);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
+  if (ctx->cap_st2) cudaStreamDestroy(ctx->cap_st2);
+  if (ctx->cap_fork) cudaEventDestroy(ctx->cap_fork);
+  if (ctx->cap_join) cudaEventDestroy(ctx->cap_join);
   cudaFree(ctx->derr);
   cudaFree(ctx->dsmall);
   for (auto &ev : ctx->ev)
