@@ -497,9 +497,10 @@ k_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tl * COUT + c0), v);
           if (ci >= CIN) continue;
-          float *d = dw + ((size_t)(t0 + tl) * CIN + ci) * COUT + c0;
+          // 16-byte vector reductions (every dW tensor starts 16-byte aligned)
+          float4 *d = reinterpret_cast<float4 *>(dw + ((size_t)(t0 + tl) * CIN + ci) * COUT + c0);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) atomicAdd(d + j, v[j]);
+          for (int j = 0; j < 8; ++j) atomicAdd(d + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         }
       }
     }
