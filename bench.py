@@ -215,10 +215,12 @@ def workload_text(w, n, center, length=None):
                                                 else "sampled exact (1,000 references)"))
 
 
-def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp):
+def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp, refs):
     """Train the selector on exact-kernel distances (untimed), then time the
     whole step with the learned center (network embedding + exact row sums of
-    its 128 best candidates) against the exact all-pairs center."""
+    its 128 best candidates, over every sequence when the exact center is the
+    all-pairs one, else over the same reference sample) against the exact
+    center's step."""
     import torch
     from seqgen import training_pairs
     pairs = training_pairs(n, 60000, fam, seed=8)
@@ -229,7 +231,7 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
 
     def step_learned():
         b.msa_load(h, dlet, offsets)
-        c, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED_REFINED, candidates=128)
+        c, _ = b.msa_select_center_refined(h, candidates=128, refs=refs)
         b.msa_align_to_center(h, c)
         b.msa_merge_gaps(h, want_rows=False)
         return c, b.msa_sp_score(h)
@@ -246,6 +248,7 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
         ev1.record(stream)
         torch.cuda.synchronize()
         ms.append(ev0.elapsed_time(ev1))
+    stages = b.msa_stage_times(h)[0]
     pairs_n = n * (n - 1) / 2
     return {"exact_step_ms": exact_ms, "learned_step_ms": float(np.mean(ms)),
             "speedup": exact_ms / float(np.mean(ms)),
@@ -255,7 +258,10 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
             "train": {"pairs": int(pairs.shape[0]), "steps": 6000, "batch_pairs": 256,
                       "seconds": train_s, "loss_first": float(losses[:10].mean()),
                       "loss_last": float(losses[-50:].mean())},
-            "candidates_refined_exactly": 128}
+            "candidates_refined_exactly": 128,
+            "refined_over": "every sequence" if refs is None else "the %d references" % len(refs),
+            "stages_ms": {k: round(stages[k], 3) for k in
+                          ("encode", "selector", "center", "align_dp", "traceback", "merge", "sp")}}
 
 
 def run_ours(args):
@@ -435,7 +441,7 @@ def run_ours(args):
     learned = None
     if not args.no_learned:
         learned = learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream,
-                                   total_ms / args.steps, sp)
+                                   total_ms / args.steps, sp, refs)
 
     t_max = reduce_max(total_ms)
     all_cells = reduce_sum(float(cells))

@@ -125,7 +125,8 @@ int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int
  * LEARNED_REFINED: the nref (0 = 32) sequences with the smallest
  *   ||e_i - mean(e)||^2, then the exact sum_j d(i,j) over all j for each of
  *   them (nref x n alignments instead of n^2/2) and its argmin; refs unused;
- *   sum_dist_out gets the winner's exact row sum.
+ *   sum_dist_out gets the winner's exact row sum (msa_select_center_refined
+ *   ranks them over a reference sample instead).
  * FIRST: 0.
  * The exact modes run their length-bucketed kernels as one CUDA graph
  * (captured on a stream private to the context, launched on its stream).
@@ -133,6 +134,20 @@ int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int
  * row sum (EXACT modes), else 0.  ESTATE for LEARNED without a selector. */
 int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
                       int64_t *center_out, int64_t *sum_dist_out);
+
+/* LEARNED_REFINED with a choice of what the exact row sums run over:
+ * the `candidates` (0 = 32, at most n) sequences with the smallest
+ * ||e_i - mean(e)||^2, then for each of them sum_j d(i,j) and the argmin
+ * (lowest index on ties).  refs NULL or nref 0: j runs over every sequence
+ * (as msa_select_center's LEARNED_REFINED, candidates x n alignments); else
+ * j runs over refs (host int64[nref], distinct input indices), the
+ * EXACT_SAMPLED row sum of each candidate (candidates x nref alignments), so
+ * that with the same refs the result is EXACT_SAMPLED's argmin restricted to
+ * the candidates.  center_out: host int64; sum_dist_out (nullable, host
+ * int64): the winner's row sum.  ESTATE without a selector; EINVAL for a bad
+ * reference list (as EXACT_SAMPLED) or a negative candidate count. */
+int msa_select_center_refined(msa_ctx *ctx, int32_t candidates, const int64_t *refs, int64_t nref,
+                              int64_t *center_out, int64_t *sum_dist_out);
 
 /* Row sums of d for every sequence from the last EXACT / EXACT_SAMPLED
  * selection: rowsum_out host or device int64[n]. */
@@ -287,6 +302,14 @@ int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out);
  * context usable (a later call after raising the cap succeeds); 0 removes
  * the cap.  EINVAL for a negative limit. */
 int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes);
+
+/* Device memory msa_align_to_center may hold for traceback codes at once
+ * (0.5 byte per DP cell; default 32 GiB, and at most half the free device
+ * memory and half of what a memory limit leaves).  The alignment runs in
+ * batches of subjects whose codes fit, each batch's traceback after its fill;
+ * a budget below one subject's codes gives one subject per batch.  The
+ * result does not depend on it.  EINVAL for a budget < 1. */
+int msa_set_codes_budget(msa_ctx *ctx, int64_t bytes);
 
 /* Self-test of the bounded waits of the tensor-core convolution (no
  * counterpart in the paper): runs one small convolution whose loads are

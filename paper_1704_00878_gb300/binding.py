@@ -51,6 +51,8 @@ _SIGS = {
     "msa_pair_scores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "msa_select_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_select_center_refined": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_center_rowsums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_align_to_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "msa_alignment_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -64,6 +66,7 @@ _SIGS = {
     "msa_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "msa_memory": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_set_memory_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "msa_set_codes_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "msa_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
@@ -202,6 +205,18 @@ def msa_select_center(ctx, mode, refs=None, candidates=0):
     return int(c[0]), int(s[0])
 
 
+def msa_select_center_refined(ctx, candidates=0, refs=None):
+    """Returns (center, winning row sum of distances): the selector's
+    `candidates` best sequences (0 = 32) ranked by exact row sums over refs
+    (None = every sequence)."""
+    c = np.zeros(1, np.int64)
+    s = np.zeros(1, np.int64)
+    r = None if refs is None else np.ascontiguousarray(refs, dtype=np.int64)
+    _check(ctx, lib().msa_select_center_refined(ctx, int(candidates), _ptr(r),
+                                                0 if r is None else r.size, _ptr(c), _ptr(s)))
+    return int(c[0]), int(s[0])
+
+
 def msa_center_rowsums(ctx, out=None):
     n = msa_dims(ctx)[0]
     res = np.zeros(n, np.int64) if out is None else out
@@ -278,6 +293,13 @@ def msa_memory(ctx):
 
 def msa_set_memory_limit(ctx, limit_bytes):
     _check(ctx, lib().msa_set_memory_limit(ctx, int(limit_bytes)))
+
+
+def msa_set_codes_budget(ctx, nbytes):
+    """Bytes of traceback codes the alignment holds at once (its batch size)."""
+    rc = lib().msa_set_codes_budget(ctx, int(nbytes))
+    if rc != MSA_OK:
+        raise MSAError(rc, "codes budget must be >= 1 byte")
 
 
 def msa_debug_wait_timeout(ctx):

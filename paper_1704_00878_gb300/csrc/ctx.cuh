@@ -80,7 +80,10 @@ struct msa_ctx {
   int64_t launches = 0;
   // device memory held through ensure(): current, peak, optional cap (0 = none)
   size_t dev_bytes = 0, dev_peak = 0, dev_limit = 0;
-  size_t codes_budget = (size_t)4 << 30;
+  // traceback codes held at once (0.5 B per cell): the alignment runs in
+  // batches of subjects whose codes fit; a batch should fill the GPU many
+  // times over, and the traceback of each batch waits for its fill
+  size_t codes_budget = (size_t)32 << 30;
 
   msa_detail::Selector *sel = nullptr;
 
@@ -106,8 +109,21 @@ Scoring scoring(msa_ctx *ctx);
 int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector<int32_t> &dst_in,
               int32_t *d_out);
 int selector_center(msa_ctx *ctx, int64_t *center_out);
-int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *sum_out);
-int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted);
+// refs: ascending sorted positions of a reference sample, empty = every sequence
+int selector_center_refined(msa_ctx *ctx, int k, const std::vector<int32_t> &refs,
+                            int64_t *center_out, int64_t *sum_out);
+// A subset of the loaded set with indices of its own: entry v is the loaded
+// sequence at sorted position idx[v] (device starts and lengths in ss); the
+// center planner and kernels see only the view, its first n_sub entries being
+// the subjects.  Entries ascend in length within the subjects and within the
+// queries.
+struct SetView {
+  SeqSet ss;
+  std::vector<int32_t> idx, len;
+  int n_sub = 0;
+};
+int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted,
+               const SetView *view = nullptr);
 // the device error word -> an MSA_E* code (synchronises the stream)
 int check_derr(msa_ctx *ctx);
 

@@ -364,8 +364,7 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
 // captured on the context's private capture stream and launched on its
 // stream (which may be the legacy default stream).
 int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, int sub_off,
-                 int sub_n) {
-  const SeqSet ss = seqset(ctx);
+                 int sub_n, const SeqSet &ss) {
   const Scoring sc = scoring(ctx);
   std::vector<int> top(kNumCenterVariants, 0);
   for (const ClassPlan &pl : plans) top[pl.cc.variant] = std::max(top[pl.cc.variant], pl.smem);
@@ -441,18 +440,23 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
   return MSA_OK;
 }
 
-int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
+int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, const SetView *view) {
   // qsorted: ascending sorted indices of the queries (modes 1, 2); mode 0 uses all.
-  const int n = ctx->n;
+  // With a view, indices are the view's and its first n_sub entries are the subjects.
+  if (view && mode == 0) return fail(ctx, MSA_EINVAL, "all-pairs selection over a view");
+  const std::vector<int32_t> &lens = view ? view->len : ctx->len_sorted;
+  const int n = view ? view->n_sub : ctx->n;
+  if (n < 1) return fail(ctx, MSA_EINVAL, "no subjects");
+  const SeqSet ss = view ? view->ss : seqset(ctx);
   std::vector<int> qlen;
-  if (mode == 0) qlen.assign(ctx->len_sorted.begin(), ctx->len_sorted.end());
-  else for (int q : qsorted) qlen.push_back(ctx->len_sorted[q]);
+  if (mode == 0) qlen.assign(lens.begin(), lens.end());
+  else for (int q : qsorted) qlen.push_back(lens[q]);
   const int nq = (int)qlen.size();
   double mean = 0;
-  for (int k = 0; k < n; ++k) mean += ctx->len_sorted[k];
+  for (int k = 0; k < n; ++k) mean += lens[k];
   mean /= n;
   std::vector<int64_t> suffix(n + 1, 0);
-  for (int k = n - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + ctx->len_sorted[k];
+  for (int k = n - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + lens[k];
   if (mode != 0) {
     TRY(ensure(ctx, ctx->qlist, sizeof(int32_t) * qsorted.size()));
     CK(cudaMemcpyAsync(ctx->qlist.p, qsorted.data(), sizeof(int32_t) * qsorted.size(),
@@ -554,15 +558,15 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     plans.push_back(plan_class(ctx, mode, nq_list, cc, qlen, n, prefix_all, streams));
   }
   TRY(stage_plans(ctx, plans, prefix_all, streams));
-  TRY(launch_plans(ctx, mode, plans, 0, n));
+  TRY(launch_plans(ctx, mode, plans, 0, n, ss));
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_CENTER_K);
   const float center_ms = ctx->stage_ms[ST_CENTER_K];
   int64_t cells = 0;
   if (mode == 0) {
-    for (int x = 0; x < nq; ++x) cells += (int64_t)ctx->len_sorted[x] * suffix[x];
+    for (int x = 0; x < nq; ++x) cells += (int64_t)lens[x] * suffix[x];
   } else {
-    for (int q : qsorted) cells += (int64_t)ctx->len_sorted[q] * suffix[0];
+    for (int q : qsorted) cells += (int64_t)lens[q] * suffix[0];
   }
   ctx->cells[0] = cells;
   ctx->stage_ms[ST_CENTER_K] = center_ms;
@@ -580,7 +584,10 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted) {
     std::vector<int32_t> dst(cnt);
     std::iota(dst.begin(), dst.end(), 0);
     TRY(ensure(ctx, ctx->ovf_scores, sizeof(int32_t) * cnt));
-    TRY(run_pairs(ctx, ov, dst, P<int32_t>(ctx->ovf_scores)));
+    std::vector<int2> ov_set(ov);  // the re-run takes loaded-set indices
+    if (view)
+      for (int2 &p : ov_set) p = make_int2(view->idx[p.x], view->idx[p.y]);
+    TRY(run_pairs(ctx, ov_set, dst, P<int32_t>(ctx->ovf_scores)));
     CK((++ctx->launches, launch_apply_overflow)(mode, P<int2>(ctx->ovf),
                                                 P<int32_t>(ctx->ovf_scores), cnt,
                                                 P<unsigned long long>(ctx->pairsum),
@@ -642,6 +649,22 @@ int autotune(msa_ctx *ctx) {
   ctx->tune_edges.assign(edges, edges + nb + 1);
   ctx->tune_rate = rate;
   ctx->tune_corr = corr;
+  return MSA_OK;
+}
+
+// A reference list (input indices, distinct) -> ascending sorted positions.
+int reference_positions(msa_ctx *ctx, const int64_t *refs, int64_t nref, std::vector<int32_t> &out) {
+  const int n = ctx->n;
+  if (!refs || nref < 1 || nref > n) return fail(ctx, MSA_EINVAL, "bad reference list");
+  std::vector<char> seen(n, 0);
+  out.clear();
+  for (int64_t r = 0; r < nref; ++r) {
+    if (refs[r] < 0 || refs[r] >= n) return fail(ctx, MSA_EINVAL, "reference index out of range");
+    if (seen[refs[r]]) return fail(ctx, MSA_EINVAL, "duplicate reference index");
+    seen[refs[r]] = 1;
+    out.push_back(ctx->inv[refs[r]]);
+  }
+  std::sort(out.begin(), out.end());
   return MSA_OK;
 }
 
@@ -858,6 +881,20 @@ int msa_pair_scores(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, int32_t 
   return MSA_OK;
 }
 
+int msa_select_center_refined(msa_ctx *ctx, int32_t candidates, const int64_t *refs, int64_t nref,
+                              int64_t *center_out, int64_t *sum_dist_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (!center_out) return fail(ctx, MSA_EINVAL, "center_out is NULL");
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  if (candidates < 0) return fail(ctx, MSA_EINVAL, "negative candidate count");
+  TRY(set_device(ctx));
+  if (sum_dist_out) *sum_dist_out = 0;
+  std::vector<int32_t> rs;
+  if (refs && nref > 0) TRY(reference_positions(ctx, refs, nref, rs));
+  return selector_center_refined(ctx, candidates > 0 ? std::min(candidates, ctx->n) : 32, rs,
+                                 center_out, sum_dist_out);
+}
+
 int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
                       int64_t *center_out, int64_t *sum_dist_out) {
   if (!ctx) return MSA_EINVAL;
@@ -872,22 +909,12 @@ int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
   if (mode == MSA_CENTER_LEARNED) return selector_center(ctx, center_out);
   if (mode == MSA_CENTER_LEARNED_REFINED)
     return selector_center_refined(ctx, nref > 0 ? (int)std::min<int64_t>(nref, ctx->n) : 32,
-                                   center_out, sum_dist_out);
+                                   {}, center_out, sum_dist_out);
   if (mode != MSA_CENTER_EXACT && mode != MSA_CENTER_EXACT_SAMPLED)
     return fail(ctx, MSA_EINVAL, "unknown center mode %d", mode);
   const int n = ctx->n;
   std::vector<int32_t> qs;
-  if (mode == MSA_CENTER_EXACT_SAMPLED) {
-    if (!refs || nref < 1 || nref > n) return fail(ctx, MSA_EINVAL, "bad reference list");
-    std::vector<char> seen(n, 0);
-    for (int64_t r = 0; r < nref; ++r) {
-      if (refs[r] < 0 || refs[r] >= n) return fail(ctx, MSA_EINVAL, "reference index out of range");
-      if (seen[refs[r]]) return fail(ctx, MSA_EINVAL, "duplicate reference index");
-      seen[refs[r]] = 1;
-      qs.push_back(ctx->inv[refs[r]]);
-    }
-    std::sort(qs.begin(), qs.end());
-  }
+  if (mode == MSA_CENTER_EXACT_SAMPLED) TRY(reference_positions(ctx, refs, nref, qs));
   stage_begin(ctx, ST_CENTER);
   CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
   CK(cudaMemsetAsync(ctx->self.p, 0, sizeof(int32_t) * n, ctx->st));
@@ -957,6 +984,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
   size_t budget = std::min(ctx->codes_budget, free_b / 2);
+  if (ctx->dev_limit) budget = std::min(budget, ctx->dev_limit > ctx->dev_bytes ? (ctx->dev_limit - ctx->dev_bytes) / 2 : 0);
   size_t max_one = (size_t)nblk * ctx->maxlen * 8;
   if (budget < max_one) budget = max_one;
   std::vector<std::pair<int, int>> batches;
@@ -1253,6 +1281,12 @@ int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out) {
 int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes) {
   if (!ctx || limit_bytes < 0) return MSA_EINVAL;
   ctx->dev_limit = (size_t)limit_bytes;
+  return MSA_OK;
+}
+
+int msa_set_codes_budget(msa_ctx *ctx, int64_t bytes) {
+  if (!ctx || bytes < 1) return MSA_EINVAL;
+  ctx->codes_budget = (size_t)bytes;
   return MSA_OK;
 }
 

@@ -26,6 +26,7 @@ struct Selector {
   // batch buffers
   DevBuf seq, base, len, rowseq, x0, a1, a2, a3, y4, emb, demb, dy4, dz3, dz2, dz1;
   DevBuf bpairs, btargets, loss, small, allemb, dist;
+  DevBuf vstart, vlen;  // a reference/candidate view of the loaded set
 };
 
 namespace {
@@ -296,7 +297,7 @@ void selector_free(msa_ctx *ctx, Selector *s) {
                     &s->w3n, &s->w4t, &s->w4n, &s->seq, &s->base, &s->len, &s->rowseq, &s->x0,
                     &s->a1, &s->a2, &s->a3, &s->y4, &s->emb, &s->demb, &s->dy4, &s->dz3,
                     &s->dz2, &s->dz1, &s->bpairs, &s->btargets, &s->loss, &s->small, &s->allemb,
-                    &s->dist};
+                    &s->dist, &s->vstart, &s->vlen};
   for (DevBuf *b : bufs) release(ctx, *b);
   delete s;
 }
@@ -321,10 +322,14 @@ int selector_center(msa_ctx *ctx, int64_t *center_out) {
 }
 
 // LEARNED_REFINED: the k candidates with the smallest ||e_i - mean(e)||^2,
-// then their exact row sums sum_j d(i, j) over every sequence (k x n
-// alignments with the center kernels, summed on the query side) and the
-// argmin among them (lowest input index on ties).
-int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *sum_out) {
+// then their exact row sums sum_j d(i, j) and the argmin among them (lowest
+// input index on ties).  refs (ascending sorted positions) empty: j runs over
+// every sequence (k x n alignments with the center kernels, summed on the
+// query side); else j runs over refs, the EXACT_SAMPLED row sum, computed as
+// k x |refs| alignments over a view whose subjects are the references and
+// whose queries are the candidates.
+int selector_center_refined(msa_ctx *ctx, int k, const std::vector<int32_t> &refs,
+                            int64_t *center_out, int64_t *sum_out) {
   Selector *s = ctx->sel;
   if (!s || !s->params.p) return fail(ctx, MSA_ESTATE, "no trained selector loaded");
   const int n = ctx->n;
@@ -346,28 +351,77 @@ int selector_center_refined(msa_ctx *ctx, int k, int64_t *center_out, int64_t *s
   });
   std::vector<int32_t> qs(idx.begin(), idx.begin() + k);
   std::sort(qs.begin(), qs.end());
-  // exact row sums of the candidates
   stage_begin(ctx, ST_CENTER);
-  CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
   CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
-  TRY(run_center(ctx, 2, qs));
-  std::vector<int2> sp(n);
-  std::vector<int32_t> dst(n);
-  for (int x = 0; x < n; ++x) { sp[x] = make_int2(x, x); dst[x] = x; }
+  std::vector<unsigned long long> ps(k);  // sum_j S(q, j) per candidate
+  std::vector<int32_t> self(n, 0);        // S(x, x) where needed
+  std::vector<int32_t> need;              // sorted positions whose self score is needed
+  if (refs.empty()) {
+    CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
+    TRY(run_center(ctx, 2, qs));
+    need.resize(n);
+    std::iota(need.begin(), need.end(), 0);
+  } else {
+    const int R = (int)refs.size();
+    SetView view;
+    view.idx = refs;
+    view.idx.insert(view.idx.end(), qs.begin(), qs.end());
+    view.n_sub = R;
+    const int nv = (int)view.idx.size();
+    std::vector<int64_t> vstart(nv);
+    view.len.resize(nv);
+    for (int v = 0; v < nv; ++v) {
+      vstart[v] = ctx->pstart[view.idx[v]];
+      view.len[v] = ctx->len_sorted[view.idx[v]];
+    }
+    TRY(ensure(ctx, s->vstart, sizeof(int64_t) * nv));
+    TRY(ensure(ctx, s->vlen, sizeof(int32_t) * nv));
+    TRY(ensure(ctx, ctx->pairsum, sizeof(unsigned long long) * std::max(n, nv)));
+    CK(cudaMemcpyAsync(s->vstart.p, vstart.data(), sizeof(int64_t) * nv, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(s->vlen.p, view.len.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * nv, ctx->st));
+    view.ss = SeqSet{P<uint8_t>(ctx->res), P<int64_t>(s->vstart), P<int32_t>(s->vlen), nv};
+    std::vector<int32_t> vq(k);
+    std::iota(vq.begin(), vq.end(), R);
+    TRY(run_center(ctx, 2, vq, &view));
+    need = refs;
+    need.insert(need.end(), qs.begin(), qs.end());
+    std::sort(need.begin(), need.end());
+    need.erase(std::unique(need.begin(), need.end()), need.end());
+  }
+  // self scores of the needed sequences into slots 0..|need|-1
+  const int nn = (int)need.size();
+  std::vector<int2> sp(nn);
+  std::vector<int32_t> dst(nn);
+  for (int x = 0; x < nn; ++x) { sp[x] = make_int2(need[x], need[x]); dst[x] = x; }
   TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
   stage_end(ctx, ST_CENTER);
-  std::vector<unsigned long long> ps(n);
-  std::vector<int32_t> self(n);
-  CK(cudaMemcpyAsync(ps.data(), ctx->pairsum.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(self.data(), ctx->self.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<int32_t> selfc(nn);
+  const size_t ps_off = refs.empty() ? 0 : refs.size();  // candidates' first view index
+  if (refs.empty()) {
+    std::vector<unsigned long long> all(n);
+    CK(cudaMemcpyAsync(all.data(), ctx->pairsum.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(selfc.data(), ctx->self.p, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int c = 0; c < k; ++c) ps[c] = all[qs[c]];
+  } else {
+    CK(cudaMemcpyAsync(ps.data(), P<unsigned long long>(ctx->pairsum) + ps_off,
+                       sizeof(unsigned long long) * k, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(selfc.data(), ctx->self.p, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
   stage_collect(ctx, ST_CENTER);
+  for (int x = 0; x < nn; ++x) self[need[x]] = selfc[x];
+  // sum_j d(q, j) = |J| S(q,q) + sum_j S(j,j) - 2 sum_j S(q,j)
   long long T = 0;
-  for (int x = 0; x < n; ++x) T += self[x];
+  if (refs.empty()) for (int x = 0; x < n; ++x) T += self[x];
+  else for (int j : refs) T += self[j];
+  const long long nj = refs.empty() ? n : (long long)refs.size();
   long long best = 0;
   int bestq = -1;
-  for (int q : qs) {
-    const long long v = (long long)n * self[q] + T - 2 * (long long)ps[q];
+  for (int c = 0; c < k; ++c) {
+    const int q = qs[c];
+    const long long v = nj * self[q] + T - 2 * (long long)ps[c];
     if (bestq < 0 || v < best || (v == best && ctx->perm[q] < ctx->perm[bestq])) { best = v; bestq = q; }
   }
   *center_out = ctx->perm[bestq];

@@ -808,9 +808,10 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
 // M >= max(P, F*) >= P, a row's new best >= its old best), so each flag is one
 // 32-bit subtraction, which borrows across no lane, and a per-lane min with 1:
 //   F bit = min(F* - H_up, 1)          E bit = min(E* - H_left, 1)
-//   a     = min(M - P, 1)              (the diagonal is not a best source)
-//   x     = min(M - max(P, F*), 1)     (E is the only best source)
-//   src   = min(1 + a + x, H | 2H)    (0 for H = 0, else 1 + a + x)
+//   z     = min(H, 1)                  (H > 0)
+//   a     = min(M - P, z)              (the diagonal is not a best source)
+//   x     = min(M - max(P, F*), z)     (E is the only best source)
+//   src   = z + a + x                  (0 for H = 0, else 1 + a + x)
 // and the first column reaching a row's best is max(column, d * j) with
 // d = min(best' - best, 1).
 // per-lane unsigned min of two int16 lanes: one instruction (the library's
@@ -887,11 +888,10 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
       const uint32_t tm = __vimax_s16x2_relu(p, f);
       const uint32_t m = __vimax_s16x2_relu(tm, E[r]);
       const uint32_t hn = __viaddmax_s16x2_relu(m, negO, 0u);
-      const uint32_t a = min_u16x2(m - p, ONE);
-      const uint32_t x = min_u16x2(m - tm, ONE);
-      // hn | hn << 1 is 0 for H = 0 and >= 3 otherwise (H < 2^15: nothing
-      // crosses into the other lane)
-      const uint32_t src = min_u16x2(a + x + ONE, hn | (hn << 1));
+      const uint32_t z = min_u16x2(hn, ONE);
+      const uint32_t a = min_u16x2(m - p, z);
+      const uint32_t x = min_u16x2(m - tm, z);
+      const uint32_t src = z + a + x;
       const uint32_t bE = min_u16x2(E[r] - H[r], ONE);
       const uint32_t code = (bF << 3) + (bE << 2) + src;
       acc[r >> 2] = (code << (4 * (r & 3))) + acc[r >> 2];

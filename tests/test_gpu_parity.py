@@ -157,6 +157,21 @@ def test_msa_long_center_multipass():
     check_against_oracle(prob, center, *out)
 
 
+@pytest.mark.parametrize("budget", [1, 300_000])
+def test_msa_in_code_batches(budget):
+    """Codes budgets that split the alignment into one subject per batch and
+    into a few batches give the same MSA as the oracle."""
+    b = binding()
+    letters, offsets, w, alph, M = workload("plain_protein_200", n=60, seed=12)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_set_codes_budget(h, budget)
+        with pytest.raises(b.MSAError):
+            b.msa_set_codes_budget(h, 0)
+        out = run_pipeline(b, h, letters, offsets, 7)
+    check_against_oracle(prob, 7, *out)
+
+
 def test_msa_dna_workload():
     b = binding()
     letters, offsets, w, alph, M = workload("similar_dna_100k", n=40, seed=4)

@@ -164,3 +164,34 @@ def test_training_gains_over_the_method_without_it(tmp_path):
         b.msa_load_selector(h2, path)
         assert (b.msa_selector_params(h2) == saved).all()
         assert b.msa_select_center(h2, b.MSA_CENTER_LEARNED)[0] == top1
+
+
+@pytest.mark.parametrize("k", [400, 24])
+def test_refined_over_references_is_the_sampled_row_sum(k):
+    """Candidates ranked by their row sums over a reference sample (the
+    candidates and the references meet as a view of the set): the winner's
+    sum is the oracle's sampled row sum; with every sequence a candidate the
+    winner is the sampled exact center, and with 24 no candidate beats it."""
+    b = binding()
+    from seqgen import reference_sample
+    letters, offsets, w, alph, M = workload("learned_center_50k", n=400, seed=3)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    refs = reference_sample(400, 37, seed=9)
+    oc, orow = oracle.exact_center(prob, refs=refs)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        b.msa_selector_init(h, seed=1)
+        c, s = b.msa_select_center_refined(h, candidates=k, refs=refs)
+        emb = b.msa_selector_embed(h).astype(np.float64)
+        with pytest.raises(b.MSAError):
+            b.msa_select_center_refined(h, candidates=k, refs=np.array([3, 3]))
+    assert s == orow[c]
+    if k == 400:
+        assert c == oc
+        return
+    d = ((emb - emb.mean(0)) ** 2).sum(1)
+    order = np.argsort(d, kind="stable")
+    # the device ranks in fp32: allow a near-tie at the k-th place
+    assert c in set(order[:k + 2].tolist())
+    for q in order[:k - 2]:
+        assert orow[q] > orow[c] or (orow[q] == orow[c] and q >= c)
