@@ -72,8 +72,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+__device__ __forceinline__ void mbar_arrive_relaxed(uint32_t bar) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // true once the phase with the given parity has completed; false after
@@ -284,21 +284,29 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
       const int r = tile * TBM + q * 32 + lane;
       const bool inb = r < T;
       const bool valid = inb && rowseq[r] >= 0;
+      // the row slice into registers, then the accumulator goes back to the
+      // issuer before any store
+      float v[TBN / 32][32];
 #pragma unroll
-      for (int c0 = 0; c0 < TBN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TBN + c0), v);
+      for (int c = 0; c < TBN / 32; ++c)
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TBN + 32 * c), v[c]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_relaxed(bar(B_CEMPTY + b));
+      if (!inb) continue;
+#pragma unroll
+      for (int c = 0; c < TBN / 32; ++c) {
+        const int c0 = 32 * c;
         const int cb = half * TBN + c0;
-        if (!inb) continue;
         if constexpr (MODE == 1) {
           float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + (size_t)r * COUT + cb);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             float4 o;
-            o.x = valid ? v[4 * j] + s_bias[c0 + 4 * j] : 0.f;
-            o.y = valid ? v[4 * j + 1] + s_bias[c0 + 4 * j + 1] : 0.f;
-            o.z = valid ? v[4 * j + 2] + s_bias[c0 + 4 * j + 2] : 0.f;
-            o.w = valid ? v[4 * j + 3] + s_bias[c0 + 4 * j + 3] : 0.f;
+            o.x = valid ? v[c][4 * j] + s_bias[c0 + 4 * j] : 0.f;
+            o.y = valid ? v[c][4 * j + 1] + s_bias[c0 + 4 * j + 1] : 0.f;
+            o.z = valid ? v[c][4 * j + 2] + s_bias[c0 + 4 * j + 2] : 0.f;
+            o.w = valid ? v[c][4 * j + 3] + s_bias[c0 + 4 * j + 3] : 0.f;
             dst[j] = o;
           }
         } else {
@@ -312,11 +320,11 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
             const uint32_t pw[4] = {pm.x, pm.y, pm.z, pm.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const int c = 8 * j + 2 * h;
-              float a = v[c], bb = v[c + 1];
+              const int cc = 8 * j + 2 * h;
+              float a = v[c][cc], bb = v[c][cc + 1];
               if constexpr (MODE == 0) {
-                a = valid ? fmaxf(a + s_bias[c0 + c], 0.f) : 0.f;
-                bb = valid ? fmaxf(bb + s_bias[c0 + c + 1], 0.f) : 0.f;
+                a = valid ? fmaxf(a + s_bias[c0 + cc], 0.f) : 0.f;
+                bb = valid ? fmaxf(bb + s_bias[c0 + cc + 1], 0.f) : 0.f;
               } else {
                 const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162 *>(&pw[h]);
                 a = valid && __bfloat162float(p2.x) > 0.f ? a : 0.f;
@@ -329,10 +337,6 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
           }
         }
       }
-      // this warp's reads of the accumulator are done: hand it back
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(B_CEMPTY + b));
     }
   }
   if (!ok) atomicOr(err, MSA_DERR_TIMEOUT_TC);
@@ -343,6 +347,274 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
   tc_fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
+}
+
+// ---------------------------------------------------------------- CTA-pair convolution
+// 128 output channels: a cluster of two CTAs on two SMs computes 256
+// positions x 128 channels per tile with tcgen05.mma.cta_group::2 (M 256,
+// N 128, K 16): CTA rank r stages rows 256 tile + 128 r - 4 .. + 135 of the
+// input (A rows 128 r .. 128 r + 127 of the MMA) and the weights of output
+// channels 64 r .. 64 r + 63 (B rows 64 r .. of the MMA), at the same
+// shared-memory offsets in both CTAs; the even CTA issues every MMA, and
+// each CTA's tensor memory receives the accumulator rows of its own
+// positions for all 128 channels.  Per SM this is twice the work of one
+// 1-SM M 128 x N 64 instruction, and each CTA keeps only half the weights.
+//   even CTA: warp 0 TMA of its tiles, warp 1 MMA issuer, warps 2-5 epilogue
+//   odd CTA:  warp 0 TMA of its tiles, relaying each landed load to the even
+//             CTA's barrier; warps 2-5 epilogue
+// Barriers (same offsets in both CTAs): W and AFULL count the even CTA's
+// own expect_tx arrival plus the odd CTA's relay; AEMPTY and CFULL are
+// signalled in both CTAs by the multicast commit of the MMAs; CEMPTY (even
+// CTA) counts the eight epilogue warps of the pair.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// the shared::cluster address of this CTA's shared variable at `saddr` in CTA `rank`
+__device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// mbar_wait with cluster-scope acquire: the barriers of the pair kernel are
+// also signalled from the other CTA (relayed arrivals, multicast commits)
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, long long spins) {
+  for (long long i = 0; i < spins; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// no memory ordering: for handing back an accumulator whose tensor-memory
+// reads have completed (tcgen05.wait::ld) and been fenced
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+
+// kind::f16, fp32 accumulator, bf16 A and B, K-major, N 128, M 256 (the pair)
+constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                                ((uint32_t)(256 >> 4) << 24);
+
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p; }"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accumulate)
+      : "memory");
+}
+
+// arrive once on the mbarrier at `bar` in both CTAs of the pair when every
+// MMA issued before has completed
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+      ::"r"(bar), "h"((unsigned short)3)
+      : "memory");
+}
+
+constexpr int PAIR_TBM = 2 * TBM;  // positions per pair tile
+constexpr int PAIR_COUT = 128;
+constexpr int PAIR_TMEM = 2 * PAIR_COUT;  // two accumulators of 128 columns
+
+template <int CIN, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
+           const float *__restrict__ bias, const int32_t *__restrict__ rowseq,
+           const bf16 *__restrict__ prev, bf16 *__restrict__ y, int T, unsigned *err,
+           long long spins) {
+  using Gm = Geo<CIN>;
+  constexpr int COUT = PAIR_COUT;
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) unsigned long long bars[NBARS];
+  __shared__ float s_bias[COUT];
+  __shared__ uint32_t tmem_slot;
+  const uint32_t raw = smem_u32(tc_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t sW = base;
+  const uint32_t sA0 = base + Gm::W_BYTES;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();
+  const bool even = rank == 0;
+  const int first = (int)(blockIdx.x >> 1), stride = (int)(gridDim.x >> 1);
+  const int ntiles = (T + PAIR_TBM - 1) / PAIR_TBM;
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+
+  if (tid == 0) {
+    mbar_init(bar(B_W), even ? 2 : 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(B_AFULL + b), even ? 2 : 1);
+      mbar_init(bar(B_AEMPTY + b), 1);
+      mbar_init(bar(B_CFULL + b), 1);
+      mbar_init(bar(B_CEMPTY + b), 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (tid < COUT) s_bias[tid] = MODE == 2 ? 0.f : bias[tid];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(PAIR_TMEM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  // both CTAs' barriers are initialised before either signals the other's
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---- TMA producer (both CTAs): own tiles into own shared memory
+    if (lane == 0 && first < ntiles) {
+      mbar_expect_tx(bar(B_W), (uint32_t)Gm::W_BYTES);
+      for (int t = 0; t < TAPS; ++t)
+        for (int kb = 0; kb < Gm::KB; ++kb)
+          tma_load_2d(sW + (uint32_t)((t * Gm::KB + kb) * Gm::B_BLOCK), &wmap, kb * Gm::BLK,
+                      t * COUT + (int)rank * TBN, bar(B_W));
+      int issued = 0;
+      for (int it = 0, tile = first; tile < ntiles && ok; tile += stride, ++it) {
+        const int b = it & 1, k = it >> 1;
+        if (k > 0 && !mbar_wait_cl(bar(B_AEMPTY + b), (uint32_t)((k - 1) & 1), spins)) { ok = false; break; }
+        const uint32_t sA = sA0 + (uint32_t)(b * Gm::A_BYTES);
+        mbar_expect_tx(bar(B_AFULL + b), (uint32_t)(Gm::KB * Gm::A_BLOCK));
+        for (int kb = 0; kb < Gm::KB; ++kb)
+          tma_load_2d(sA + (uint32_t)(kb * Gm::A_BLOCK), &xmap, kb * Gm::BLK,
+                      tile * PAIR_TBM + (int)rank * TBM - HALF, bar(B_AFULL + b));
+        ++issued;
+        if (!even) {
+          // relay: once this CTA's weights and tile have landed, arrive on
+          // the even CTA's barriers
+          if (it == 0) {
+            if (!mbar_wait_cl(bar(B_W), 0, spins)) { ok = false; break; }
+            mbar_arrive_cluster(peer_addr(bar(B_W), 0));
+          }
+          if (!mbar_wait_cl(bar(B_AFULL + b), (uint32_t)(k & 1), spins)) { ok = false; break; }
+          mbar_arrive_cluster(peer_addr(bar(B_AFULL + b), 0));
+        }
+      }
+      if (even) {
+        // no copy may still be landing when the CTA exits (bounded)
+        mbar_wait_cl(bar(B_W), 0, spins);
+        for (int it = issued - 2; it < issued; ++it)
+          if (it >= 0) mbar_wait_cl(bar(B_AFULL + (it & 1)), (uint32_t)((it >> 1) & 1), spins);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer (even CTA)
+    if (even && lane == 0 && first < ntiles) {
+      int last = -1;
+      if (!mbar_wait_cl(bar(B_W), 0, spins)) ok = false;
+      for (int it = 0, tile = first; ok && tile < ntiles; tile += stride, ++it) {
+        const int b = it & 1, k = it >> 1;
+        if (!mbar_wait_cl(bar(B_AFULL + b), (uint32_t)(k & 1), spins)) { ok = false; break; }
+        if (k > 0 && !mbar_wait_cl(bar(B_CEMPTY + b), (uint32_t)((k - 1) & 1), spins)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sA = sA0 + (uint32_t)(b * Gm::A_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(b * COUT);
+#pragma unroll 1
+        for (int t = 0; t < TAPS; ++t) {
+          const int wt = MODE == 2 ? TAPS - 1 - t : t;
+#pragma unroll
+          for (int kb = 0; kb < Gm::KB; ++kb) {
+#pragma unroll
+            for (int kk = 0; kk < Gm::BLK / 16; ++kk) {
+              const uint64_t ad = smem_desc<Gm::ROWB>(sA + (uint32_t)(kb * Gm::A_BLOCK + t * Gm::ROWB + kk * 32));
+              const uint64_t bd = smem_desc<Gm::ROWB>(sW + (uint32_t)((wt * Gm::KB + kb) * Gm::B_BLOCK + kk * 32));
+              umma_pair(acc, ad, bd, (t | kb | kk) != 0 ? 1u : 0u);
+            }
+          }
+        }
+        umma_commit_pair(bar(B_AEMPTY + b));
+        umma_commit_pair(bar(B_CFULL + b));
+        last = it;
+      }
+      // no MMA may still be running: the last commit's barrier (bounded)
+      if (last >= 0) mbar_wait_cl(bar(B_AEMPTY + (last & 1)), (uint32_t)((last >> 1) & 1), spins);
+    }
+  } else {
+    // ---- epilogue (both CTAs): warp w reads accumulator rows 32 (w % 4) ..
+    // + 31 of this CTA's tensor memory, all 128 channels
+    const int q = warp & 3;
+    for (int it = 0, tile = first; tile < ntiles; tile += stride, ++it) {
+      const int b = it & 1, k = it >> 1;
+      if (!mbar_wait_cl(bar(B_CFULL + b), (uint32_t)(k & 1), spins)) { ok = false; break; }
+      tc_fence_after();
+      const int r = tile * PAIR_TBM + (int)rank * TBM + q * 32 + lane;
+      const bool inb = r < T;
+      const bool valid = inb && rowseq[r] >= 0;
+      // the whole row slice into registers, then the accumulator goes back
+      // to the issuer before any store (a release here would wait on them)
+      float v[COUT / 32][32];
+#pragma unroll
+      for (int c = 0; c < COUT / 32; ++c)
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * COUT + 32 * c), v[c]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster_relaxed(peer_addr(bar(B_CEMPTY + b), 0));
+      if (!inb) continue;
+#pragma unroll
+      for (int c = 0; c < COUT / 32; ++c) {
+        const int c0 = 32 * c;
+        uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)r * COUT + c0);
+        const uint4 *pv = MODE == 2 ? reinterpret_cast<const uint4 *>(prev + (size_t)r * COUT + c0) : nullptr;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t w[4];
+          uint4 pm = make_uint4(0u, 0u, 0u, 0u);
+          if constexpr (MODE == 2) pm = pv[j];
+          const uint32_t pw[4] = {pm.x, pm.y, pm.z, pm.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int cc = 8 * j + 2 * h;
+            float a = v[c][cc], bb = v[c][cc + 1];
+            if constexpr (MODE == 0) {
+              a = valid ? fmaxf(a + s_bias[c0 + cc], 0.f) : 0.f;
+              bb = valid ? fmaxf(bb + s_bias[c0 + cc + 1], 0.f) : 0.f;
+            } else {
+              const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162 *>(&pw[h]);
+              a = valid && __bfloat162float(p2.x) > 0.f ? a : 0.f;
+              bb = valid && __bfloat162float(p2.y) > 0.f ? bb : 0.f;
+            }
+            const __nv_bfloat162 o2 = __floats2bfloat162_rn(a, bb);
+            w[h] = *reinterpret_cast<const uint32_t *>(&o2);
+          }
+          dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+    }
+  }
+  if (!ok) atomicOr(err, MSA_DERR_TIMEOUT_TC);
+  // both CTAs stay resident until every role of the pair has returned (the
+  // even CTA's MMAs read the odd CTA's shared memory and write its tensor
+  // memory); then the pair frees its tensor memory
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PAIR_TMEM));
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -577,6 +849,41 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int
   return cudaGetLastError();
 }
 
+// the CTA-pair kernel: one pair per tile of 256 positions, at most as many
+// pairs as can be resident at once
+template <int CIN, int MODE>
+cudaError_t launch_tc2(const bf16 *x, const bf16 *w, const float *bias, const int32_t *rowseq,
+                       const bf16 *prev, bf16 *y, int T, unsigned *err, cudaStream_t st,
+                       long long spins) {
+  using Gm = Geo<CIN>;
+  CUtensorMap xm, wm;
+  if (!make_map(&xm, x, (uint64_t)T, CIN, AROWS, Gm::BLK) ||
+      !make_map(&wm, w, (uint64_t)TAPS * PAIR_COUT, CIN, TBN, Gm::BLK))
+    return cudaErrorInvalidValue;
+  constexpr int smem = Gm::SMEM;
+  auto fn = k_conv_tc2<CIN, MODE>;
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  static int mp = 0;  // resident pairs of this instantiation (one device per process)
+  if (mp == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (unsigned)std::max(1, sm_count() / 2));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)fn, &cfg) != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      clusters = std::max(1, sm_count() / 2);
+    }
+    mp = clusters;
+  }
+  const int ntiles = (T + PAIR_TBM - 1) / PAIR_TBM;
+  const int pairs = std::min(ntiles, mp);
+  fn<<<2 * pairs, TC_THREADS, smem, st>>>(xm, wm, bias, rowseq, prev, y, T, err, spins);
+  return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t launch_wgrad_tc(const bf16 *x, const bf16 *dy, float *dw, int T, unsigned *err,
                             cudaStream_t st, long long spins) {
@@ -617,6 +924,15 @@ cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, c
   if (T <= 0) return cudaSuccess;
   if (spins <= 0) spins = kSpinLimit;
   const int nl = no_loads ? 1 : 0;
+  // 128 output channels: the CTA-pair kernel (the load-free self-test keeps
+  // the single-CTA one)
+  if (!no_loads && cout == 128) {
+    bf16 *yb = static_cast<bf16 *>(y);
+    if (cin == 128 && mode == 0) return launch_tc2<128, 0>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
+    if (cin == 128 && mode == 2) return launch_tc2<128, 2>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
+    if (cin == 64 && mode == 2) return launch_tc2<64, 2>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
+    if (cin == 32 && mode == 0) return launch_tc2<32, 0>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
+  }
 #define NET_TC(CI, CO, MD) \
   if (cin == CI && cout == CO && mode == MD) \
     return launch_tc<CI, CO, MD>(x, w, bias, rowseq, prev, y, T, err, st, spins, nl);
