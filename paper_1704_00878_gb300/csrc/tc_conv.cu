@@ -157,6 +157,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 consecutive fp32 accumulator columns of this warp's 32 rows, one
+// load and one wait
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -350,22 +365,25 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
 }
 
 // ---------------------------------------------------------------- CTA-pair convolution
-// 128 output channels: a cluster of two CTAs on two SMs computes 256
-// positions x 128 channels per tile with tcgen05.mma.cta_group::2 (M 256,
-// N 128, K 16): CTA rank r stages rows 256 tile + 128 r - 4 .. + 135 of the
-// input (A rows 128 r .. 128 r + 127 of the MMA) and the weights of output
-// channels 64 r .. 64 r + 63 (B rows 64 r .. of the MMA), at the same
-// shared-memory offsets in both CTAs; the even CTA issues every MMA, and
-// each CTA's tensor memory receives the accumulator rows of its own
-// positions for all 128 channels.  Per SM this is twice the work of one
-// 1-SM M 128 x N 64 instruction, and each CTA keeps only half the weights.
-//   even CTA: warp 0 TMA of its tiles, warp 1 MMA issuer, warps 2-5 epilogue
+// Every convolution of the network also runs on CTA pairs: a cluster of two
+// CTAs on two SMs computes 256 positions x COUT (64 or 128) channels per
+// tile with tcgen05.mma.cta_group::2 (M 256, N COUT, K 16).  CTA rank r
+// stages rows 256 tile + 128 r - 4 .. + 135 of the input (A rows 128 r ..
+// 128 r + 127 of the MMA) and the weights of output channels COUT / 2 r ..
+// + COUT / 2 - 1 (its half of B), at the same shared-memory offsets in both
+// CTAs; the even CTA issues every MMA, and each CTA's tensor memory
+// receives the accumulator rows of its own positions for all COUT
+// channels.  One instruction drives both SMs' tensor cores, and each CTA
+// keeps only half the weights.
+//   even CTA: warp 0 TMA of its tiles, warp 1 MMA issuer, warps 2-9 epilogue
 //   odd CTA:  warp 0 TMA of its tiles, relaying each landed load to the even
-//             CTA's barrier; warps 2-5 epilogue
-// Barriers (same offsets in both CTAs): W and AFULL count the even CTA's
-// own expect_tx arrival plus the odd CTA's relay; AEMPTY and CFULL are
-// signalled in both CTAs by the multicast commit of the MMAs; CEMPTY (even
-// CTA) counts the eight epilogue warps of the pair.
+//             CTA's barrier; warps 2-9 epilogue
+// Epilogue warps w and w + 4 share tensor-memory lanes 32 (w % 4) .. + 31
+// and take one half of the channels each.  Barriers (same offsets in both
+// CTAs): W and AFULL count the even CTA's own expect_tx arrival plus the odd
+// CTA's relay; AEMPTY and CFULL are signalled in both CTAs by the multicast
+// commit of the MMAs; CEMPTY (even CTA) counts the sixteen epilogue warps of
+// the pair.
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -412,16 +430,19 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
                : "memory");
 }
 
-// kind::f16, fp32 accumulator, bf16 A and B, K-major, N 128, M 256 (the pair)
-constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
-                                ((uint32_t)(256 >> 4) << 24);
+// kind::f16, fp32 accumulator, bf16 A and B, K-major, N = COUT, M 256 (the pair)
+template <int COUT>
+__host__ __device__ constexpr uint32_t pair_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
 
+template <int COUT>
 __device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                           uint32_t accumulate) {
   asm volatile(
       "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
       "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p; }"
-      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accumulate)
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(pair_idesc<COUT>()), "r"(accumulate)
       : "memory");
 }
 
@@ -435,17 +456,29 @@ __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
 }
 
 constexpr int PAIR_TBM = 2 * TBM;  // positions per pair tile
-constexpr int PAIR_COUT = 128;
-constexpr int PAIR_TMEM = 2 * PAIR_COUT;  // two accumulators of 128 columns
+// the pair kernel's warps: TMA producer, MMA issuer, eight epilogue warps
+// (two per 32-lane quarter of tensor memory, each taking half the channels)
+constexpr int PAIR_THREADS = 320;
 
-template <int CIN, int MODE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+// Shared-memory geometry of the pair kernel: the input tile as in Geo, and
+// each CTA's half of the output channels' weights (BN = COUT / 2 rows).
+template <int CIN, int COUT> struct PairGeo {
+  using G = Geo<CIN>;
+  static constexpr int BN = COUT / 2;
+  static constexpr int B_BLOCK = BN * G::ROWB;
+  static constexpr int W_BYTES = TAPS * G::KB * B_BLOCK;
+  static constexpr int SMEM = W_BYTES + 2 * G::A_BYTES + 1024;
+  static constexpr int TMEM = 2 * COUT;  // two accumulators
+};
+
+template <int CIN, int COUT, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PAIR_THREADS, 1)
 k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
            const float *__restrict__ bias, const int32_t *__restrict__ rowseq,
-           const bf16 *__restrict__ prev, bf16 *__restrict__ y, int T, unsigned *err,
+           const bf16 *__restrict__ prev, void *__restrict__ y, int T, unsigned *err,
            long long spins) {
   using Gm = Geo<CIN>;
-  constexpr int COUT = PAIR_COUT;
+  using Pg = PairGeo<CIN, COUT>;
   extern __shared__ unsigned char tc_raw[];
   __shared__ __align__(8) unsigned long long bars[NBARS];
   __shared__ float s_bias[COUT];
@@ -453,7 +486,7 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
   const uint32_t raw = smem_u32(tc_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   const uint32_t sW = base;
-  const uint32_t sA0 = base + Gm::W_BYTES;
+  const uint32_t sA0 = base + Pg::W_BYTES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = cluster_rank();
   const bool even = rank == 0;
@@ -467,7 +500,7 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
       mbar_init(bar(B_AFULL + b), even ? 2 : 1);
       mbar_init(bar(B_AEMPTY + b), 1);
       mbar_init(bar(B_CFULL + b), 1);
-      mbar_init(bar(B_CEMPTY + b), 8);
+      mbar_init(bar(B_CEMPTY + b), 16);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -476,7 +509,7 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(PAIR_TMEM));
+                 "r"(Pg::TMEM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   // both CTAs' barriers are initialised before either signals the other's
@@ -489,11 +522,11 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
   if (warp == 0) {
     // ---- TMA producer (both CTAs): own tiles into own shared memory
     if (lane == 0 && first < ntiles) {
-      mbar_expect_tx(bar(B_W), (uint32_t)Gm::W_BYTES);
+      mbar_expect_tx(bar(B_W), (uint32_t)Pg::W_BYTES);
       for (int t = 0; t < TAPS; ++t)
         for (int kb = 0; kb < Gm::KB; ++kb)
-          tma_load_2d(sW + (uint32_t)((t * Gm::KB + kb) * Gm::B_BLOCK), &wmap, kb * Gm::BLK,
-                      t * COUT + (int)rank * TBN, bar(B_W));
+          tma_load_2d(sW + (uint32_t)((t * Gm::KB + kb) * Pg::B_BLOCK), &wmap, kb * Gm::BLK,
+                      t * COUT + (int)rank * Pg::BN, bar(B_W));
       int issued = 0;
       for (int it = 0, tile = first; tile < ntiles && ok; tile += stride, ++it) {
         const int b = it & 1, k = it >> 1;
@@ -542,8 +575,8 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
 #pragma unroll
             for (int kk = 0; kk < Gm::BLK / 16; ++kk) {
               const uint64_t ad = smem_desc<Gm::ROWB>(sA + (uint32_t)(kb * Gm::A_BLOCK + t * Gm::ROWB + kk * 32));
-              const uint64_t bd = smem_desc<Gm::ROWB>(sW + (uint32_t)((wt * Gm::KB + kb) * Gm::B_BLOCK + kk * 32));
-              umma_pair(acc, ad, bd, (t | kb | kk) != 0 ? 1u : 0u);
+              const uint64_t bd = smem_desc<Gm::ROWB>(sW + (uint32_t)((wt * Gm::KB + kb) * Pg::B_BLOCK + kk * 32));
+              umma_pair<COUT>(acc, ad, bd, (t | kb | kk) != 0 ? 1u : 0u);
             }
           }
         }
@@ -556,8 +589,12 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
     }
   } else {
     // ---- epilogue (both CTAs): warp w reads accumulator rows 32 (w % 4) ..
-    // + 31 of this CTA's tensor memory, all 128 channels
-    const int q = warp & 3;
+    // + 31 of this CTA's tensor memory, channels hh * COUT / 2 .. + COUT / 2
+    // (hh = 0 for warps 2-5, 1 for warps 6-9)
+    constexpr int HC = COUT / 2;                      // channels per warp
+    constexpr int OUTB = MODE == 1 ? 4 : 2;           // output bytes per channel
+    constexpr int NCH = HC * OUTB / 16;               // 16-byte chunks per warp row
+    const int q = warp & 3, hh = (warp - 2) >> 2;
     for (int it = 0, tile = first; tile < ntiles; tile += stride, ++it) {
       const int b = it & 1, k = it >> 1;
       if (!mbar_wait_cl(bar(B_CFULL + b), (uint32_t)(k & 1), spins)) { ok = false; break; }
@@ -565,34 +602,41 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
       const int r = tile * PAIR_TBM + (int)rank * TBM + q * 32 + lane;
       const bool inb = r < T;
       const bool valid = inb && rowseq[r] >= 0;
-      // the whole row slice into registers, then the accumulator goes back
-      // to the issuer before any store (a release here would wait on them)
-      float v[COUT / 32][32];
-#pragma unroll
-      for (int c = 0; c < COUT / 32; ++c)
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * COUT + 32 * c), v[c]);
+      // this warp's slice into registers (one load, one wait), then the
+      // accumulator goes back to the issuer before any store
+      float v[HC];
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * COUT + hh * HC);
+      if constexpr (HC == 64) tmem_ld64(ta, v);
+      else tmem_ld32(ta, v);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster_relaxed(peer_addr(bar(B_CEMPTY + b), 0));
       if (!inb) continue;
+      const int cb = hh * HC;  // first channel of this warp
+      uint4 *dst = reinterpret_cast<uint4 *>(static_cast<unsigned char *>(y) + ((size_t)r * COUT + cb) * OUTB);
+      const uint4 *pv = MODE == 2 ? reinterpret_cast<const uint4 *>(prev + (size_t)r * COUT + cb) : nullptr;
 #pragma unroll
-      for (int c = 0; c < COUT / 32; ++c) {
-        const int c0 = 32 * c;
-        uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)r * COUT + c0);
-        const uint4 *pv = MODE == 2 ? reinterpret_cast<const uint4 *>(prev + (size_t)r * COUT + c0) : nullptr;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          uint32_t w[4];
+      for (int jc = 0; jc < NCH; ++jc) {
+        if constexpr (MODE == 1) {
+          const int e = 4 * jc;
+          float4 o;
+          o.x = valid ? v[e] + s_bias[cb + e] : 0.f;
+          o.y = valid ? v[e + 1] + s_bias[cb + e + 1] : 0.f;
+          o.z = valid ? v[e + 2] + s_bias[cb + e + 2] : 0.f;
+          o.w = valid ? v[e + 3] + s_bias[cb + e + 3] : 0.f;
+          dst[jc] = *reinterpret_cast<const uint4 *>(&o);
+        } else {
+          const int e = 8 * jc;
           uint4 pm = make_uint4(0u, 0u, 0u, 0u);
-          if constexpr (MODE == 2) pm = pv[j];
-          const uint32_t pw[4] = {pm.x, pm.y, pm.z, pm.w};
+          if constexpr (MODE == 2) pm = pv[jc];
+          [[maybe_unused]] const uint32_t pw[4] = {pm.x, pm.y, pm.z, pm.w};
+          uint32_t w[4];
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const int cc = 8 * j + 2 * h;
-            float a = v[c][cc], bb = v[c][cc + 1];
+            float a = v[e + 2 * h], bb = v[e + 2 * h + 1];
             if constexpr (MODE == 0) {
-              a = valid ? fmaxf(a + s_bias[c0 + cc], 0.f) : 0.f;
-              bb = valid ? fmaxf(bb + s_bias[c0 + cc + 1], 0.f) : 0.f;
+              a = valid ? fmaxf(a + s_bias[cb + e + 2 * h], 0.f) : 0.f;
+              bb = valid ? fmaxf(bb + s_bias[cb + e + 2 * h + 1], 0.f) : 0.f;
             } else {
               const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162 *>(&pw[h]);
               a = valid && __bfloat162float(p2.x) > 0.f ? a : 0.f;
@@ -601,7 +645,7 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
             const __nv_bfloat162 o2 = __floats2bfloat162_rn(a, bb);
             w[h] = *reinterpret_cast<const uint32_t *>(&o2);
           }
-          dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[jc] = make_uint4(w[0], w[1], w[2], w[3]);
         }
       }
     }
@@ -614,7 +658,7 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
   cluster_sync_all();
   tc_fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PAIR_TMEM));
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Pg::TMEM));
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -851,24 +895,25 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int
 
 // the CTA-pair kernel: one pair per tile of 256 positions, at most as many
 // pairs as can be resident at once
-template <int CIN, int MODE>
+template <int CIN, int COUT, int MODE>
 cudaError_t launch_tc2(const bf16 *x, const bf16 *w, const float *bias, const int32_t *rowseq,
-                       const bf16 *prev, bf16 *y, int T, unsigned *err, cudaStream_t st,
+                       const bf16 *prev, void *y, int T, unsigned *err, cudaStream_t st,
                        long long spins) {
   using Gm = Geo<CIN>;
+  using Pg = PairGeo<CIN, COUT>;
   CUtensorMap xm, wm;
   if (!make_map(&xm, x, (uint64_t)T, CIN, AROWS, Gm::BLK) ||
-      !make_map(&wm, w, (uint64_t)TAPS * PAIR_COUT, CIN, TBN, Gm::BLK))
+      !make_map(&wm, w, (uint64_t)TAPS * COUT, CIN, Pg::BN, Gm::BLK))
     return cudaErrorInvalidValue;
-  constexpr int smem = Gm::SMEM;
-  auto fn = k_conv_tc2<CIN, MODE>;
+  constexpr int smem = Pg::SMEM;
+  auto fn = k_conv_tc2<CIN, COUT, MODE>;
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   static int mp = 0;  // resident pairs of this instantiation (one device per process)
   if (mp == 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * (unsigned)std::max(1, sm_count() / 2));
-    cfg.blockDim = dim3(TC_THREADS);
+    cfg.blockDim = dim3(PAIR_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     int clusters = 0;
@@ -880,7 +925,7 @@ cudaError_t launch_tc2(const bf16 *x, const bf16 *w, const float *bias, const in
   }
   const int ntiles = (T + PAIR_TBM - 1) / PAIR_TBM;
   const int pairs = std::min(ntiles, mp);
-  fn<<<2 * pairs, TC_THREADS, smem, st>>>(xm, wm, bias, rowseq, prev, y, T, err, spins);
+  fn<<<2 * pairs, PAIR_THREADS, smem, st>>>(xm, wm, bias, rowseq, prev, y, T, err, spins);
   return cudaGetLastError();
 }
 
@@ -924,14 +969,19 @@ cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, c
   if (T <= 0) return cudaSuccess;
   if (spins <= 0) spins = kSpinLimit;
   const int nl = no_loads ? 1 : 0;
-  // 128 output channels: the CTA-pair kernel (the load-free self-test keeps
-  // the single-CTA one)
-  if (!no_loads && cout == 128) {
-    bf16 *yb = static_cast<bf16 *>(y);
-    if (cin == 128 && mode == 0) return launch_tc2<128, 0>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
-    if (cin == 128 && mode == 2) return launch_tc2<128, 2>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
-    if (cin == 64 && mode == 2) return launch_tc2<64, 2>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
-    if (cin == 32 && mode == 0) return launch_tc2<32, 0>(x, w, bias, rowseq, prev, yb, T, err, st, spins);
+  // every shape runs on CTA pairs (the load-free self-test keeps the
+  // single-CTA kernel)
+  if (!no_loads) {
+#define NET_TC2(CI, CO, MD) \
+    if (cin == CI && cout == CO && mode == MD) \
+      return launch_tc2<CI, CO, MD>(x, w, bias, rowseq, prev, y, T, err, st, spins);
+    NET_TC2(128, 128, 0)
+    NET_TC2(128, 128, 2)
+    NET_TC2(128, 64, 1)
+    NET_TC2(64, 128, 2)
+    NET_TC2(32, 128, 0)
+#undef NET_TC2
+    return cudaErrorInvalidValue;
   }
 #define NET_TC(CI, CO, MD) \
   if (cin == CI && cout == CO && mode == MD) \
