@@ -57,6 +57,8 @@ def parse():
                     help="override lengths, e.g. uniform:340:360 (profiling cases)")
     ap.add_argument("--only-center", action="store_true",
                     help="time the exact-center selection alone (profiling cases)")
+    ap.add_argument("--align-group", type=int, default=0,
+                    help="lanes per subject group of the alignment kernels (0 = modelled)")
     ap.add_argument("--only-align", action="store_true",
                     help="time the alignment to one center alone (profiling cases): the "
                          "workload's own center if it has one, else the median-length sequence")
@@ -358,6 +360,8 @@ def run_ours(args):
         ctx.close()
         return
 
+    if args.align_group:
+        b.msa_set_align_group(h, args.align_group)
     if args.only_align:
         lens = np.diff(offsets)
         center = 0 if w.center_seq else int(np.argsort(lens, kind="stable")[len(lens) // 2])

@@ -311,6 +311,12 @@ int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes);
  * result does not depend on it.  EINVAL for a budget < 1. */
 int msa_set_codes_budget(msa_ctx *ctx, int64_t bytes);
 
+/* Lanes per subject group of the alignment kernels (8, 16 or 32; each lane
+ * holds 16 center rows, so a pass covers 16 x lanes rows), or 0 for the
+ * choice of the library's cost model (the default).  A tuning knob: the
+ * result does not depend on it.  EINVAL for any other value. */
+int msa_set_align_group(msa_ctx *ctx, int32_t lanes);
+
 /* Self-test of the bounded waits of the tensor-core convolution (no
  * counterpart in the paper): runs one small convolution whose loads are
  * never issued, with a short poll limit, so every mbarrier wait runs out.

@@ -67,6 +67,7 @@ _SIGS = {
     "msa_memory": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_set_memory_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "msa_set_codes_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "msa_set_align_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "msa_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
@@ -293,6 +294,13 @@ def msa_memory(ctx):
 
 def msa_set_memory_limit(ctx, limit_bytes):
     _check(ctx, lib().msa_set_memory_limit(ctx, int(limit_bytes)))
+
+
+def msa_set_align_group(ctx, lanes):
+    """Lanes per subject group of the alignment kernels (8, 16, 32; 0 = modelled)."""
+    rc = lib().msa_set_align_group(ctx, int(lanes))
+    if rc != MSA_OK:
+        raise MSAError(rc, "align group must be 0, 8, 16 or 32")
 
 
 def msa_set_codes_budget(ctx, nbytes):

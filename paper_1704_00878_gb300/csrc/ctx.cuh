@@ -84,6 +84,7 @@ struct msa_ctx {
   // batches of subjects whose codes fit; a batch should fill the GPU many
   // times over, and the traceback of each batch waits for its fill
   size_t codes_budget = (size_t)32 << 30;
+  int align_group = 0;  // lanes per subject group of the codes kernels, 0 = modelled choice
 
   msa_detail::Selector *sel = nullptr;
 

@@ -216,6 +216,7 @@ static bool codes_packed(msa_ctx *ctx, int Lc) {
 
 // group size of the alignment kernel for this set and a center of length Lc
 static int align_group(msa_ctx *ctx, int Lc, bool packed) {
+  if (ctx->align_group > 0) return ctx->align_group;
   double total = 0.0;
   for (int L : ctx->len_sorted) total += L;
   return codes_group(Lc, packed, ctx->K, ctx->n, ctx->n ? total / ctx->n : 0.0, ctx->maxlen);
@@ -1281,6 +1282,12 @@ int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out) {
 int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes) {
   if (!ctx || limit_bytes < 0) return MSA_EINVAL;
   ctx->dev_limit = (size_t)limit_bytes;
+  return MSA_OK;
+}
+
+int msa_set_align_group(msa_ctx *ctx, int32_t lanes) {
+  if (!ctx || (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32)) return MSA_EINVAL;
+  ctx->align_group = lanes;
   return MSA_OK;
 }
 

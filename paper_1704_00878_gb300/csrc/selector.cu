@@ -271,7 +271,7 @@ int exact_targets(msa_ctx *ctx, const int64_t *pairs, int64_t np, float scale,
 int embed_all(msa_ctx *ctx, Selector *s) {
   const int n = ctx->n;
   TRY(ensure(ctx, s->allemb, sizeof(float) * (size_t)n * net::DIM));
-  const int64_t max_rows = (int64_t)1 << 21;
+  const int64_t max_rows = (int64_t)1 << 23;  // ~1.1 KB of activations per row
   int k = 0;
   while (k < n) {
     std::vector<int32_t> seqs;

@@ -1142,7 +1142,10 @@ int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_
     const double units = packed ? (double)((n + 1) / 2) : (double)n;
     const double tasks = std::ceil(units / (32 / G));
     const double mean_steps = npass * (mean_len + G - 1), max_steps = npass * (max_len + G - 1.0);
-    const double est = std::max(tasks * mean_steps / warps, max_steps);
+    // a step costs more the narrower the group (measured on one GB300: 1.5 kb
+    // DNA against a 1.5 kb center at G = 8 / 16 / 32 took 1.17 / 1.04 / 1 x
+    // the time for the same number of steps): 1 + 1.8 / G
+    const double est = std::max(tasks * mean_steps / warps, max_steps) * (1.0 + 1.8 / G);
     if (G == 32 || est < best) { best = est; best_g = G; }
   }
   return best_g;

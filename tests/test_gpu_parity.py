@@ -157,17 +157,21 @@ def test_msa_long_center_multipass():
     check_against_oracle(prob, center, *out)
 
 
-@pytest.mark.parametrize("budget", [1, 300_000])
-def test_msa_in_code_batches(budget):
+@pytest.mark.parametrize("budget,lanes", [(1, 8), (300_000, 32), (300_000, 16)])
+def test_msa_in_code_batches(budget, lanes):
     """Codes budgets that split the alignment into one subject per batch and
-    into a few batches give the same MSA as the oracle."""
+    into a few batches, with each group width of the alignment kernels, give
+    the same MSA as the oracle."""
     b = binding()
     letters, offsets, w, alph, M = workload("plain_protein_200", n=60, seed=12)
     prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
         b.msa_set_codes_budget(h, budget)
+        b.msa_set_align_group(h, lanes)
         with pytest.raises(b.MSAError):
             b.msa_set_codes_budget(h, 0)
+        with pytest.raises(b.MSAError):
+            b.msa_set_align_group(h, 12)
         out = run_pipeline(b, h, letters, offsets, 7)
     check_against_oracle(prob, 7, *out)
 
