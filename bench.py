@@ -382,9 +382,10 @@ def run_ours(args):
         for _ in range(max(1, args.warmup)):
             b.msa_select_center(h, b.MSA_CENTER_LEARNED)
         ms = b.msa_stage_times(h)[0]["selector"]
-        # conv flops per row: 2 x 9 taps x (32x128 + 128x128 + 128x128 + 128x64)
+        # convolution flops: 2 x 9 taps x (32x128 + 128x128 + 128x128) per row,
+        # and the output layer (128x64) on the nine window sums per sequence
         rows = int(lens.sum()) + 4 * (n + 1)
-        flops = 2 * 9 * (32 * 128 + 2 * 128 * 128 + 128 * 64) * rows
+        flops = 2 * 9 * (32 * 128 + 2 * 128 * 128) * rows + 2 * 9 * 128 * 64 * 9 * n
         print(json.dumps({"only_embed": True, "n": n, "rows": rows, "selector_ms": ms,
                           "tflops": flops / (ms * 1e-3) / 1e12}))
         ctx.close()
@@ -401,10 +402,14 @@ def run_ours(args):
         b.msa_selector_train(h, pairs, targets, steps=max(1, args.warmup), batch_pairs=256)
         b.msa_selector_train(h, pairs, targets, steps=steps, batch_pairs=256)
         ms = b.msa_stage_times(h)[0]["selector"] / steps
-        # forward + data gradient + weight gradient: 3x the forward flops of
-        # 512 sequences of the set's mean length (+ 4 zero rows each)
+        # 512 sequences of the set's mean length (+ 4 zero rows each): forward
+        # (output layer on nine window sums per sequence), data gradients of
+        # layers 4-2, weight gradients of all four layers
         rows = 512 * (float(lens.mean()) + 4)
-        flops = 3 * 2 * 9 * (32 * 128 + 2 * 128 * 128 + 128 * 64) * rows
+        fwd = 2 * 9 * (32 * 128 + 2 * 128 * 128) * rows + 2 * 9 * 128 * 64 * 9 * 512
+        dgrad = 2 * 9 * (64 * 128 + 2 * 128 * 128) * rows
+        wgrad = 2 * 9 * (32 * 128 + 2 * 128 * 128 + 128 * 64) * rows
+        flops = fwd + dgrad + wgrad
         print(json.dumps({"only_train": True, "n": n, "ms_per_step": ms,
                           "tflops": flops / (ms * 1e-3) / 1e12}))
         ctx.close()

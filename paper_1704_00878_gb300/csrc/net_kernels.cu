@@ -49,13 +49,72 @@ __global__ void k_onehot(Batch b, const uint8_t *__restrict__ res, const int64_t
   }
 }
 
-__global__ void k_pool(Batch b, const float *__restrict__ y4, float *__restrict__ emb) {
-  const int s = blockIdx.x, c = threadIdx.x;
-  if (s >= b.nseq || c >= DIM) return;
-  float acc = 0.f;
+// Pooling commutes with the linear output convolution: summed over the rows
+// r of sequence s, y4[r] = sum_t a3[r + t - 4] W4_t + b4 gives
+// sum_t P_t W4_t + len b4 with the window sums P_t = sum_r a3[r + t - 4]
+// (rows outside the sequence are zero).  P_0 covers rows base - 4 ..
+// base + len - 5 and P_{t+1} = P_t - a3[base - 4 + t] + a3[base + len - 4 + t].
+// One 128-thread block per sequence: each warp sums every fourth row of P_0
+// (four channels per lane), warp 0 adds the partial sums and slides the
+// window; the nine sums are written as rows 9 s .. 9 s + 8 of pw (bf16),
+// the input of the output convolution.
+__device__ __forceinline__ void load4(const bf16 *p, float (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2 *>(p);
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+  v[0] = __low2float(lo);
+  v[1] = __high2float(lo);
+  v[2] = __low2float(hi);
+  v[3] = __high2float(hi);
+}
+
+__global__ void k_window_sums(Batch b, const bf16 *__restrict__ a3, bf16 *__restrict__ pw) {
+  __shared__ float part[4][WD];
+  const int s = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (s >= b.nseq) return;
   const int base = b.base[s], L = b.len[s];
-  for (int i = 0; i < L; ++i) acc += y4[(size_t)(base + i) * DIM + c];
-  emb[(size_t)s * DIM + c] = acc * rsqrtf((float)L);
+  const bf16 *row0 = a3 + (size_t)(base - HALF) * WD + 4 * lane;  // row base - 4
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int i = warp; i < L; i += 4) {
+    float v[4];
+    load4(row0 + (size_t)i * WD, v);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] += v[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) part[warp][4 * lane + c] = acc[c];
+  __syncthreads();
+  if (warp != 0) return;
+  float p[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    p[c] = part[0][4 * lane + c] + part[1][4 * lane + c] + part[2][4 * lane + c] + part[3][4 * lane + c];
+  for (int t = 0; t < TAPS; ++t) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(p[0], p[1]), hi = __floats2bfloat162_rn(p[2], p[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t *>(&lo);
+    u.y = *reinterpret_cast<const uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(pw + ((size_t)TAPS * s + t) * WD + 4 * lane) = u;
+    if (t + 1 < TAPS) {
+      float out[4], in[4];
+      load4(row0 + (size_t)t * WD, out);
+      load4(row0 + (size_t)(L + t) * WD, in);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p[c] += in[c] - out[c];
+    }
+  }
+}
+
+// emb[s] = (row 9 s + 4 of the output convolution over the window sums,
+// which holds sum_t P_t W4_t + b4, plus (len - 1) b4) / sqrt(len)
+__global__ void k_emb_from_windows(Batch b, const float *__restrict__ yw, const float *__restrict__ b4,
+                                   float *__restrict__ emb) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)b.nseq * DIM) return;
+  const int s = (int)(idx / DIM), c = (int)(idx - (size_t)s * DIM);
+  const int L = b.len[s];
+  emb[idx] = (yw[((size_t)TAPS * s + HALF) * DIM + c] + (float)(L - 1) * b4[c]) * rsqrtf((float)L);
 }
 
 // One warp per pair: r = ||e_a - e_b||^2 - t; loss += r^2 / m;
@@ -191,9 +250,17 @@ cudaError_t colsum(int cout, const bf16 *dy, float *db, int T, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-cudaError_t pool(const Batch &b, const float *y4, float *emb, cudaStream_t st) {
+cudaError_t window_sums(const Batch &b, const bf16 *a3, bf16 *pw, cudaStream_t st) {
   if (b.nseq <= 0) return cudaSuccess;
-  k_pool<<<b.nseq, DIM, 0, st>>>(b, y4, emb);
+  k_window_sums<<<b.nseq, 128, 0, st>>>(b, a3, pw);
+  return cudaGetLastError();
+}
+
+cudaError_t emb_from_windows(const Batch &b, const float *yw, const float *b4, float *emb,
+                             cudaStream_t st) {
+  const size_t total = (size_t)b.nseq * DIM;
+  if (total == 0) return cudaSuccess;
+  k_emb_from_windows<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(b, yw, b4, emb);
   return cudaGetLastError();
 }
 

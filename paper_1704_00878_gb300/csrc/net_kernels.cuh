@@ -44,7 +44,8 @@ cudaError_t onehot(const Batch &b, const uint8_t *res, const int64_t *pstart, __
 // cout) = (32, 128) and (128, 128) mode 0, (128, 128) and (64, 128) mode 2,
 // (128, 64) mode 1.  mode 0: relu(x * W + b) -> bf16; mode 1: x * W + b ->
 // fp32; mode 2 (data gradient): (dy * W^T, taps reversed) masked by prev >
-// 0 -> bf16.  Padding rows are written as zero.  w: bf16 [9][cout][cin]
+// 0 -> bf16.  Padding rows (rowseq < 0) are written as zero; rowseq may be
+// null (every row valid).  w: bf16 [9][cout][cin]
 // ([tap][n][k]).  err: device error word (MSA_DERR_TIMEOUT_TC).  spins: polls
 // before an mbarrier wait gives up (<= 0: the default, seconds); no_loads:
 // the TMA warp issues nothing, so every wait runs out (the self-test of the
@@ -61,7 +62,14 @@ cudaError_t wgrad_tc(int cin, int cout, const __nv_bfloat16 *x, const __nv_bfloa
 // db[c] += sum_r dy[r][c]
 cudaError_t colsum(int cout, const __nv_bfloat16 *dy, float *db, int T, cudaStream_t st);
 
-cudaError_t pool(const Batch &b, const float *y4, float *emb, cudaStream_t st);
+// Pooled output layer: the nine window sums of the last hidden layer per
+// sequence (pw: bf16 [9 nseq][128], rows 9 s + t), then, after the output
+// convolution over them (mode 1, 9 nseq rows), the embedding
+// emb[s] = (yw[9 s + 4] + (len - 1) b4) / sqrt(len) of the length-scaled sum
+// of the output layer over the sequence's rows.
+cudaError_t window_sums(const Batch &b, const __nv_bfloat16 *a3, __nv_bfloat16 *pw, cudaStream_t st);
+cudaError_t emb_from_windows(const Batch &b, const float *yw, const float *b4, float *emb,
+                             cudaStream_t st);
 cudaError_t pair_loss(const int2 *pairs, const float *targets, int npairs, const float *emb,
                       float *demb, float *loss, cudaStream_t st);
 cudaError_t pool_backward(const Batch &b, const float *demb, __nv_bfloat16 *dy4, cudaStream_t st);

@@ -24,7 +24,7 @@ struct Selector {
   DevBuf w1t, w2t, w2n, w3t, w3n, w4t, w4n;        // bf16 weight copies
   int step = 0;
   // batch buffers
-  DevBuf seq, base, len, rowseq, x0, a1, a2, a3, y4, emb, demb, dy4, dz3, dz2, dz1;
+  DevBuf seq, base, len, rowseq, x0, a1, a2, a3, pw, yw, emb, demb, dy4, dz3, dz2, dz1;
   DevBuf bpairs, btargets, loss, small, allemb, dist;
   DevBuf vstart, vlen;  // a reference/candidate view of the loaded set
 };
@@ -127,7 +127,8 @@ int build_batch(msa_ctx *ctx, Selector *s, const std::vector<int32_t> &seqs, net
   TRY(ensure(ctx, s->a1, sizeof(bf16) * (size_t)T * net::WD));
   TRY(ensure(ctx, s->a2, sizeof(bf16) * (size_t)T * net::WD));
   TRY(ensure(ctx, s->a3, sizeof(bf16) * (size_t)T * net::WD));
-  TRY(ensure(ctx, s->y4, sizeof(float) * (size_t)T * net::DIM));
+  TRY(ensure(ctx, s->pw, sizeof(bf16) * (size_t)net::TAPS * ns * net::WD));
+  TRY(ensure(ctx, s->yw, sizeof(float) * (size_t)net::TAPS * ns * net::DIM));
   TRY(ensure(ctx, s->emb, sizeof(float) * (size_t)ns * net::DIM));
   CK(cudaMemcpyAsync(s->seq.p, seqs.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(s->base.p, base.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, ctx->st));
@@ -165,8 +166,12 @@ int forward(msa_ctx *ctx, Selector *s, const net::Batch &b) {
   CK(conv(ctx, net::KP, net::WD, 0, P<bf16>(s->x0), P<bf16>(s->w1t), p + net::B1_OFF, b.rowseq, nullptr, s->a1.p, T));
   CK(conv(ctx, net::WD, net::WD, 0, P<bf16>(s->a1), P<bf16>(s->w2t), p + net::B2_OFF, b.rowseq, nullptr, s->a2.p, T));
   CK(conv(ctx, net::WD, net::WD, 0, P<bf16>(s->a2), P<bf16>(s->w3t), p + net::B3_OFF, b.rowseq, nullptr, s->a3.p, T));
-  CK(conv(ctx, net::WD, net::DIM, 1, P<bf16>(s->a3), P<bf16>(s->w4t), p + net::B4_OFF, b.rowseq, nullptr, s->y4.p, T));
-  CK((++ctx->launches, net::pool)(b, P<float>(s->y4), P<float>(s->emb), ctx->st));
+  // output layer and pooling: the output convolution runs on the nine
+  // window sums of each sequence instead of on every row
+  CK((++ctx->launches, net::window_sums)(b, P<bf16>(s->a3), P<bf16>(s->pw), ctx->st));
+  CK(conv(ctx, net::WD, net::DIM, 1, P<bf16>(s->pw), P<bf16>(s->w4t), p + net::B4_OFF, nullptr, nullptr,
+          s->yw.p, net::TAPS * b.nseq));
+  CK((++ctx->launches, net::emb_from_windows)(b, P<float>(s->yw), p + net::B4_OFF, P<float>(s->emb), ctx->st));
   return MSA_OK;
 }
 
@@ -295,7 +300,7 @@ void selector_free(msa_ctx *ctx, Selector *s) {
   if (!s) return;
   DevBuf *bufs[] = {&s->params, &s->grads, &s->m, &s->v, &s->w1t, &s->w2t, &s->w2n, &s->w3t,
                     &s->w3n, &s->w4t, &s->w4n, &s->seq, &s->base, &s->len, &s->rowseq, &s->x0,
-                    &s->a1, &s->a2, &s->a3, &s->y4, &s->emb, &s->demb, &s->dy4, &s->dz3,
+                    &s->a1, &s->a2, &s->a3, &s->pw, &s->yw, &s->emb, &s->demb, &s->dy4, &s->dz3,
                     &s->dz2, &s->dz1, &s->bpairs, &s->btargets, &s->loss, &s->small, &s->allemb,
                     &s->dist, &s->vstart, &s->vlen};
   for (DevBuf *b : bufs) release(ctx, *b);

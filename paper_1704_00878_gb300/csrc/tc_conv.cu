@@ -298,7 +298,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
       tc_fence_after();
       const int r = tile * TBM + q * 32 + lane;
       const bool inb = r < T;
-      const bool valid = inb && rowseq[r] >= 0;
+      const bool valid = inb && (rowseq == nullptr || rowseq[r] >= 0);
       // the row slice into registers, then the accumulator goes back to the
       // issuer before any store
       float v[TBN / 32][32];
@@ -601,7 +601,7 @@ k_conv_tc2(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUt
       tc_fence_after();
       const int r = tile * PAIR_TBM + (int)rank * TBM + q * 32 + lane;
       const bool inb = r < T;
-      const bool valid = inb && rowseq[r] >= 0;
+      const bool valid = inb && (rowseq == nullptr || rowseq[r] >= 0);
       // this warp's slice into registers (one load, one wait), then the
       // accumulator goes back to the issuer before any store
       float v[HC];
