@@ -88,3 +88,22 @@ def test_flatten_roundtrip_and_center_rule():
     emb = np.array([[0.0, 0.0], [1.0, 0.0], [-1.0, 0.0], [0.0, 3.0]])
     assert net.center_of(emb) == 0
     assert np.allclose(net.distance_targets([5, 0], [10, 4], [10, 6], 0.01), [0.1, 0.1])
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 9, 40])
+def test_pooled_output_layer_on_window_sums(L):
+    """The GPU embedding runs the output layer on nine window sums per
+    sequence: P_0 = sum of padded rows 0 .. L-1 (row i = a3[i - 4], zero
+    outside), P_{t+1} = P_t - row t + row L + t, and
+    sum_r y4[r] = sum_t P_t W4_t + L b4.  Checked against the oracle's
+    convolution followed by the sum over positions, down to one residue."""
+    rng = np.random.default_rng(L)
+    a3 = np.maximum(rng.normal(size=(L, net.WIDTH)), 0)
+    W = rng.normal(size=(net.TAPS, net.WIDTH, net.DIM))
+    b = rng.normal(size=net.DIM)
+    pad = np.vstack([np.zeros((net.HALF, net.WIDTH)), a3, np.zeros((net.HALF, net.WIDTH))])
+    P = [pad[0:L].sum(axis=0)]
+    for t in range(net.TAPS - 1):
+        P.append(P[-1] - pad[t] + pad[L + t])
+    window = sum(P[t] @ W[t] for t in range(net.TAPS)) + L * b
+    assert np.allclose(window, net.conv9(a3, W, b).sum(axis=0), rtol=1e-12, atol=1e-9)
