@@ -220,7 +220,7 @@ def workload_text(w, n, center, length=None):
 def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp, refs):
     """Train the selector on exact-kernel distances (untimed), then time the
     whole step with the learned center (network embedding + exact row sums of
-    its 128 best candidates, over every sequence when the exact center is the
+    its best candidates, over every sequence when the exact center is the
     all-pairs one, else over the same reference sample) against the exact
     center's step."""
     import torch
@@ -231,9 +231,15 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
     losses = b.msa_selector_train(h, pairs, steps=6000, batch_pairs=256, lr=3e-4, seed=3)
     train_s = time.perf_counter() - t0
 
+    # candidates checked exactly: as many as ~2e10 DP cells of row sums
+    # allow (short sequences: more of them), at least 128, at most 4096
+    lens = np.diff(offsets).astype(np.float64)
+    nj = n if refs is None else len(refs)
+    cand = int(np.clip(2e10 / (nj * float(lens.mean()) ** 2), 128, 4096))
+
     def step_learned():
         b.msa_load(h, dlet, offsets)
-        c, _ = b.msa_select_center_refined(h, candidates=128, refs=refs)
+        c, _ = b.msa_select_center_refined(h, candidates=cand, refs=refs)
         b.msa_align_to_center(h, c)
         b.msa_merge_gaps(h, want_rows=False)
         return c, b.msa_sp_score(h)
@@ -260,7 +266,7 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
             "train": {"pairs": int(pairs.shape[0]), "steps": 6000, "batch_pairs": 256,
                       "seconds": train_s, "loss_first": float(losses[:10].mean()),
                       "loss_last": float(losses[-50:].mean())},
-            "candidates_refined_exactly": 128,
+            "candidates_refined_exactly": min(cand, n),
             "refined_over": "every sequence" if refs is None else "the %d references" % len(refs),
             "stages_ms": {k: round(stages[k], 3) for k in
                           ("encode", "selector", "center", "align_dp", "traceback", "merge", "sp")}}

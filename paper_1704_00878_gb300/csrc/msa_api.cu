@@ -108,13 +108,16 @@ int run_pairs(msa_ctx *ctx, const std::vector<int2> &pairs_in, const std::vector
   std::vector<int32_t> order(np);
   std::iota(order.begin(), order.end(), 0);
   const int short_rows = pairs_rows(8);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+  auto before = [&](int x, int y) {
     const int ax = ctx->len_sorted[pairs_in[x].x] > short_rows;
     const int ay = ctx->len_sorted[pairs_in[y].x] > short_rows;
     if (ax != ay) return ax < ay;
     const int lx = ctx->len_sorted[pairs_in[x].y], ly = ctx->len_sorted[pairs_in[y].y];
     return lx < ly;
-  });
+  };
+  // (self pairs of the sorted set arrive in order already)
+  if (!std::is_sorted(order.begin(), order.end(), before))
+    std::stable_sort(order.begin(), order.end(), before);
   std::vector<int2> pr(np);
   std::vector<int32_t> dst(np);
   int n_short = 0;
@@ -808,10 +811,14 @@ int msa_load(msa_ctx *ctx, const uint8_t *letters, const int64_t *offsets, int64
   ctx->aligned = ctx->merged = ctx->have_rowsum = false;
   ctx->n = (int)n;
   ctx->maxlen = maxlen;
+  // stable sort by length: a counting sort (lengths are at most MSA_MAX_LEN)
   ctx->perm.resize(n);
-  std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
-  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
-                   [&](int32_t a, int32_t b) { return lens[a] < lens[b]; });
+  {
+    std::vector<int64_t> first(maxlen + 2, 0);
+    for (int64_t t = 0; t < n; ++t) ++first[lens[t] + 1];
+    for (int L = 1; L <= maxlen + 1; ++L) first[L] += first[L - 1];
+    for (int64_t t = 0; t < n; ++t) ctx->perm[first[lens[t]]++] = (int32_t)t;
+  }
   ctx->inv.resize(n);
   ctx->len_sorted.resize(n);
   ctx->pstart.resize(n);

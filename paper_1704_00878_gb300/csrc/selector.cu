@@ -349,11 +349,13 @@ int selector_center_refined(msa_ctx *ctx, int k, const std::vector<int32_t> &ref
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_SELECTOR);
   TRY(check_derr(ctx));
+  // the k smallest distances (a total order: ties by input index), as a set
   std::vector<int32_t> idx(n);
   std::iota(idx.begin(), idx.end(), 0);
-  std::partial_sort(idx.begin(), idx.begin() + k, idx.end(), [&](int32_t a, int32_t b) {
-    return dist[a] < dist[b] || (dist[a] == dist[b] && ctx->perm[a] < ctx->perm[b]);
-  });
+  if (k < n)
+    std::nth_element(idx.begin(), idx.begin() + (k - 1), idx.end(), [&](int32_t a, int32_t b) {
+      return dist[a] < dist[b] || (dist[a] == dist[b] && ctx->perm[a] < ctx->perm[b]);
+    });
   std::vector<int32_t> qs(idx.begin(), idx.begin() + k);
   std::sort(qs.begin(), qs.end());
   stage_begin(ctx, ST_CENTER);

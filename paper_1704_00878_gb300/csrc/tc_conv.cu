@@ -3,26 +3,28 @@
 // accumulators in tensor memory), every operand tile brought into shared
 // memory by TMA.
 //
-// Output tile: 128 positions (rows of the flat batch) x 64 output channels.
-// For tap t the A operand is rows r0 - 4 + t .. r0 + 123 + t of the input,
-// i.e. the same 136-row tile shifted by t rows, so a CTA loads the tile once
-// (TMA, 128-byte swizzle for 64 or 128 channels, 64-byte swizzle for 32;
-// rows outside the batch read as zeros) and points the MMA's shared-memory
-// descriptor t rows further for each tap.  The B operand (the 64 output
-// channels' weights of all 9 taps) stays resident in shared memory for the
-// CTA's whole life.  CTAs are persistent, each owns one 64-channel slice of
-// the output and walks the row tiles with three roles:
+// For tap t the A operand of an output tile starting at row r0 is rows
+// r0 - 4 + t .. of the input, i.e. the same tile plus an 8-row halo shifted
+// by t rows, so a CTA loads it once (TMA, 128-byte swizzle for 64 or 128
+// channels, 64-byte swizzle for 32; rows outside the batch read as zeros)
+// and points the MMA's shared-memory descriptor t rows further for each tap.
+// The B operand (output channels' weights of all 9 taps) stays resident in
+// shared memory for the CTA's whole life.  Warp roles:
 //   warp 0   TMA producer: input tiles into two buffers,
-//   warp 1   MMA issuer: 9 x (CIN / 16) MMAs (M 128, N 64, K 16) per tile
-//            into one of two accumulators in tensor memory, committed to
-//            mbarriers that free the input buffer and hand the accumulator
-//            to the epilogue,
-//   warps 2-5 epilogue: each reads the 32 accumulator rows its warp may
-//            address (tcgen05.ld 32x32b), adds the bias, applies the mode's
-//            activation or mask and stores bf16 / fp32 rows, then frees the
-//            accumulator,
+//   warp 1   MMA issuer: 9 x (CIN / 16) MMAs per tile into one of two
+//            accumulators in tensor memory, committed to mbarriers that free
+//            the input buffer and hand the accumulator to the epilogue,
+//   the rest epilogue: each warp reads the accumulator rows its warp may
+//            address (tcgen05.ld 32x32b), hands the accumulator back, adds
+//            the bias, applies the mode's activation or mask and stores
+//            bf16 / fp32 rows,
 // so the epilogue of tile i runs under the MMAs of tile i + 1 and the load
 // of tile i + 2.
+//
+// k_conv_tc2 (every convolution of the network) runs this on CTA pairs with
+// tcgen05.mma.cta_group::2 (M 256 per instruction, the weights split across
+// the pair); k_conv_tc, the single-CTA form (M 128 x N 64), remains for the
+// self-test of the bounded waits.  k_wgrad_tc computes the weight gradient.
 //
 // Every wait on an mbarrier gives up after a bounded number of polls, sets
 // bit MSA_DERR_TIMEOUT_TC of the caller's error word and ends the role;
@@ -52,11 +54,15 @@ template <int CIN> struct Geo {
   static constexpr int ROWB = CIN >= 64 ? 128 : 64;
   static constexpr int BLK = ROWB / 2;
   static constexpr int KB = CIN / BLK;
-  static constexpr int A_BLOCK = AROWS * ROWB;         // one block of the A tile
-  static constexpr int B_BLOCK = TBN * ROWB;           // one block of one tap's weights
-  static constexpr int W_BYTES = TAPS * KB * B_BLOCK;  // resident weights
+  static constexpr int A_BLOCK = AROWS * ROWB;  // one block of the A tile
   static constexpr int A_BYTES = (KB * A_BLOCK + 1023) / 1024 * 1024;
-  static constexpr int SMEM = W_BYTES + 2 * A_BYTES + 1024;  // + alignment slack
+};
+
+// the single-CTA kernel's weights: TBN output channels per CTA
+template <int CIN> struct SoloGeo : Geo<CIN> {
+  static constexpr int B_BLOCK = TBN * Geo<CIN>::ROWB;               // one block of one tap's weights
+  static constexpr int W_BYTES = TAPS * Geo<CIN>::KB * B_BLOCK;      // resident weights
+  static constexpr int SMEM = W_BYTES + 2 * Geo<CIN>::A_BYTES + 1024;  // + alignment slack
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -191,7 +197,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUte
           const float *__restrict__ bias, const int32_t *__restrict__ rowseq,
           const bf16 *__restrict__ prev, void *__restrict__ y, int T, unsigned *err,
           long long spins, int no_loads) {
-  using Gm = Geo<CIN>;
+  using Gm = SoloGeo<CIN>;
   constexpr int NH = COUT / TBN;  // output-channel slices
   extern __shared__ unsigned char tc_raw[];
   __shared__ __align__(8) unsigned long long bars[NBARS];
@@ -877,7 +883,7 @@ template <int CIN, int COUT, int MODE>
 cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, const int32_t *rowseq,
                       const bf16 *prev, void *y, int T, unsigned *err, cudaStream_t st,
                       long long spins, int no_loads) {
-  using Gm = Geo<CIN>;
+  using Gm = SoloGeo<CIN>;
   CUtensorMap xm, wm;
   if (!make_map(&xm, x, (uint64_t)T, CIN, AROWS, Gm::BLK) ||
       !make_map(&wm, w, (uint64_t)TAPS * COUT, CIN, TBN, Gm::BLK))
@@ -983,15 +989,9 @@ cudaError_t conv_tc(int cin, int cout, int mode, const bf16 *x, const bf16 *w, c
 #undef NET_TC2
     return cudaErrorInvalidValue;
   }
-#define NET_TC(CI, CO, MD) \
-  if (cin == CI && cout == CO && mode == MD) \
-    return launch_tc<CI, CO, MD>(x, w, bias, rowseq, prev, y, T, err, st, spins, nl);
-  NET_TC(128, 128, 0)
-  NET_TC(128, 128, 2)
-  NET_TC(128, 64, 1)
-  NET_TC(64, 128, 2)
-  NET_TC(32, 128, 0)
-#undef NET_TC
+  // the load-free self-test: the single-CTA kernel, 128 -> 128 channels
+  if (cin == 128 && cout == 128 && mode == 0)
+    return launch_tc<128, 128, 0>(x, w, bias, rowseq, prev, y, T, err, st, spins, nl);
   return cudaErrorInvalidValue;
 }
 
