@@ -212,7 +212,9 @@ int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out);
  * 128 channels + ReLU -> two 9-tap 128->128 convs + ReLU -> 9-tap 128->64
  * conv -> sum over the sequence's L positions divided by sqrt(L) (so that
  * ||e||^2 can grow with length like S(A,A)).  Compute in bf16 on the
- * tensor cores with fp32 accumulation; fp32 master weights; Adam.
+ * tensor cores with fp32 accumulation (the linear last layer is applied to
+ * nine window sums of the third layer per sequence, which the sum over
+ * positions allows); fp32 master weights; Adam.
  * Parameters (fp32, flat, in this order): W1 [9][32][128], b1 [128],
  * W2 [9][128][128], b2 [128], W3 [9][128][128], b3 [128], W4 [9][128][64],
  * b4 [64]; W[tap][in][out] multiplies the input row at offset tap-4. */
