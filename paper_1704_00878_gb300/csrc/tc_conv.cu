@@ -915,7 +915,12 @@ cudaError_t launch_tc2(const bf16 *x, const bf16 *w, const float *bias, const in
   auto fn = k_conv_tc2<CIN, COUT, MODE>;
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  static int mp = 0;  // resident pairs of this instantiation (one device per process)
+  // resident pairs of this instantiation per device (only the grid size
+  // depends on it; devices past 63 share the last slot)
+  static int mp_dev[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int &mp = mp_dev[std::min(std::max(dev, 0), 63)];
   if (mp == 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * (unsigned)std::max(1, sm_count() / 2));
