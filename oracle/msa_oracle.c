@@ -26,8 +26,13 @@
  *     left-aligned without gaps; excess sequence residues go to insertion slot 0
  *     (prefix) or slot Lc (suffix), excess center residues face a gap;
  *   - inserted residues are left-justified in their slot, gaps follow;
- *   - distance d(A,B) = S(A,A) + S(B,B) - 2 S(A,B); center = argmin of the row
- *     sums, lowest index on ties.
+ *   - center (Figure 3: "extracted ... based on Smith-Waterman"; the trie
+ *     paragraph: the sequence "most similar to other sequences"): similarity of
+ *     a pair = its local score as a fraction of the larger self score,
+ *     S(A,B) / max(S(A,A), S(B,B)), held in 16-bit fixed point; distance
+ *     d(A,B) = 2^16 - floor(2^16 S(A,B) / max(S(A,A), S(B,B))), and d = 0 when
+ *     both self scores are 0; center = argmin of the row sums of d, lowest
+ *     index on ties.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -348,9 +353,25 @@ int64_t orc_sp_columns(const uint8_t *msa, int64_t n, int64_t width)
 }
 
 /*
- * Exact center star (reading of "extracted ... based on Smith-Waterman"):
- * d(A,B) = S(A,A) + S(B,B) - 2 S(A,B); rowsum[i] = sum_{r in refs} d(i, r)
- * where refs is every sequence (nref == n, refs == NULL) or a given subset.
+ * Distance of a pair for the exact center, in units of 2^-16:
+ *   d(A,B) = 2^16 - floor(2^16 * S(A,B) / m),  m = max(S(A,A), S(B,B)),
+ * i.e. one minus the fraction of the larger self score that the pair's local
+ * alignment reaches (0 for identical sequences, 2^16 for a pair with no
+ * positive local alignment).  d = 0 when m == 0.  S(A,B) >= 0, so the integer
+ * division is the floor.
+ */
+#define ORC_ONE ((int64_t)1 << 16)
+
+static int64_t orc_distance(int32_t sab, int32_t saa, int32_t sbb)
+{
+    int64_t m = saa > sbb ? saa : sbb;
+    if (m <= 0) return 0;
+    return ORC_ONE - ((int64_t)sab * ORC_ONE) / m;
+}
+
+/*
+ * Exact center star: rowsum[i] = sum_{r in refs} d(i, r) where refs is every
+ * sequence (nref == n, refs == NULL) or a given subset; d(i, i) = 0.
  * Returns the lowest index with the smallest row sum (-1 on error).
  */
 int64_t orc_exact_center(const uint8_t *res, const int64_t *off, int64_t n,
@@ -381,7 +402,7 @@ int64_t orc_exact_center(const uint8_t *res, const int64_t *off, int64_t n,
         int64_t sum = 0;
         for (int64_t r = 0; r < nr; r++) {
             int64_t ri = refs ? refs[r] : r;
-            sum += (int64_t)self[i] + self[ri] - 2 * (int64_t)S[i * nr + r];
+            sum += orc_distance(S[i * nr + r], self[i], self[ri]);
         }
         if (rowsum) rowsum[i] = sum;
         if (bestc < 0 || sum < bests) { bestc = i; bests = sum; }

@@ -20,8 +20,18 @@ MUTATIONS = {
     "suffix_short_by_one": ("for (int32_t t = 1; t <= k; t++) occ[i2 + t] = 1;",
                             "for (int32_t t = 1; t < k; t++) occ[i2 + t] = 1;"),
     "gap_cost_halved": ("+ 2 * g * r;", "+ g * r;"),
-    "distance_drops_term": ("sum += (int64_t)self[i] + self[ri] - 2",
-                            "sum += (int64_t)self[i] - 2"),
+    "distance_smaller_self": ("int64_t m = saa > sbb ? saa : sbb;",
+                              "int64_t m = saa < sbb ? saa : sbb;"),
+    "distance_rounds_up": ("return ORC_ONE - ((int64_t)sab * ORC_ONE) / m;",
+                           "return ORC_ONE - ((int64_t)sab * ORC_ONE + m - 1) / m;"),
+    "distance_zero_self_far": ("if (m <= 0) return 0;", "if (m <= 0) return ORC_ONE;"),
+    "distance_unnormalised": ("sum += orc_distance(S[i * nr + r], self[i], self[ri]);",
+                              "sum += (int64_t)self[i] + self[ri] - 2 * (int64_t)S[i * nr + r];"),
+    "right_justified": (
+        "            for (int32_t u = 0; u < in[j]; u++) row[pos++] = (uint8_t)letters[s[k++]];\n"
+        "            for (int32_t u = in[j]; u < G[j]; u++) row[pos++] = '-';\n",
+        "            for (int32_t u = in[j]; u < G[j]; u++) row[pos++] = '-';\n"
+        "            for (int32_t u = 0; u < in[j]; u++) row[pos++] = (uint8_t)letters[s[k++]];\n"),
     "F_dropped_from_H": ("max2(max2(0, dv), max2(ev, fv));", "max2(max2(0, dv), ev);"),
 }
 

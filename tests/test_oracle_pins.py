@@ -239,6 +239,37 @@ def test_merge_invariants():
                                      prob.M, prob.o, prob.e) == seg[t, 0]
 
 
+def _msa_golden():
+    out = []
+    for ln in open(os.path.join(GOLDEN, "msa_cases.txt")):
+        ln = ln.strip()
+        if not ln or ln.startswith("#"):
+            continue
+        f = [x.strip() for x in ln.split("|")]
+        rows = []
+        for ent in f[2].split(";"):
+            seq, ins, occ = [x.strip() for x in ent.split("/")]
+            rows.append((seq, [int(v) for v in ins.split()], [int(v) for v in occ.split()]))
+        out.append(dict(name=f[0], center=f[1], rows=rows, G=[int(v) for v in f[3].split()],
+                        W=int(f[4]), msa=f[5].split()))
+    return out
+
+
+@pytest.mark.parametrize("case", _msa_golden(), ids=lambda c: c["name"])
+def test_hand_written_merge(case):
+    """Inserted residues are left-justified in their slot (gaps after them)."""
+    alphabet, M = dna_matrix(2, -3)
+    seqs = [r[0].encode() for r in case["rows"]]
+    assert seqs[0] == case["center"].encode()
+    offsets = np.concatenate([[0], np.cumsum([len(x) for x in seqs])])
+    prob = oracle.Problem(np.frombuffer(b"".join(seqs), np.uint8), offsets, alphabet, M, 5, 2)
+    ins = np.array([r[1] for r in case["rows"]], dtype=np.uint16)
+    occ = np.array([r[2] for r in case["rows"]], dtype=np.uint8)
+    G, W, msa = oracle.merge(prob, 0, ins, occ)
+    assert list(G) == case["G"] and W == case["W"]
+    assert [bytes(r).decode() for r in msa] == case["msa"]
+
+
 def test_sp_columns_equal_pairwise():
     prob, _, _ = _small_problem(n=20)
     *_, msa = oracle.msa(prob, 3)
@@ -250,6 +281,19 @@ def test_sp_columns_equal_pairwise():
 
 # ----------------------------------------------------------- exact center
 
+ONE = 1 << 16
+
+
+def _distance_matrix(S):
+    """d(A,B) = 2^16 - floor(2^16 S(A,B) / max(S(A,A), S(B,B))), 0 when that max is 0."""
+    S = np.asarray(S, dtype=np.int64)
+    m = np.maximum(np.diag(S)[:, None], np.diag(S)[None, :])
+    d = np.zeros_like(S)
+    pos = m > 0
+    d[pos] = ONE - (S[pos] * ONE) // m[pos]
+    return d
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_exact_center_equals_brute_force(seed):
     rng = np.random.default_rng(5000 + seed)
@@ -259,7 +303,7 @@ def test_exact_center_equals_brute_force(seed):
     o, e = rand_gaps(rng)
     seqs = [rng.integers(0, K, int(rng.integers(1, 5))) for _ in range(9)]
     S = np.array([[_pins.brute_local(list(a), list(b), M, o, e)[0] for b in seqs] for a in seqs])
-    d = np.diag(S)[:, None] + np.diag(S)[None, :] - 2 * S
+    d = _distance_matrix(S)
     rowsum = d.sum(axis=1)
     letters = "".join("ABC"[x] for s in seqs for x in s).encode()
     offsets = np.concatenate([[0], np.cumsum([len(s) for s in seqs])])
@@ -274,10 +318,107 @@ def test_exact_center_equals_brute_force(seed):
     assert (rs2 == exp2).all() and c2 == int(np.argmin(exp2))
 
 
+def _center_golden():
+    out = []
+    for ln in open(os.path.join(GOLDEN, "center_cases.txt")):
+        ln = ln.strip()
+        if not ln or ln.startswith("#"):
+            continue
+        f = [x.strip() for x in ln.split("|")]
+        ints = lambda x: [int(v) for v in x.split()]
+        out.append(dict(name=f[0], matrix=f[1], o=int(f[2]), e=int(f[3]), seqs=f[4].split(),
+                        self=ints(f[5]), S=ints(f[6]), d=ints(f[7]), rowsum=ints(f[8]),
+                        center=int(f[9])))
+    return out
+
+
+def _center_matrix(spec):
+    M = np.full((2, 2), -1, np.int8)
+    M[0, 0] = 2
+    M[1, 1] = 2 if spec == "ab" else 0
+    return "AB", M
+
+
+@pytest.mark.parametrize("case", _center_golden(), ids=lambda c: c["name"])
+def test_hand_worked_center(case):
+    alphabet, M = _center_matrix(case["matrix"])
+    seqs = [s.encode() for s in case["seqs"]]
+    offsets = np.concatenate([[0], np.cumsum([len(s) for s in seqs])])
+    prob = oracle.Problem(np.frombuffer(b"".join(seqs), np.uint8), offsets, alphabet, M,
+                          case["o"], case["e"])
+    n = prob.n
+    iu = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    assert list(oracle.pair_scores(prob, [(i, i) for i in range(n)])) == case["self"]
+    assert list(oracle.pair_scores(prob, iu)) == case["S"]
+    # d of each pair: the row sum over a single reference
+    for (i, j), dv in zip(iu, case["d"]):
+        _, rs = oracle.exact_center(prob, refs=np.array([j]))
+        assert rs[i] == dv
+        _, rs = oracle.exact_center(prob, refs=np.array([i]))
+        assert rs[j] == dv
+    c, rs = oracle.exact_center(prob)
+    assert list(rs) == case["rowsum"]
+    assert c == case["center"]
+
+
 def test_distance_properties_on_protein_set():
     prob, _, _ = _small_problem(n=12)
     pairs = np.array([(i, j) for i in range(prob.n) for j in range(prob.n)])
     S = oracle.pair_scores(prob, pairs).reshape(prob.n, prob.n)
     assert (S == S.T).all()
-    d = np.diag(S)[:, None] + np.diag(S)[None, :] - 2 * S.astype(np.int64)
-    assert (np.diag(d) == 0).all() and (d >= 0).all()
+    d = _distance_matrix(S)
+    # zero on the diagonal, symmetric, and in [0, 2^16] under BLOSUM62's
+    # dominance s(a,b) <= (s(a,a) + s(b,b)) / 2 (a local score never exceeds
+    # the larger self score)
+    assert (np.diag(d) == 0).all() and (d == d.T).all()
+    assert (d >= 0).all() and (d <= ONE).all()
+    _, rs = oracle.exact_center(prob)
+    assert (rs == d.sum(axis=1)).all()
+
+
+def _workload_subset(name, m, seed, keep_first=False):
+    letters, offsets, w, _ = generate(name, n=min(w_n(name), 4000))
+    rng = np.random.default_rng(seed)
+    n = offsets.size - 1
+    idx = np.sort(rng.choice(n, size=m, replace=False))
+    if keep_first:
+        idx = np.unique(np.concatenate([[0], idx[1:]]))
+    seqs = [letters[offsets[i]:offsets[i + 1]] for i in idx]
+    alph, M = (blosum62() if w.kind == "protein" else dna_matrix(2, -3))
+    offs = np.concatenate([[0], np.cumsum([len(s) for s in seqs])])
+    return oracle.Problem(np.concatenate(seqs), offs, alph, M, w.gap_open, w.gap_extend)
+
+
+def w_n(name):
+    from seqgen import WORKLOADS
+    return WORKLOADS[name].n
+
+
+@pytest.mark.parametrize("name", ["batched_uneven_10k", "learned_center_50k"])
+def test_exact_center_is_not_a_length_proxy(name):
+    """On 200-sequence samples of the uneven multi-family protein sets the
+    center is neither the shortest nor the longest sequence (the row sums of
+    S(A,A) + S(B,B) - 2 S(A,B) rank sequences by length: correlation 1.00
+    and the shortest sequence as center on these samples)."""
+    prob = _workload_subset(name, 200, 3)
+    lens = np.diff(prob.off)
+    c, rs = oracle.exact_center(prob)
+    corr = float(np.corrcoef(rs, lens)[0, 1])
+    print(f"{name}: center length {lens[c]}, length range {lens.min()}-{lens.max()}, "
+          f"corr(row sum, length) {corr:+.3f}")
+    lo, hi = np.percentile(lens, [10, 90])
+    assert lo <= lens[c] <= hi
+    assert abs(corr) < 0.99
+
+
+def test_exact_center_ranks_the_common_ancestor_first():
+    """Short peptides cut (and mutated) from one 500-residue ancestor, with the
+    ancestor itself in the set: the ancestor's local alignments reach a large
+    fraction of every peptide's self score, so its row sum is among the
+    smallest 2 % (the shortest peptide's is not)."""
+    prob = _workload_subset("short_peptides_1m", 200, 1, keep_first=True)
+    c, rs = oracle.exact_center(prob)
+    lens = np.diff(prob.off)
+    assert lens[0] == 500
+    assert int((rs < rs[0]).sum()) <= 0.02 * prob.n
+    assert int((rs < rs[int(np.argmin(lens))]).sum()) > 0.5 * prob.n
