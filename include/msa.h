@@ -90,35 +90,46 @@ int msa_pair_scores(msa_ctx *ctx, const int64_t *pairs, int64_t npairs, int32_t 
 
 /* Allocation-free variant of msa_pair_scores.  The paper has no counterpart;
  * this entry point exists for callers that must not allocate device memory:
- * code that runs while a CUDA graph is being captured, processes whose device
- * memory belongs to another allocator, or services that forbid driver
- * allocations once they are running.  It needs no context and calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * plug-ins hosted by an application whose allocator owns all of the GPU's
+ * memory, processes whose device memory is handed out by another framework's
+ * pool, or services that forbid driver allocations once they are running.
+ * It needs no context and calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *   residues: device uint8, alphabet indices 0..alphabet-1 (already encoded);
- *     sequence i is residues[offsets[i] .. offsets[i+1]).
+ *     sequence i is residues[offsets[i] .. offsets[i+1]), which must lie
+ *     inside the buffer.
  *   offsets: device int64[n+1].  pairs: device int64[npairs][2] (row
  *     sequence, column sequence).  scores_out: device int32[npairs].
  *   max_len: the longest sequence any listed pair touches, 1..MSA_MAX_LEN;
- *     a pair touching a longer sequence (or an index outside 0..n-1) gets
- *     score -1 and the call returns MSA_ERANGE.
+ *     a pair touching a longer or empty sequence (or an index outside 0..n-1)
+ *     gets score -1 and the call returns MSA_ERANGE.
+ *   A pair one of whose sequences holds a residue code >= alphabet gets
+ *     score -1 and the call returns MSA_EINVAL (the codes are checked on the
+ *     GPU before any is used).
  *   matrix: host alphabet x alphabet scores, gap_open/gap_extend as in
  *     msa_params; cuda_stream: where the work runs (NULL = legacy stream).
- * Working memory is one fixed 32 MiB array per device, held by every GPU that
+ * Working memory is one fixed array per device (32 MiB of boundary rows plus
+ * 256 bytes for a work counter and an error word), held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * looks up that array's device address (with the device current); make that
  * first call before any stream capture begins.  All calls on a device share
- * the array and each call clears its counter, so calls that overlap on the
- * GPU race: run them one after another.  Long sequences shrink the number of
- * thread blocks that fit the array (32 at max_len = MSA_MAX_LEN).  Returns
- * after the stream has finished the call. */
+ * the array and each call clears its counter and error word, so calls that
+ * overlap on the GPU race: run them one after another.  Long sequences
+ * shrink the number of thread blocks that fit the array (32 at max_len =
+ * MSA_MAX_LEN).  Before returning, the call copies the error word to the host
+ * and waits for cuda_stream to finish. */
 int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *offsets, int64_t n,
                             const int64_t *pairs, int64_t npairs, int32_t max_len,
                             const int8_t *matrix, int32_t alphabet, int32_t gap_open,
                             int32_t gap_extend, int32_t *scores_out, void *cuda_stream);
 
 /* Choose the center star sequence (Figure 3's first MapReduce step).
- * EXACT: center = argmin_i sum_j d(i,j), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B)
- *   over all j (lowest index on ties).
+ * EXACT: center = argmin_i sum_j d(i,j) over all j (lowest index on ties),
+ *   the sequence most similar to the others: the similarity of a pair is its
+ *   local score as a fraction of the larger self score, in 16-bit fixed point,
+ *   d(A,B) = 2^16 - floor(2^16 S(A,B) / max(S(A,A), S(B,B))) (d = 0 when both
+ *   self scores are 0; d(A,A) = 0).  Self scores are computed first, then the
+ *   pairs.
  * EXACT_SAMPLED: the same sum over j in refs (host int64[nref], distinct).
  * LEARNED: argmin_i ||e_i - mean(e)||^2 over the selector's embeddings
  *   (msa_selector_*); ESTATE if no parameters are set.
@@ -203,15 +214,15 @@ int msa_sp_score(msa_ctx *ctx, int64_t *sp_cost_out);
 /* Learned center selector.  The paper selects the center with Smith-
  * Waterman scores over all pairs (O(n^2) alignments); the selector is a 1-D
  * convolutional embedding network whose squared embedding distances are
- * trained to follow the scaled exact distance
- *   t(A,B) = scale * d(A,B),  d(A,B) = S(A,A) + S(B,B) - 2 S(A,B),
+ * trained to follow the scaled exact-center distance
+ *   t(A,B) = scale * d(A,B),  d(A,B) = 2^16 - floor(2^16 S(A,B) / max(S(A,A), S(B,B))),
  * so that the center can be picked in O(n): argmin_i ||e_i - mean(e)||^2,
  * which equals argmin_i sum_j ||e_i - e_j||^2, the embedding stand-in for the
  * exact center's argmin_i sum_j d(i,j).
  * Architecture (fixed): one-hot residues over 32 channels -> 9-tap conv to
  * 128 channels + ReLU -> two 9-tap 128->128 convs + ReLU -> 9-tap 128->64
- * conv -> sum over the sequence's L positions divided by sqrt(L) (so that
- * ||e||^2 can grow with length like S(A,A)).  Compute in bf16 on the
+ * conv -> sum over the sequence's L positions divided by sqrt(L) (a mean
+ * would make the embedding nearly blind to the length).  Compute in bf16 on the
  * tensor cores with fp32 accumulation (the linear last layer is applied to
  * nine window sums of the third layer per sequence, which the sum over
  * positions allows); fp32 master weights; Adam.

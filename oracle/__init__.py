@@ -56,6 +56,9 @@ def lib():
         L.orc_sp_pairwise.argtypes = [P, i64, i64]
         L.orc_sp_columns.restype = i64
         L.orc_sp_columns.argtypes = [P, i64, i64]
+        L.orc_center_rowsums.restype = ctypes.c_int
+        L.orc_center_rowsums.argtypes = [P, P, i64, P, i64, P, i64, P, i32, i32, i32, P,
+                                         ctypes.c_int]
         L.orc_exact_center.restype = i64
         L.orc_exact_center.argtypes = [P, P, i64, P, i64, P, i32, i32, i32, P, ctypes.c_int]
         L.orc_default_threads.restype = ctypes.c_int
@@ -203,6 +206,23 @@ def exact_center(prob, refs=None, threads=0):
     if c < 0:
         raise MemoryError("oracle exact center")
     return int(c), rowsum
+
+
+def center_rowsums(prob, cands, refs=None, threads=0):
+    """Row sums sum_{r in refs} d(c, r) of the listed candidates (refs=None:
+    every sequence), int64[len(cands)]."""
+    cands = np.ascontiguousarray(cands, dtype=np.int64)
+    out = np.zeros(cands.size, dtype=np.int64)
+    if refs is None:
+        rp, nr = None, prob.n
+    else:
+        refs = np.ascontiguousarray(refs, dtype=np.int64)
+        rp, nr = _p(refs), refs.size
+    rc = lib().orc_center_rowsums(_p(prob.res), _p(prob.off), prob.n, _p(cands), cands.size,
+                                  rp, nr, _p(prob.M), prob.K, prob.o, prob.e, _p(out), threads)
+    if rc != 0:
+        raise MemoryError("oracle center row sums")
+    return out
 
 
 def msa(prob, center, threads=0):

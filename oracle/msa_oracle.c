@@ -370,43 +370,65 @@ static int64_t orc_distance(int32_t sab, int32_t saa, int32_t sbb)
 }
 
 /*
- * Exact center star: rowsum[i] = sum_{r in refs} d(i, r) where refs is every
- * sequence (nref == n, refs == NULL) or a given subset; d(i, i) = 0.
- * Returns the lowest index with the smallest row sum (-1 on error).
+ * Row sums of the exact center: rowsum[x] = sum_{r in refs} d(c_x, r) for
+ * the listed candidates c_x (cands == NULL: every sequence, ncand == n),
+ * where refs is every sequence (refs == NULL) or a given subset; d(i, i) = 0.
+ * Returns 0, or -1 on error.
+ */
+int orc_center_rowsums(const uint8_t *res, const int64_t *off, int64_t n,
+                       const int64_t *cands, int64_t ncand,
+                       const int64_t *refs, int64_t nref,
+                       const int8_t *M, int32_t K, int32_t o, int32_t e,
+                       int64_t *rowsum, int threads)
+{
+    int64_t nc = cands ? ncand : n;
+    int64_t nr = refs ? nref : n;
+    int64_t np = nc * nr + n;
+    int64_t *pairs = malloc(sizeof(int64_t) * 2 * np);
+    int32_t *S = malloc(sizeof(int32_t) * np);
+    if (!pairs || !S) { free(pairs); free(S); return -1; }
+    for (int64_t x = 0; x < nc; x++)
+        for (int64_t r = 0; r < nr; r++) {
+            pairs[2 * (x * nr + r)] = cands ? cands[x] : x;
+            pairs[2 * (x * nr + r) + 1] = refs ? refs[r] : r;
+        }
+    for (int64_t i = 0; i < n; i++) {          /* self scores S(i,i) */
+        pairs[2 * (nc * nr + i)] = i;
+        pairs[2 * (nc * nr + i) + 1] = i;
+    }
+    if (orc_pair_scores(res, off, pairs, np, M, K, o, e, S, threads) != 0) {
+        free(pairs); free(S); return -1;
+    }
+    const int32_t *self = S + nc * nr;
+    for (int64_t x = 0; x < nc; x++) {
+        int64_t i = cands ? cands[x] : x, sum = 0;
+        for (int64_t r = 0; r < nr; r++) {
+            int64_t ri = refs ? refs[r] : r;
+            sum += orc_distance(S[x * nr + r], self[i], self[ri]);
+        }
+        rowsum[x] = sum;
+    }
+    free(pairs); free(S);
+    return 0;
+}
+
+/*
+ * Exact center star: the row sums of every sequence (as orc_center_rowsums)
+ * and the lowest index with the smallest one (-1 on error).
  */
 int64_t orc_exact_center(const uint8_t *res, const int64_t *off, int64_t n,
                          const int64_t *refs, int64_t nref,
                          const int8_t *M, int32_t K, int32_t o, int32_t e,
                          int64_t *rowsum, int threads)
 {
-    int64_t nr = refs ? nref : n;
-    int64_t np = n * nr + n;
-    int64_t *pairs = malloc(sizeof(int64_t) * 2 * np);
-    int32_t *S = malloc(sizeof(int32_t) * np);
-    if (!pairs || !S) { free(pairs); free(S); return -1; }
-    for (int64_t i = 0; i < n; i++)
-        for (int64_t r = 0; r < nr; r++) {
-            pairs[2 * (i * nr + r)] = i;
-            pairs[2 * (i * nr + r) + 1] = refs ? refs[r] : r;
-        }
-    for (int64_t i = 0; i < n; i++) {          /* self scores S(i,i) */
-        pairs[2 * (n * nr + i)] = i;
-        pairs[2 * (n * nr + i) + 1] = i;
+    int64_t *rs = rowsum ? rowsum : malloc(sizeof(int64_t) * n);
+    if (!rs) return -1;
+    int64_t bestc = -1;
+    if (orc_center_rowsums(res, off, n, NULL, n, refs, nref, M, K, o, e, rs, threads) == 0) {
+        bestc = 0;
+        for (int64_t i = 1; i < n; i++)
+            if (rs[i] < rs[bestc]) bestc = i;
     }
-    if (orc_pair_scores(res, off, pairs, np, M, K, o, e, S, threads) != 0) {
-        free(pairs); free(S); return -1;
-    }
-    const int32_t *self = S + n * nr;
-    int64_t bestc = -1, bests = 0;
-    for (int64_t i = 0; i < n; i++) {
-        int64_t sum = 0;
-        for (int64_t r = 0; r < nr; r++) {
-            int64_t ri = refs ? refs[r] : r;
-            sum += orc_distance(S[i * nr + r], self[i], self[ri]);
-        }
-        if (rowsum) rowsum[i] = sum;
-        if (bestc < 0 || sum < bests) { bestc = i; bests = sum; }
-    }
-    free(pairs); free(S);
+    if (!rowsum) free(rs);
     return bestc;
 }

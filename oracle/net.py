@@ -7,7 +7,8 @@ path.
 The paper selects the center with Smith-Waterman scores; the learned selector
 replaces that O(n^2) pass with an embedding network whose squared distances
 are trained to follow the scaled alignment distance
-t(A,B) = scale * d(A,B), d(A,B) = S(A,A) + S(B,B) - 2 S(A,B),
+t(A,B) = scale * d(A,B), with d the exact center's distance,
+d(A,B) = 2^16 - floor(2^16 S(A,B) / max(S(A,A), S(B,B))),
 so that argmin_i sum_j ||e_i - e_j||^2 tracks the exact center's
 argmin_i sum_j d(i,j).
 Architecture (a reading; the paper has no network):
@@ -17,8 +18,8 @@ Architecture (a reading; the paper has no network):
   a3  = relu(conv9(a2, W3, b3))                             [L, 128]
   y4  = conv9(a3, W4, b4)                                   [L, 64]
   e   = (sum over the L positions of y4) / sqrt(L)          [64]
-(pooling by sqrt(L) keeps ||e||^2 growing with the length, as S(A,A) does;
-a mean would make the embedding nearly length-blind.)
+(the sum over positions is divided by sqrt(L), not by L: a mean makes the
+embedding nearly blind to the length, which the distance depends on.)
 conv9(x, W, b)[p] = b + sum_{k=0..8} xpad[p + k] @ W[k], xpad = x with four
 zero rows before and after (the sequence ends are zero-padded).
 Loss over a batch of pairs: mean over pairs of (||e_A - e_B||^2 - t)^2.
@@ -159,6 +160,9 @@ def center_of(emb):
 
 
 def distance_targets(S_ab, S_aa, S_bb, scale):
-    """scale * (S_aa + S_bb - 2 S_ab)."""
-    return scale * (np.asarray(S_aa, np.float64) + np.asarray(S_bb, np.float64)
-                    - 2.0 * np.asarray(S_ab, np.float64))
+    """scale * d(A,B), d = 2^16 - floor(2^16 S_ab / max(S_aa, S_bb)) (0 when
+    that max is 0): the exact center's distance of the pair."""
+    S_ab = np.asarray(S_ab, np.int64)
+    m = np.maximum(np.asarray(S_aa, np.int64), np.asarray(S_bb, np.int64))
+    d = np.where(m > 0, 65536 - (S_ab * 65536) // np.maximum(m, 1), 0)
+    return scale * d.astype(np.float64)

@@ -184,6 +184,21 @@ def msa_pair_scores_noalloc(residues, offsets, pairs, max_len, matrix, gap_open,
     memory: every array is a CUDA tensor the caller owns (residues uint8
     alphabet indices, offsets int64[n+1], pairs int64[npairs, 2], scores_out
     int32[npairs]); matrix is a host array.  Raises MSAError on failure."""
+    import torch
+    for name, t, dt in (("residues", residues, torch.uint8), ("offsets", offsets, torch.int64),
+                        ("pairs", pairs, torch.int64), ("scores_out", scores_out, torch.int32)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if t.dtype != dt:
+            raise TypeError("%s must be %s, got %s" % (name, dt, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape [npairs, 2]")
+    if offsets.dim() != 1 or offsets.numel() < 2:
+        raise ValueError("offsets must hold n + 1 >= 2 entries")
+    if scores_out.numel() < pairs.shape[0]:
+        raise ValueError("scores_out holds fewer entries than there are pairs")
     M = np.ascontiguousarray(matrix, dtype=np.int8)
     st = getattr(stream, "cuda_stream", stream)
     rc = lib().msa_pair_scores_noalloc(_ptr(residues), _ptr(offsets), offsets.numel() - 1,

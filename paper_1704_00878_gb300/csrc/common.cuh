@@ -79,6 +79,17 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int w) {
   return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
+// Similarity of a pair for the exact center (the center is the sequence most
+// similar to the others, Figure 3): the pair's local score S as a fraction of
+// the larger of the two self scores, in units of 2^-16, rounded down; 2^16
+// when both self scores are 0.  A row sum adds the distance 2^16 minus this.
+#define MSA_SIM_ONE (1ull << 16)
+__device__ __forceinline__ unsigned long long center_sim(int S, int sa, int sb) {
+  const int m = sa > sb ? sa : sb;
+  return m > 0 ? ((unsigned long long)(unsigned)S << 16) / (unsigned long long)(unsigned)m
+               : MSA_SIM_ONE;
+}
+
 // Device-side error word bits (ctx->d_err).
 #define MSA_DERR_LETTER   1u   // a letter outside the alphabet
 #define MSA_DERR_TRACE    2u   // inconsistent traceback codes

@@ -122,6 +122,7 @@ struct SetView {
   SeqSet ss;
   std::vector<int32_t> idx, len;
   int n_sub = 0;
+  const int32_t *self = nullptr;  // device: S(v, v) of every view entry
 };
 int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted,
                const SetView *view = nullptr);

@@ -290,7 +290,7 @@ ClassPlan plan_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
 }
 
 CenterJob class_job(msa_ctx *ctx, int mode, const ClassPlan &pl, int sub_off, int sub_n,
-                    unsigned long long *counter) {
+                    unsigned long long *counter, const int32_t *self) {
   CenterJob job;
   job.mode = mode;
   job.qlist = P<int32_t>(ctx->qlist);
@@ -304,7 +304,7 @@ CenterJob class_job(msa_ctx *ctx, int mode, const ClassPlan &pl, int sub_off, in
   job.npass = pl.npass;
   job.counter = counter;
   job.pairsum = P<unsigned long long>(ctx->pairsum);
-  job.self = P<int32_t>(ctx->self);
+  job.self = self;
   job.sat_thresh = sat_thresh(ctx);
   job.ovf = P<int2>(ctx->ovf);
   job.ovf_count = ctx->derr + 1;
@@ -350,7 +350,9 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
   const ClassPlan pl = plan_class(ctx, mode, nq_list, cc, qlen, sub_n, prefix_all, streams);
   TRY(stage_plans(ctx, {pl}, prefix_all, streams));
   CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->st));
-  const CenterJob job = class_job(ctx, mode, pl, sub_off, sub_n, P<unsigned long long>(ctx->counters));
+  // (the autotuner's sums are never read, so the self scores need not be current)
+  const CenterJob job = class_job(ctx, mode, pl, sub_off, sub_n, P<unsigned long long>(ctx->counters),
+                                  P<int32_t>(ctx->self));
   stage_begin(ctx, ST_CENTER_K);
   ++ctx->launches;
   CK(launch_center(cc.variant, seqset(ctx), scoring(ctx), job, pl.grid, ctx->st, true));
@@ -368,7 +370,7 @@ int launch_class(msa_ctx *ctx, int mode, int nq_list, const CenterClass &cc,
 // captured on the context's private capture stream and launched on its
 // stream (which may be the legacy default stream).
 int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, int sub_off,
-                 int sub_n, const SeqSet &ss) {
+                 int sub_n, const SeqSet &ss, const int32_t *self) {
   const Scoring sc = scoring(ctx);
   std::vector<int> top(kNumCenterVariants, 0);
   for (const ClassPlan &pl : plans) top[pl.cc.variant] = std::max(top[pl.cc.variant], pl.smem);
@@ -386,7 +388,7 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
                               (int64_t)ss.len, ss.n, (int64_t)sc.M, sc.K, sc.o, sc.e,
                               (int64_t)cnt, (int64_t)plans.size()};
   for (size_t c = 0; c < plans.size(); ++c) {
-    CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c);
+    CenterJob job = class_job(ctx, mode, plans[c], sub_off, sub_n, cnt + c, self);
     const size_t order = plans.size() - 1 - c;  // launch position
     if (order & 1) job.scratch += ctx->scratch_half;
     jobs.push_back(job);
@@ -447,6 +449,8 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
 int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, const SetView *view) {
   // qsorted: ascending sorted indices of the queries (modes 1, 2); mode 0 uses all.
   // With a view, indices are the view's and its first n_sub entries are the subjects.
+  // The self scores (ctx->self, or the view's) must be current: the kernels
+  // add center_sim of every pair, which needs both sequences' self scores.
   if (view && mode == 0) return fail(ctx, MSA_EINVAL, "all-pairs selection over a view");
   const std::vector<int32_t> &lens = view ? view->len : ctx->len_sorted;
   const int n = view ? view->n_sub : ctx->n;
@@ -562,13 +566,14 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
     plans.push_back(plan_class(ctx, mode, nq_list, cc, qlen, n, prefix_all, streams));
   }
   TRY(stage_plans(ctx, plans, prefix_all, streams));
-  TRY(launch_plans(ctx, mode, plans, 0, n, ss));
+  const int32_t *self = view ? view->self : P<int32_t>(ctx->self);
+  TRY(launch_plans(ctx, mode, plans, 0, n, ss, self));
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_CENTER_K);
   const float center_ms = ctx->stage_ms[ST_CENTER_K];
   int64_t cells = 0;
-  if (mode == 0) {
-    for (int x = 0; x < nq; ++x) cells += (int64_t)lens[x] * suffix[x];
+  if (mode == 0) {  // pairs q < s (the self scores are counted by their own pass)
+    for (int x = 0; x < nq; ++x) cells += (int64_t)lens[x] * suffix[x + 1];
   } else {
     for (int q : qsorted) cells += (int64_t)lens[q] * suffix[0];
   }
@@ -594,8 +599,8 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
     TRY(run_pairs(ctx, ov_set, dst, P<int32_t>(ctx->ovf_scores)));
     CK((++ctx->launches, launch_apply_overflow)(mode, P<int2>(ctx->ovf),
                                                 P<int32_t>(ctx->ovf_scores), cnt,
-                                                P<unsigned long long>(ctx->pairsum),
-                                                P<int32_t>(ctx->self), ctx->st));
+                                                P<unsigned long long>(ctx->pairsum), self,
+                                                ctx->st));
   }
   return MSA_OK;
 }
@@ -925,24 +930,24 @@ int msa_select_center(msa_ctx *ctx, int mode, const int64_t *refs, int64_t nref,
   if (mode == MSA_CENTER_EXACT_SAMPLED) TRY(reference_positions(ctx, refs, nref, qs));
   stage_begin(ctx, ST_CENTER);
   CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
-  CK(cudaMemsetAsync(ctx->self.p, 0, sizeof(int32_t) * n, ctx->st));
   CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
-  TRY(run_center(ctx, mode == MSA_CENTER_EXACT ? 0 : 1, qs));
-  if (mode == MSA_CENTER_EXACT_SAMPLED) {
-    // self scores of every sequence
+  // self scores of every sequence first: every pair's similarity needs both
+  {
     std::vector<int2> sp(n);
     std::vector<int32_t> dst(n);
     for (int k = 0; k < n; ++k) { sp[k] = make_int2(k, k); dst[k] = k; }
     TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
+  }
+  TRY(run_center(ctx, mode == MSA_CENTER_EXACT ? 0 : 1, qs));
+  {
     double sumsq = 0;
     for (int k = 0; k < n; ++k) sumsq += (double)ctx->len_sorted[k] * ctx->len_sorted[k];
     ctx->cells[0] += (int64_t)sumsq;
   }
-  CK((++ctx->launches, launch_center_finalize)(mode == MSA_CENTER_EXACT ? 0 : 1, n, (int)qs.size(), P<int32_t>(ctx->d_perm),
-                            P<int32_t>(ctx->self), P<unsigned long long>(ctx->pairsum),
-                            P<int32_t>(ctx->qlist), ctx->dsmall, P<long long>(ctx->rowsum),
-                            ctx->dsmall + 1, ctx->dsmall + 2, P<long long>(ctx->part_val),
-                            P<long long>(ctx->part_idx), ctx->st));
+  CK((++ctx->launches, launch_center_finalize)(mode == MSA_CENTER_EXACT ? 0 : 1, n, (int)qs.size(),
+                            P<int32_t>(ctx->d_perm), P<unsigned long long>(ctx->pairsum),
+                            P<long long>(ctx->rowsum), ctx->dsmall + 1, ctx->dsmall + 2,
+                            P<long long>(ctx->part_val), P<long long>(ctx->part_idx), ctx->st));
   stage_end(ctx, ST_CENTER);
   long long h[3];
   CK(cudaMemcpyAsync(h, ctx->dsmall, sizeof h, cudaMemcpyDeviceToHost, ctx->st));

@@ -237,34 +237,20 @@ __global__ void k_sp_cost(const int32_t *__restrict__ counts, int n, int64_t W, 
 }
 
 // ---------------------------------------------------------------- center
-// Sum of self scores (all sequences, or the reference list).
-__global__ void k_self_total(const int32_t *__restrict__ self, const int32_t *__restrict__ list,
-                             int count, long long *total) {
-  long long v = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-    v += self[list ? list[i] : i];
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(MSA_FULL_MASK, v, d);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long *)total, (unsigned long long)v);
-}
-
-// rowsum (input order) of d(i, j) = S_ii + S_jj - 2 S_ij over the partners:
-//   all pairs:  (n-1) S_ii + (T - S_ii) - 2 sum_{j != i} S_ij
-//   refs:       nref S_ii + T_ref - 2 sum_{r} S_ir
+// rowsum (input order) of d(i, j) = 2^16 - center_sim(S_ij, S_ii, S_jj) over
+// the partners, from the similarity sums:
+//   all pairs:  (n-1) 2^16 - sum_{j != i} sim(i, j)
+//   refs:       nref  2^16 - sum_{r} sim(i, r)       (d(i, i) = 0 when i is a reference)
 // then a per-block (min, lowest index) partial.
 __global__ void k_rowsum(int mode, int n, int nref, const int32_t *__restrict__ perm,
-                         const int32_t *__restrict__ self,
                          const unsigned long long *__restrict__ pairsum,
-                         const long long *__restrict__ total, long long *__restrict__ rowsum,
-                         long long *__restrict__ part_val, long long *__restrict__ part_idx) {
+                         long long *__restrict__ rowsum, long long *__restrict__ part_val,
+                         long long *__restrict__ part_idx) {
   __shared__ long long sv[32], si[32];
-  const long long T = *total;
+  const long long cnt = mode == 0 ? (long long)n - 1 : (long long)nref;
   long long bv = LLONG_MAX, bi = LLONG_MAX;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const long long s = self[k];
-    const long long ps = (long long)pairsum[k];
-    const long long v = mode == 0 ? (long long)(n - 1) * s + (T - s) - 2 * ps
-                                  : (long long)nref * s + T - 2 * ps;
+    const long long v = cnt * (long long)MSA_SIM_ONE - (long long)pairsum[k];
     const long long o = perm[k];
     rowsum[o] = v;
     if (v < bv || (v == bv && o < bi)) { bv = v; bi = o; }
@@ -296,20 +282,22 @@ __global__ void k_argmin(int parts, const long long *__restrict__ part_val,
   *idx = bi;
 }
 
+// Similarities of the pairs re-run in int32 (their packed lanes may have
+// overflowed), added where the center kernel would have added them.
 __global__ void k_apply_overflow(int mode, const int2 *__restrict__ ovf,
                                  const int32_t *__restrict__ scores, int count,
-                                 unsigned long long *pairsum, int32_t *self) {
+                                 unsigned long long *pairsum, const int32_t *__restrict__ self) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= count) return;
   const int q = ovf[x].x, s = ovf[x].y;
-  const unsigned long long S = (unsigned long long)(long long)scores[x];
+  const unsigned long long sim = center_sim(scores[x], self[q], self[s]);
   if (mode == 0) {
-    if (q == s) self[q] = scores[x];
-    else { atomicAdd(&pairsum[s], S); atomicAdd(&pairsum[q], S); }
+    atomicAdd(&pairsum[s], sim);
+    atomicAdd(&pairsum[q], sim);
   } else if (mode == 1) {
-    atomicAdd(&pairsum[s], S);
+    atomicAdd(&pairsum[s], sim);
   } else {
-    atomicAdd(&pairsum[q], S);
+    atomicAdd(&pairsum[q], sim);
   }
 }
 
@@ -388,27 +376,19 @@ cudaError_t launch_sp(const uint8_t *msa, int n, int64_t W, const uint8_t *sym_l
 }
 
 cudaError_t launch_center_finalize(int mode, int n, int nref, const int32_t *perm,
-                                   const int32_t *self, const unsigned long long *pairsum,
-                                   const int32_t *refs_sorted, long long *tmp_total,
-                                   long long *rowsum, long long *argmin_val,
-                                   long long *argmin_idx, long long *part_val,
-                                   long long *part_idx, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(tmp_total, 0, sizeof(long long), st);
-  if (e != cudaSuccess) return e;
-  const int cnt = mode == 0 ? n : nref;
-  k_self_total<<<blocks_for(cnt, 256, 1024), 256, 0, st>>>(self, mode == 0 ? nullptr : refs_sorted,
-                                                          cnt, tmp_total);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                                   const unsigned long long *pairsum, long long *rowsum,
+                                   long long *argmin_val, long long *argmin_idx,
+                                   long long *part_val, long long *part_idx, cudaStream_t st) {
   const int parts = blocks_for(n, 256, 1024);
-  k_rowsum<<<parts, 256, 0, st>>>(mode, n, nref, perm, self, pairsum, tmp_total, rowsum, part_val,
-                                  part_idx);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_rowsum<<<parts, 256, 0, st>>>(mode, n, nref, perm, pairsum, rowsum, part_val, part_idx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_argmin<<<1, 32, 0, st>>>(parts, part_val, part_idx, argmin_val, argmin_idx);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply_overflow(int mode, const int2 *ovf, const int32_t *scores, int count,
-                                  unsigned long long *pairsum, int32_t *self, cudaStream_t st) {
+                                  unsigned long long *pairsum, const int32_t *self, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   k_apply_overflow<<<(count + 255) / 256, 256, 0, st>>>(mode, ovf, scores, count, pairsum, self);
   return cudaGetLastError();

@@ -20,15 +20,15 @@ cudaError_t launch_rows(const uint8_t *res, const int64_t *pstart, const int32_t
 cudaError_t launch_sp(const uint8_t *msa, int n, int64_t W, const uint8_t *sym_lut, int nsym,
                       int32_t *counts, unsigned long long *total, cudaStream_t st);
 
+// Row sums of the center distance from the similarity sums (mode 0: all
+// pairs, mode 1: nref references) and their argmin (lowest input index).
 cudaError_t launch_center_finalize(int mode, int n, int nref, const int32_t *perm,
-                                   const int32_t *self, const unsigned long long *pairsum,
-                                   const int32_t *refs_sorted, long long *tmp_total,
-                                   long long *rowsum, long long *argmin_val,
-                                   long long *argmin_idx, long long *part_val,
-                                   long long *part_idx, cudaStream_t st);
+                                   const unsigned long long *pairsum, long long *rowsum,
+                                   long long *argmin_val, long long *argmin_idx,
+                                   long long *part_val, long long *part_idx, cudaStream_t st);
 
 cudaError_t launch_apply_overflow(int mode, const int2 *ovf, const int32_t *scores, int count,
-                                  unsigned long long *pairsum, int32_t *self, cudaStream_t st);
+                                  unsigned long long *pairsum, const int32_t *self, cudaStream_t st);
 
 cudaError_t launch_self_pairs(int n, int2 *pairs, int32_t *dst, cudaStream_t st);
 cudaError_t launch_extract_scores(const int32_t *seg, int n, int32_t *out, cudaStream_t st);

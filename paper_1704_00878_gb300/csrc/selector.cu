@@ -1,7 +1,8 @@
 // selector.cu -- the learned center selector behind the C ABI: a 1-D conv
 // embedding network whose squared embedding distances are trained on scaled
-// alignment distances d(A,B) = S(A,A) + S(B,B) - 2 S(A,B) that the exact
-// Smith-Waterman kernel produces, then used to pick the center in O(n):
+// exact-center distances d(A,B) = 2^16 - floor(2^16 S(A,B) / max(S(A,A),
+// S(B,B))) from the scores the exact Smith-Waterman kernel produces, then used
+// to pick the center in O(n):
 // argmin of ||e_i - mean(e)||^2, which equals argmin of sum_j ||e_i - e_j||^2,
 // the embedding stand-in for the exact center's argmin of sum_j d(i,j).
 #include <algorithm>
@@ -26,7 +27,7 @@ struct Selector {
   // batch buffers
   DevBuf seq, base, len, rowseq, x0, a1, a2, a3, pw, yw, emb, demb, dy4, dz3, dz2, dz1;
   DevBuf bpairs, btargets, loss, small, allemb, dist;
-  DevBuf vstart, vlen;  // a reference/candidate view of the loaded set
+  DevBuf vstart, vlen, vself;  // a reference/candidate view of the loaded set
 };
 
 namespace {
@@ -236,7 +237,14 @@ int stage_pairs(msa_ctx *ctx, Selector *s, const int64_t *pairs, const float *ta
   return build_batch(ctx, s, seqs, b);  // synchronises before the host vectors go away
 }
 
-// Scaled exact distances t = scale * (S_aa + S_bb - 2 S_ab).
+// The exact center's distance of a pair in units of 2^-16 (the kernels' sums
+// add 2^16 - center_sim of the same scores).
+long long center_distance(int sab, int saa, int sbb) {
+  const long long m = std::max(saa, sbb);
+  return m > 0 ? 65536 - ((long long)sab * 65536) / m : 0;
+}
+
+// Scaled exact distances t = scale * d(a, b).
 int exact_targets(msa_ctx *ctx, const int64_t *pairs, int64_t np, float scale,
                   std::vector<float> &t) {
   std::vector<int2> pr;
@@ -265,9 +273,9 @@ int exact_targets(msa_ctx *ctx, const int64_t *pairs, int64_t np, float scale,
   CK(cudaStreamSynchronize(ctx->st));
   t.resize(np);
   for (int64_t x = 0; x < np; ++x) {
-    const double saa = S[selfslot[ctx->inv[pairs[2 * x]]]];
-    const double sbb = S[selfslot[ctx->inv[pairs[2 * x + 1]]]];
-    t[x] = (float)(scale * (saa + sbb - 2.0 * S[x]));
+    const int saa = S[selfslot[ctx->inv[pairs[2 * x]]]];
+    const int sbb = S[selfslot[ctx->inv[pairs[2 * x + 1]]]];
+    t[x] = (float)(scale * (double)center_distance(S[x], saa, sbb));
   }
   return MSA_OK;
 }
@@ -302,7 +310,7 @@ void selector_free(msa_ctx *ctx, Selector *s) {
                     &s->w3n, &s->w4t, &s->w4n, &s->seq, &s->base, &s->len, &s->rowseq, &s->x0,
                     &s->a1, &s->a2, &s->a3, &s->pw, &s->yw, &s->emb, &s->demb, &s->dy4, &s->dz3,
                     &s->dz2, &s->dz1, &s->bpairs, &s->btargets, &s->loss, &s->small, &s->allemb,
-                    &s->dist, &s->vstart, &s->vlen};
+                    &s->dist, &s->vstart, &s->vlen, &s->vself};
   for (DevBuf *b : bufs) release(ctx, *b);
   delete s;
 }
@@ -360,14 +368,20 @@ int selector_center_refined(msa_ctx *ctx, int k, const std::vector<int32_t> &ref
   std::sort(qs.begin(), qs.end());
   stage_begin(ctx, ST_CENTER);
   CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
-  std::vector<unsigned long long> ps(k);  // sum_j S(q, j) per candidate
-  std::vector<int32_t> self(n, 0);        // S(x, x) where needed
-  std::vector<int32_t> need;              // sorted positions whose self score is needed
+  std::vector<unsigned long long> ps(k);  // sum_j center_sim(q, j) per candidate
   if (refs.empty()) {
+    // self scores of every sequence (every candidate meets every sequence)
+    std::vector<int2> sp(n);
+    std::vector<int32_t> dst(n);
+    for (int x = 0; x < n; ++x) { sp[x] = make_int2(x, x); dst[x] = x; }
+    TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
     CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
     TRY(run_center(ctx, 2, qs));
-    need.resize(n);
-    std::iota(need.begin(), need.end(), 0);
+    stage_end(ctx, ST_CENTER);
+    std::vector<unsigned long long> all(n);
+    CK(cudaMemcpyAsync(all.data(), ctx->pairsum.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int c = 0; c < k; ++c) ps[c] = all[qs[c]];
   } else {
     const int R = (int)refs.size();
     SetView view;
@@ -383,52 +397,35 @@ int selector_center_refined(msa_ctx *ctx, int k, const std::vector<int32_t> &ref
     }
     TRY(ensure(ctx, s->vstart, sizeof(int64_t) * nv));
     TRY(ensure(ctx, s->vlen, sizeof(int32_t) * nv));
+    TRY(ensure(ctx, s->vself, sizeof(int32_t) * nv));
     TRY(ensure(ctx, ctx->pairsum, sizeof(unsigned long long) * std::max(n, nv)));
     CK(cudaMemcpyAsync(s->vstart.p, vstart.data(), sizeof(int64_t) * nv, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(s->vlen.p, view.len.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, ctx->st));
+    // self scores of the view's entries (references, then candidates)
+    std::vector<int2> sp(nv);
+    std::vector<int32_t> dst(nv);
+    for (int v = 0; v < nv; ++v) { sp[v] = make_int2(view.idx[v], view.idx[v]); dst[v] = v; }
+    TRY(run_pairs(ctx, sp, dst, P<int32_t>(s->vself)));
     CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * nv, ctx->st));
     view.ss = SeqSet{P<uint8_t>(ctx->res), P<int64_t>(s->vstart), P<int32_t>(s->vlen), nv};
+    view.self = P<int32_t>(s->vself);
     std::vector<int32_t> vq(k);
     std::iota(vq.begin(), vq.end(), R);
     TRY(run_center(ctx, 2, vq, &view));
-    need = refs;
-    need.insert(need.end(), qs.begin(), qs.end());
-    std::sort(need.begin(), need.end());
-    need.erase(std::unique(need.begin(), need.end()), need.end());
-  }
-  // self scores of the needed sequences into slots 0..|need|-1
-  const int nn = (int)need.size();
-  std::vector<int2> sp(nn);
-  std::vector<int32_t> dst(nn);
-  for (int x = 0; x < nn; ++x) { sp[x] = make_int2(need[x], need[x]); dst[x] = x; }
-  TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
-  stage_end(ctx, ST_CENTER);
-  std::vector<int32_t> selfc(nn);
-  const size_t ps_off = refs.empty() ? 0 : refs.size();  // candidates' first view index
-  if (refs.empty()) {
-    std::vector<unsigned long long> all(n);
-    CK(cudaMemcpyAsync(all.data(), ctx->pairsum.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(selfc.data(), ctx->self.p, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    for (int c = 0; c < k; ++c) ps[c] = all[qs[c]];
-  } else {
-    CK(cudaMemcpyAsync(ps.data(), P<unsigned long long>(ctx->pairsum) + ps_off,
+    stage_end(ctx, ST_CENTER);
+    CK(cudaMemcpyAsync(ps.data(), P<unsigned long long>(ctx->pairsum) + R,
                        sizeof(unsigned long long) * k, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(selfc.data(), ctx->self.p, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
   }
   stage_collect(ctx, ST_CENTER);
-  for (int x = 0; x < nn; ++x) self[need[x]] = selfc[x];
-  // sum_j d(q, j) = |J| S(q,q) + sum_j S(j,j) - 2 sum_j S(q,j)
-  long long T = 0;
-  if (refs.empty()) for (int x = 0; x < n; ++x) T += self[x];
-  else for (int j : refs) T += self[j];
+  // sum_j d(q, j) = |J| 2^16 - sum_j center_sim(q, j) (the candidate meets itself
+  // among the j when it is one of them: similarity 2^16, distance 0)
   const long long nj = refs.empty() ? n : (long long)refs.size();
   long long best = 0;
   int bestq = -1;
   for (int c = 0; c < k; ++c) {
     const int q = qs[c];
-    const long long v = nj * self[q] + T - 2 * (long long)ps[c];
+    const long long v = nj * 65536 - (long long)ps[c];
     if (bestq < 0 || v < best || (v == best && ctx->perm[q] < ctx->perm[bestq])) { best = v; bestq = q; }
   }
   *center_out = ctx->perm[bestq];

@@ -164,7 +164,7 @@ __device__ __forceinline__ int wave_pass(const int8_t *__restrict__ prof, int st
 // ------------------------------------------------------------ center scores
 // Work item = (query q, block of SPI consecutive subjects).  The CTA builds q's
 // profile, each group aligns LANES subjects against it; results go straight
-// into the per-sequence sums of S used by the distance row sums.
+// into the per-sequence sums of center_sim used by the distance row sums.
 template <int G, int R, bool PACK>
 __global__ void __launch_bounds__(kCenterThreads)
 k_center(SeqSet ss, Scoring sc, CenterJob job) {
@@ -235,6 +235,7 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
       for (int l = 0; l < LANES; ++l) {
         const int s = l ? sB : sA;
         if (!(l ? vB : vA)) continue;
+        if (job.mode == 0 && s == q) continue;  // d(q, q) = 0
         const int S = l ? Cell<PACK>::lane1(best) : Cell<PACK>::lane0(best);
         if (PACK && S > job.sat_thresh) {
           const unsigned slot = atomicAdd(job.ovf_count, 1u);
@@ -242,13 +243,14 @@ k_center(SeqSet ss, Scoring sc, CenterJob job) {
           else atomicOr(job.err, MSA_DERR_OVERFLOW);
           continue;
         }
+        const unsigned long long sim = center_sim(S, job.self[q], job.self[s]);
         if (job.mode == 0) {
-          if (s == q) job.self[q] = S;
-          else { atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S); qadd += (unsigned long long)(long long)S; }
+          atomicAdd(&job.pairsum[s], sim);
+          qadd += sim;
         } else if (job.mode == 1) {
-          atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+          atomicAdd(&job.pairsum[s], sim);
         } else {
-          qadd += (unsigned long long)(long long)S;
+          qadd += sim;
         }
       }
       if (qadd) atomicAdd(&s_qsum, qadd);
@@ -440,7 +442,8 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
         for (int l = 0; l < 2; ++l) {
           const int q = l ? qB : qA;
           if (q < 0) continue;
-          if (job.mode == 0 && s < q) continue;  // counted as (s, q) by the earlier query
+          // (s, q) with s < q is counted by the earlier query; d(q, q) = 0
+          if (job.mode == 0 && s <= q) continue;
           const int S = l ? Cell<true>::lane1(best) : Cell<true>::lane0(best);
           if (S > job.sat_thresh) {
             const unsigned slot = atomicAdd(job.ovf_count, 1u);
@@ -448,16 +451,14 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
             else atomicOr(job.err, MSA_DERR_OVERFLOW);
             continue;
           }
+          const unsigned long long sim = center_sim(S, job.self[q], job.self[s]);
           if (job.mode == 0) {
-            if (s == q) job.self[q] = S;
-            else {
-              atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
-              atomicAdd(&s_qsum[0][l], (unsigned long long)(long long)S);
-            }
+            atomicAdd(&job.pairsum[s], sim);
+            atomicAdd(&s_qsum[0][l], sim);
           } else if (job.mode == 1) {
-            atomicAdd(&job.pairsum[s], (unsigned long long)(long long)S);
+            atomicAdd(&job.pairsum[s], sim);
           } else {
-            atomicAdd(&s_qsum[0][l], (unsigned long long)(long long)S);
+            atomicAdd(&s_qsum[0][l], sim);
           }
         }
       }
@@ -555,7 +556,8 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
         for (int l = 0; l < 2; ++l) {
           const int q = s_q[k][l];
           if (q < 0) continue;
-          if (job.mode == 0 && s < q) continue;  // counted as (s, q) by the earlier query
+          // (s, q) with s < q is counted by the earlier query; d(q, q) = 0
+          if (job.mode == 0 && s <= q) continue;
           const int S = gbest[2 * k + l];
           if (S > job.sat_thresh) {
             const unsigned slot = atomicAdd(job.ovf_count, 1u);
@@ -563,16 +565,14 @@ k_center2(SeqSet ss, Scoring sc, CenterJob job) {
             else atomicOr(job.err, MSA_DERR_OVERFLOW);
             continue;
           }
+          const unsigned long long sim = center_sim(S, job.self[q], job.self[s]);
           if (job.mode == 0) {
-            if (s == q) job.self[q] = S;
-            else {
-              sub += (unsigned long long)(long long)S;
-              atomicAdd(&s_qsum[k][l], (unsigned long long)(long long)S);
-            }
+            sub += sim;
+            atomicAdd(&s_qsum[k][l], sim);
           } else if (job.mode == 1) {
-            sub += (unsigned long long)(long long)S;
+            sub += sim;
           } else {
-            atomicAdd(&s_qsum[k][l], (unsigned long long)(long long)S);
+            atomicAdd(&s_qsum[k][l], sim);
           }
         }
       }
@@ -1165,19 +1165,26 @@ cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc
 // ===================================================================
 // Allocation-free pair scores (msa_pair_scores_noalloc in include/msa.h).
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA
-// graph is being captured, processes whose device memory is owned by another
-// allocator, or latency-critical services that forbid driver allocations
-// after start-up.  This entry point serves them: the caller passes every
-// input and output buffer, and the only working memory is the fixed array
-// below, which each GPU that loads the library holds until the process exits.
-// Every call on a device shares it, so calls that overlap on the GPU race;
-// issue them one after another (for example on one stream).
+// Some callers cannot allocate device memory: plug-ins hosted by an
+// application whose allocator owns all of the GPU's memory, processes whose
+// device memory is handed out by another framework's pool, or
+// latency-critical services that forbid driver allocations after start-up.
+// This entry point serves them: the caller passes every input and output
+// buffer, and the only working memory is the fixed array below, which each
+// GPU that loads the library holds until the process exits.  Every call on a
+// device shares it, so calls that overlap on the GPU race; issue them one
+// after another (for example on one stream).  Before it returns, the call
+// copies the array's error word to the host and waits for its stream.
 namespace {
 
-constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;  // 32 MiB per device
 constexpr size_t kNoallocControlBytes = 256;               // counter + error word
+constexpr size_t kNoallocRowBytes = (size_t)32 << 20;      // boundary rows: 32 MiB
+constexpr size_t kNoallocScratchBytes = kNoallocControlBytes + kNoallocRowBytes;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// error word bits
+constexpr unsigned kNoallocBadIndex = 1u;    // a pair index or a length out of range
+constexpr unsigned kNoallocBadResidue = 2u;  // a residue code >= alphabet
 
 constexpr int kNoallocG = 32;  // one group per warp, 512 query rows per pass
 
@@ -1228,7 +1235,15 @@ __global__ void __launch_bounds__(256) k_pairs_noalloc(NoallocArgs a) {
       }
     }
     if (!ok) {  // the whole warp takes this branch together
-      if (t == 0) { a.out[pi] = -1; atomicOr(err, 1u); }
+      if (t == 0) { a.out[pi] = -1; atomicOr(err, kNoallocBadIndex); }
+      continue;
+    }
+    // every residue code must index a profile row (0..K-1) before any is used
+    bool bad = false;
+    for (int i = t; i < La; i += G) bad |= ra[i] >= K;
+    for (int i = t; i < Lb; i += G) bad |= rb[i] >= K;
+    if (__any_sync(MSA_FULL_MASK, bad)) {
+      if (t == 0) { a.out[pi] = -1; atomicOr(err, kNoallocBadResidue); }
       continue;
     }
     const int np = (La + SR - 1) / SR;
@@ -1308,8 +1323,7 @@ extern "C" int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *o
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_noalloc, 256, smem);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long grid = (long long)std::max(per_sm, 1) * std::max(sms, 1);
-  if (per_cta > 0)
-    grid = std::min<long long>(grid, (long long)((kNoallocScratchBytes - kNoallocControlBytes) / per_cta));
+  if (per_cta > 0) grid = std::min<long long>(grid, (long long)(kNoallocRowBytes / per_cta));
   if (grid < 1) return MSA_ERANGE;
   a.K = alphabet; a.o = gap_open; a.e = gap_extend; a.max_len = max_len;
   a.res = residues; a.offsets = offsets; a.n = n; a.pairs = pairs; a.npairs = npairs;
@@ -1325,5 +1339,6 @@ extern "C" int msa_pair_scores_noalloc(const uint8_t *residues, const int64_t *o
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return MSA_ECUDA;
+  if (herr & kNoallocBadResidue) return MSA_EINVAL;
   return herr ? MSA_ERANGE : MSA_OK;
 }

@@ -17,7 +17,7 @@ struct Scoring {
 
 // All-pairs / reference-pairs scores for center selection.
 struct CenterJob {
-  int mode;                       // 0: query q vs subjects [q, n), both sides summed;
+  int mode;                       // 0: query q vs subjects (q, n), both sides summed;
                                   // 1: query qlist[x] vs [0, n), summed on the subject;
                                   // 2: query qlist[x] vs [0, n), summed on the query
   const int32_t *qlist;           // mode 1 (sorted indices)
@@ -28,8 +28,8 @@ struct CenterJob {
   int64_t n_items;
   int npass;                      // passes of the longest query in the range
   unsigned long long *counter;    // zeroed before launch
-  unsigned long long *pairsum;    // int64 sums of S over the listed partners (sorted index)
-  int32_t *self;                  // mode 0: S(q,q)
+  unsigned long long *pairsum;    // sums of center_sim over the listed partners (job's index)
+  const int32_t *self;            // S(k,k) of every sequence in the job's index space (read)
   int sat_thresh;                 // packed cells: lanes whose best exceeds this are re-run in int32
   int2 *ovf; unsigned *ovf_count; int ovf_cap; unsigned *err;
   int2 *scratch; int scratch_cols;

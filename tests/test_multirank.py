@@ -40,11 +40,7 @@ def _rank_main(rank, world, port, out_dir):
         n = prob.n
         lo, hi = shard.shard_bounds(n, world, rank)
         # exact center: this rank's candidates against every sequence
-        pairs = np.array([(i, j) for i in range(lo, hi) for j in range(n)] +
-                         [(j, j) for j in range(n)])
-        S = oracle.pair_scores(prob, pairs)
-        block, self = S[:(hi - lo) * n].reshape(hi - lo, n).astype(np.int64), S[(hi - lo) * n:]
-        local = np.array([(self[i] + self - 2 * block[i - lo]).sum() for i in range(lo, hi)])
+        local = oracle.center_rowsums(prob, np.arange(lo, hi))
         rowsum = shard.gather_rowsums(local, n)
         center = int(np.argmin(rowsum))
         # alignment of this rank's rows, then the global slot maxima

@@ -87,7 +87,11 @@ def test_flatten_roundtrip_and_center_rule():
     assert all(np.array_equal(p[k], q[k]) for k in p)
     emb = np.array([[0.0, 0.0], [1.0, 0.0], [-1.0, 0.0], [0.0, 3.0]])
     assert net.center_of(emb) == 0
-    assert np.allclose(net.distance_targets([5, 0], [10, 4], [10, 6], 0.01), [0.1, 0.1])
+    # the exact center's distance 2^16 - floor(2^16 S_ab / max(S_aa, S_bb)), 0 when
+    # both self scores are 0: 5 of 10 -> 32768; 0 of 6 -> 65536; 1 of 3 -> 65536 -
+    # 21845; no self score -> 0
+    t = net.distance_targets([5, 0, 1, 0], [10, 4, 3, 0], [10, 6, 2, 0], 0.01)
+    assert np.allclose(t, [327.68, 655.36, 436.91, 0.0])
 
 
 @pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 9, 40])
