@@ -25,8 +25,8 @@ MUTATIONS = {
     "distance_rounds_up": ("return ORC_ONE - ((int64_t)sab * ORC_ONE) / m;",
                            "return ORC_ONE - ((int64_t)sab * ORC_ONE + m - 1) / m;"),
     "distance_zero_self_far": ("if (m <= 0) return 0;", "if (m <= 0) return ORC_ONE;"),
-    "distance_unnormalised": ("sum += orc_distance(S[i * nr + r], self[i], self[ri]);",
-                              "sum += (int64_t)self[i] + self[ri] - 2 * (int64_t)S[i * nr + r];"),
+    "distance_unnormalised": ("sum += orc_distance(S[x * nr + r], self[i], self[ri]);",
+                              "sum += (int64_t)self[i] + self[ri] - 2 * (int64_t)S[x * nr + r];"),
     "right_justified": (
         "            for (int32_t u = 0; u < in[j]; u++) row[pos++] = (uint8_t)letters[s[k++]];\n"
         "            for (int32_t u = in[j]; u < G[j]; u++) row[pos++] = '-';\n",
