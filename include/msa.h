@@ -181,9 +181,11 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out);
 int msa_alignment_info(msa_ctx *ctx, int32_t *seg_out, uint16_t *ins_out, uint8_t *occ_out);
 
 /* Traceback codes of sequence `seq` from the last msa_align_to_center, as a
- * host or device uint8[Lc][Ls] array: bits 0-1 source of H (0 zero, 1
+ * host or device uint8[Lc][Ls] array: bits 0-1 source of H where H > 0 (1
  * diagonal, 2 F = center residue vs gap, 3 E = sequence residue vs gap),
- * bit 2 E extended, bit 3 F extended.  Testing aid. */
+ * bit 2 E extended, bit 3 F extended.  Where H = 0 the traceback stops on
+ * the score it carries along its path, so the source bits there are 0 in
+ * the int32 kernel and one of 1-3 in the packed one.  Testing aid. */
 int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out);
 
 /* Merge (Figure 3's reduce + final map): G[j] = max over rows of ins[j],

@@ -90,6 +90,23 @@ __device__ __forceinline__ unsigned long long center_sim(int S, int sa, int sb) 
                : MSA_SIM_ONE;
 }
 
+// The best cell of an alignment as one 64-bit key: a larger score first, then a
+// smaller row i (center), then a smaller column j (sequence), so the maximum
+// of the keys of any set of cells is the best cell under that tie rule; 0 when
+// no cell is positive.  score < 2^35, i, j < 2^14.
+__host__ __device__ __forceinline__ unsigned long long best_key(int v, int i, int j) {
+  return v > 0 ? ((unsigned long long)v << 28) | ((unsigned long long)(16383 - i) << 14) |
+                     (unsigned long long)(16383 - j)
+               : 0ull;
+}
+__host__ __device__ __forceinline__ int best_key_score(unsigned long long k) { return (int)(k >> 28); }
+__host__ __device__ __forceinline__ int best_key_row(unsigned long long k) {
+  return k ? 16383 - (int)((k >> 14) & 16383u) : 0;
+}
+__host__ __device__ __forceinline__ int best_key_col(unsigned long long k) {
+  return k ? 16383 - (int)(k & 16383u) : 0;
+}
+
 // Device-side error word bits (ctx->d_err).
 #define MSA_DERR_LETTER   1u   // a letter outside the alphabet
 #define MSA_DERR_TRACE    2u   // inconsistent traceback codes

@@ -1022,13 +1022,14 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   }
   TRY(ensure(ctx, ctx->codes, biggest));
   TRY(ensure(ctx, ctx->code_off, sizeof(int64_t) * n));
-  TRY(ensure(ctx, ctx->best, sizeof(int32_t) * 3 * n));
+  TRY(ensure(ctx, ctx->best, sizeof(unsigned long long) * n));
   CK(cudaMemcpyAsync(ctx->code_off.p, offs.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, ctx->st));
   const SeqSet ss = seqset(ctx);
   const Scoring sc = scoring(ctx);
   const int smem = codes_smem_bytes(ctx->K, npass * G * R);
   const int grid = codes_grid(G, packed, smem);
-  if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)grid * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
+  if (npass > 1)
+    TRY(ensure(ctx, ctx->scratch, (size_t)grid * (codes_threads(packed) / G) * 2 * ctx->maxlen * sizeof(int2)));
   float ms_dp = 0.f, ms_tb = 0.f;
   int64_t cells = 0;
   for (int k = 0; k < n; ++k) cells += (int64_t)Lc * ctx->len_sorted[k];
@@ -1041,19 +1042,21 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
     job.se = se;
     job.code_off = P<int64_t>(ctx->code_off) + sb;
     job.codes = P<uint8_t>(ctx->codes);
-    job.best = P<int32_t>(ctx->best) + 3 * (size_t)sb;
+    job.best = P<unsigned long long>(ctx->best) + sb;
     job.npass = npass;
     job.counter = ctx->dcounter;
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
+
     // offsets inside the batch are relative to the batch start
     CK((++ctx->launches, launch_codes)(G, packed, ss, sc, job, grid, ctx->st));
     stage_end(ctx, ST_ALIGN);
     stage_begin(ctx, ST_TRACE);
     CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
-                        P<int32_t>(ctx->best) + 3 * (size_t)sb, sb, se, P<int32_t>(ctx->d_len),
-                        P<int32_t>(ctx->d_perm), Lc, P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ),
-                        P<int32_t>(ctx->seg), P<int32_t>(ctx->score), ctx->derr, ctx->st));
+                        P<unsigned long long>(ctx->best) + sb, sb, se, P<int32_t>(ctx->d_len),
+                        P<int32_t>(ctx->d_perm), ss.res, ss.pstart, kc, sc.M, sc.K, sc.o, sc.e, Lc,
+                        P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->seg),
+                        P<int32_t>(ctx->score), ctx->derr, ctx->st));
     stage_end(ctx, ST_TRACE);
     CK(cudaStreamSynchronize(ctx->st));
     stage_collect(ctx, ST_ALIGN);
@@ -1108,20 +1111,22 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
   int rc = [&]() -> int {
     TRY(ensure(ctx, cb, bytes_all));
     TRY(ensure(ctx, ob, 2 * sizeof(int64_t)));
-    TRY(ensure(ctx, bb, sizeof(int32_t) * 6));
+    TRY(ensure(ctx, bb, sizeof(unsigned long long) * 2));
     const int64_t offs[2] = {0, (int64_t)bytes};
     CK(cudaMemcpyAsync(ob.p, offs, sizeof(offs), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
     const int smem = codes_smem_bytes(ctx->K, npass * G * R);
     const int grid = 1;
-    if (npass > 1) TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, packed, smem) * (256 / G) * 2 * ctx->maxlen * sizeof(int2)));
+    if (npass > 1)
+      TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, packed, smem) * (codes_threads(packed) / G) *
+                                        2 * ctx->maxlen * sizeof(int2)));
     CodesJob job;
     job.center = kc;
     job.sb = ks;
     job.se = se;
     job.code_off = P<int64_t>(ob);
     job.codes = P<uint8_t>(cb);
-    job.best = P<int32_t>(bb);
+    job.best = P<unsigned long long>(bb);
     job.npass = npass;
     job.counter = ctx->dcounter;
     job.scratch = P<int2>(ctx->scratch);

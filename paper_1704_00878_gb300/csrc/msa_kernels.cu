@@ -42,6 +42,12 @@ __global__ void k_encode(const uint8_t *__restrict__ letters, const int64_t *__r
 // zero cell (state H / F / E, as in Gotoh's traceback), then applies the flank
 // rule: residues before the segment pair right-aligned with the center, after
 // it left-aligned, surplus sequence residues go to slot 0 / slot Lc.
+// The walk carries the score v of the cell it stands on: H = best at the best
+// cell; a diagonal step from (i, j) gives H(i-1, j-1) = v - s(c_i, s_j); in a
+// gap state F(i, j) = v and a step up gives F(i-1, j) = v + e (extended) or
+// H(i-1, j) = v + o (opened), and likewise for E along the row.  In state H the
+// walk stops where v = 0 (the paper's "cell with score of zero"), so the codes
+// need a source only where H > 0.
 __device__ __forceinline__ uint32_t code_at(const uint8_t *__restrict__ c, int Ls, int i, int j) {
   const int r = i - 1;
   const size_t at = ((size_t)(r >> 4) * Ls + (j - 1)) * 8 + ((r & 15) >> 1);
@@ -49,8 +55,10 @@ __device__ __forceinline__ uint32_t code_at(const uint8_t *__restrict__ c, int L
 }
 
 __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__restrict__ code_off,
-                            const int32_t *__restrict__ best, int sb, int se,
+                            const unsigned long long *__restrict__ best, int sb, int se,
                             const int32_t *__restrict__ len, const int32_t *__restrict__ perm,
+                            const uint8_t *__restrict__ res, const int64_t *__restrict__ pstart,
+                            int center, const int8_t *__restrict__ M, int K, int o, int e,
                             int Lc, uint16_t *__restrict__ ins, uint8_t *__restrict__ occ,
                             int32_t *__restrict__ seg, int32_t *__restrict__ score,
                             unsigned *err) {
@@ -60,10 +68,12 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
   const int orig = perm[k];
   const int Ls = len[k];
   const uint8_t *c = codes + code_off[x];
+  const uint8_t *rc = res + pstart[center], *rs = res + pstart[k];
   uint16_t *in = ins + (size_t)orig * (Lc + 1);
   uint8_t *oc = occ + (size_t)orig * (Lc + 1);
-  const int bv = best[3 * x];
-  int i2 = best[3 * x + 1], j2 = best[3 * x + 2];
+  const unsigned long long key = best[x];
+  const int bv = best_key_score(key);
+  int i2 = best_key_row(key), j2 = best_key_col(key);
   int i1 = 0, j1 = 0;
   if (bv > 0 && (i2 < 1 || i2 > Lc || j2 < 1 || j2 > Ls)) {  // a best cell outside the matrix
     atomicOr(err, MSA_DERR_TRACE);
@@ -73,22 +83,33 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
     i2 = 0; j2 = 0;
   } else {
     int i = i2, j = j2, state = 0;  // 0 = H, 1 = F (center residue vs gap), 2 = E (inserted residue)
+    int v = bv;
     const int limit = 2 * (i2 + j2) + 4;
     bool ok = false;
     for (int step = 0; step < limit; ++step) {
-      if (i <= 0 || j <= 0) { ok = state == 0; break; }
-      const uint32_t code = code_at(c, Ls, i, j);
+      if (i <= 0 || j <= 0) { ok = state == 0 && v == 0; break; }
       if (state == 0) {
-        const uint32_t src = code & 3u;
-        if (src == 0) { ok = true; break; }
-        if (src == 1) { oc[i] = 1; --i; --j; }
-        else state = src == 2 ? 1 : 2;
+        if (v == 0) { ok = true; break; }
+        if (v < 0) break;
+        const uint32_t src = code_at(c, Ls, i, j) & 3u;
+        if (src == 1) {
+          v -= M[rc[i - 1] * K + rs[j - 1]];
+          oc[i] = 1; --i; --j;
+        } else if (src == 0) {
+          break;  // a positive score with no source: inconsistent codes
+        } else {
+          state = src == 2 ? 1 : 2;
+        }
       } else if (state == 1) {
-        state = (code >> 3) & 1u ? 1 : 0;
+        const bool ext = (code_at(c, Ls, i, j) >> 3) & 1u;
+        v += ext ? e : o;
+        state = ext ? 1 : 0;
         --i;
       } else {
+        const bool ext = (code_at(c, Ls, i, j) >> 2) & 1u;
         in[i] = (uint16_t)(in[i] + 1);
-        state = (code >> 2) & 1u ? 2 : 0;
+        v += ext ? e : o;
+        state = ext ? 2 : 0;
         --j;
       }
     }
@@ -328,15 +349,19 @@ cudaError_t launch_encode(const uint8_t *letters, const int64_t *src_off, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off, const int32_t *best,
-                             int sb, int se, const int32_t *len, const int32_t *perm, int Lc,
+cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
+                             const unsigned long long *best,
+                             int sb, int se, const int32_t *len, const int32_t *perm,
+                             const uint8_t *res, const int64_t *pstart, int center,
+                             const int8_t *M, int K, int o, int e, int Lc,
                              uint16_t *ins, uint8_t *occ, int32_t *seg, int32_t *score,
                              unsigned *err, cudaStream_t st) {
   const int cnt = se - sb;
   if (cnt <= 0) return cudaSuccess;
   const int threads = 128;
   k_traceback<<<(cnt + threads - 1) / threads, threads, 0, st>>>(codes, code_off, best, sb, se, len,
-                                                                 perm, Lc, ins, occ, seg, score, err);
+                                                                 perm, res, pstart, center, M, K, o,
+                                                                 e, Lc, ins, occ, seg, score, err);
   return cudaGetLastError();
 }
 

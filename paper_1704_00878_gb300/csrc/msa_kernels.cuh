@@ -6,8 +6,13 @@ cudaError_t launch_encode(const uint8_t *letters, const int64_t *src_off, const 
                           const int64_t *pstart, const int32_t *len, int n, const uint8_t *lut,
                           int padc, uint8_t *res, unsigned *err, cudaStream_t st);
 
-cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off, const int32_t *best,
-                             int sb, int se, const int32_t *len, const int32_t *perm, int Lc,
+// res/pstart/center/M/K/o/e: the walk recomputes the score of each cell on
+// its path (the codes hold a source only where H > 0).
+cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
+                             const unsigned long long *best,
+                             int sb, int se, const int32_t *len, const int32_t *perm,
+                             const uint8_t *res, const int64_t *pstart, int center,
+                             const int8_t *M, int K, int o, int e, int Lc,
                              uint16_t *ins, uint8_t *occ, int32_t *seg, int32_t *score,
                              unsigned *err, cudaStream_t st);
 

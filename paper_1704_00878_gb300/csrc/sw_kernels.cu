@@ -791,12 +791,7 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
       const bool take = ov > bv || (ov == bv && (oi < bi || (oi == bi && oj < bj)));
       if (take) { bv = ov; bi = oi; bj = oj; }
     }
-    if (t == 0 && valid) {
-      int32_t *b = job.best + (size_t)(k - job.sb) * 3;
-      b[0] = bv;
-      b[1] = bv > 0 ? bi : 0;
-      b[2] = bv > 0 ? bj : 0;
-    }
+    if (t == 0 && valid) job.best[k - job.sb] = best_key(bv, bi, bj);
   }
 }
 
@@ -805,20 +800,31 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
 // high one, against the same G*16 center rows (the host takes this path only
 // while every cell value fits: Lc * smax + smax + o < 2^15 and s + o >= 0).
 // Every pair of values a flag compares is ordered (F* >= H_up, E* >= H_left,
-// M >= max(P, F*) >= P, a row's new best >= its old best), so each flag is one
+// M >= P, M >= F*, a row's new best >= its old best), so each flag is one
 // 32-bit subtraction, which borrows across no lane, and a per-lane min with 1:
 //   F bit = min(F* - H_up, 1)          E bit = min(E* - H_left, 1)
-//   z     = min(H, 1)                  (H > 0)
-//   a     = min(M - P, z)              (the diagonal is not a best source)
-//   x     = min(M - max(P, F*), z)     (E is the only best source)
-//   src   = z + a + x                  (0 for H = 0, else 1 + a + x)
-// and the first column reaching a row's best is max(column, d * j) with
+//   a     = min(M - P, 1)              (the diagonal is not a best source)
+//   x     = min(M - F*, a)             (E is the only best source)
+//   src   = 1 + a + x                  (1 diagonal, 2 F, 3 E; ties in that order)
+// with M = max(P, F*, E*) in one three-way DPX max.  The source is meaningful
+// only where H > 0: the traceback carries the score of the cell it stands on
+// along the path and stops where that score is 0, so no zero flag is stored.
+// The leading 1 of every source comes from the accumulator's initial nibbles.
+// The first column reaching a row's best is max(column, d * j) with
 // d = min(best' - best, 1).
 // per-lane unsigned min of two int16 lanes: one instruction (the library's
 // three-operand form issues two)
 __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
   uint32_t d;
   asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// a * b + c in the low 32 bits (on the multiply-add pipe, beside the integer
+// pipe the DP keeps busy)
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
 
@@ -879,25 +885,23 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
     uint32_t hdiag = htop_prev;
     htop_prev = hin;
     uint32_t hup = hin, f = fin;
-    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    uint32_t acc[4] = {0x11111111u, 0x11111111u, 0x11111111u, 0x11111111u};
     Unroll<R>::run([&](auto ic) {
       constexpr int r = decltype(ic)::value;
+      constexpr uint32_t SH = 1u << (4 * (r & 3));
       const uint32_t p = hdiag + (uint32_t)C::template score<r & 3>(pa.w[r >> 2], pq.w[r >> 2]);
-      f = __viaddmax_s16x2(f, negE, hup);  // F*
+      f = __viaddmax_s16x2(f, negE, hup);                // F*
       const uint32_t bF = min_u16x2(f - hup, ONE);
-      const uint32_t tm = __vimax_s16x2_relu(p, f);
-      const uint32_t m = __vimax_s16x2_relu(tm, E[r]);
+      const uint32_t m = __vimax3_s16x2(p, f, E[r]);      // max(P, F*, E*)
       const uint32_t hn = __viaddmax_s16x2_relu(m, negO, 0u);
-      const uint32_t z = min_u16x2(hn, ONE);
-      const uint32_t a = min_u16x2(m - p, z);
-      const uint32_t x = min_u16x2(m - tm, z);
-      const uint32_t src = z + a + x;
+      const uint32_t a = min_u16x2(m - p, ONE);
+      const uint32_t x = min_u16x2(m - f, a);
       const uint32_t bE = min_u16x2(E[r] - H[r], ONE);
-      const uint32_t code = (bF << 3) + (bE << 2) + src;
-      acc[r >> 2] = (code << (4 * (r & 3))) + acc[r >> 2];
-      E[r] = __viaddmax_s16x2(E[r], negE, hn);  // E* of the next column
+      const uint32_t code = mad_lo(bF, 8u, mad_lo(bE, 4u, a + x));
+      acc[r >> 2] = mad_lo(code, SH, acc[r >> 2]);
+      E[r] = __viaddmax_s16x2(E[r], negE, hn);           // E* of the next column
       const uint32_t rbn = __vimax_s16x2_relu(rb[r], hn);
-      rj[r] = __vimax_s16x2_relu(rj[r], min_u16x2(rbn - rb[r], ONE) * jj);
+      rj[r] = __vimax_s16x2_relu(rj[r], mad_lo(min_u16x2(rbn - rb[r], ONE), jj, 0u));
       rb[r] = rbn;
       hdiag = H[r];
       H[r] = hn;
@@ -919,9 +923,14 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
   }
 }
 
+// kCodes2Threads threads per CTA; the kernel holds ~150 registers per thread
+// (one CTA, 8 warps, per SM; 12 warps in 384-thread CTAs measured slower, and
+// so did running several subject pairs back to back along one group's columns
+// to share the wavefront ramp: the lanes leave a pair at different steps, so
+// the per-pair bookkeeping runs once per lane).
 template <int G>
-__global__ void __launch_bounds__(256) k_codes2(SeqSet ss, Scoring sc, CodesJob job) {
-  constexpr int R = kCodesR, NT = 256, NG = NT / G, GPW = 32 / G;
+__global__ void __launch_bounds__(kCodes2Threads, 1) k_codes2(SeqSet ss, Scoring sc, CodesJob job) {
+  constexpr int R = kCodesR, NT = kCodes2Threads, NG = NT / G, GPW = 32 / G;
   extern __shared__ __align__(16) int8_t smem[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
   const int K = sc.K, padc = K;
@@ -981,12 +990,7 @@ __global__ void __launch_bounds__(256) k_codes2(SeqSet ss, Scoring sc, CodesJob 
         if (take) { v = ov; bi2 = oi; bj2 = oj; }
       }
       const int ks = s2 == 0 ? ka : kb;
-      if (t == 0 && (s2 == 0 ? valid : hasb)) {
-        int32_t *b = job.best + (size_t)(ks - job.sb) * 3;
-        b[0] = v;
-        b[1] = v > 0 ? bi2 : 0;
-        b[2] = v > 0 ? bj2 : 0;
-      }
+      if (t == 0 && (s2 == 0 ? valid : hasb)) job.best[ks - job.sb] = best_key(v, bi2, bj2);
     }
   }
 }
@@ -1123,9 +1127,11 @@ static codes_fn codes_kernel(int G, bool packed) {
 }
 
 
+int codes_threads(bool packed) { return packed ? kCodes2Threads : 256; }
+
 int codes_grid(int G, bool packed, int smem) {
   codes_fn fn = codes_kernel(G, packed);
-  return fn ? occupancy_grid((const void *)fn, 256, smem) : 0;
+  return fn ? occupancy_grid((const void *)fn, codes_threads(packed), smem) : 0;
 }
 
 // Group size for a center of length Lc.  A group of G lanes spends
@@ -1138,7 +1144,7 @@ int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_
   for (int G : {32, 16, 8}) {
     const int npass = (Lc + G * kCodesR - 1) / (G * kCodesR);
     const int grid = codes_grid(G, packed, codes_smem_bytes(K, npass * G * kCodesR));
-    const double warps = (double)grid * 8;
+    const double warps = (double)grid * (codes_threads(packed) / 32);
     const double units = packed ? (double)((n + 1) / 2) : (double)n;
     const double tasks = std::ceil(units / (32 / G));
     const double mean_steps = npass * (mean_len + G - 1), max_steps = npass * (max_len + G - 1.0);
@@ -1158,7 +1164,7 @@ cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc
   const int smem = codes_smem_bytes(sc.K, job.npass * G * kCodesR);
   if (smem > 40 * 1024)  // static shared memory counts too
     cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  fn<<<grid, 256, smem, st>>>(ss, sc, job);
+  fn<<<grid, codes_threads(packed), smem, st>>>(ss, sc, job);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ struct CodesJob {
   int sb, se;                     // subjects: sorted indices [sb, se), longest first
   const int64_t *code_off;        // byte offset of each subject's codes (indexed k - sb)
   uint8_t *codes;
-  int32_t *best;                  // per subject (indexed k - sb): {score, i2, j2}
+  unsigned long long *best;       // per subject (indexed k - sb): best_key of its best cell
   int npass;
   unsigned long long *counter;
   int2 *scratch; int scratch_cols;
@@ -94,7 +94,9 @@ cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc
                          int grid, cudaStream_t st);
 int codes_smem_bytes(int K, int rows_alloc);
 int codes_grid(int G, bool packed, int smem);
+int codes_threads(bool packed);  // threads per CTA of the codes kernels
 int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_len);
 constexpr int kCodesR = 16;
+constexpr int kCodes2Threads = 256;  // packed codes kernel threads per CTA
 constexpr int kPairsR = 16;
 constexpr int kCenterThreads = 256;
