@@ -41,6 +41,14 @@ UNIT = "GCUPS"
 # instructions on GB300 (half the 128 FP32 lanes).
 SMS, INT_LANES, MAX_GHZ, OPS_PER_CELL = 152, 64, 2.07, 3.0
 ALU_PEAK_GCUPS = SMS * INT_LANES * MAX_GHZ / OPS_PER_CELL
+# Alignment with traceback codes: the same 3 DPX instructions per cell plus 4
+# two-operand integer instructions for the 4-bit code (two source flags, two
+# gap-extension flags), which issue at twice the DPX rate (128 lanes per clock
+# per SM): 3 x 2 + 4 = 10 lane-slots per cell at 128 lanes per clock per SM.
+CODES_SLOTS_PER_CELL = 3 * 2 + 4
+CODES_PEAK_GCUPS = SMS * 2 * INT_LANES * MAX_GHZ / CODES_SLOTS_PER_CELL
+CODES_BYTES_PER_CELL = 0.5   # 4-bit traceback code per cell written to HBM
+ALIGN_WORKLOAD, ALIGN_N = "short_peptides_1m", 200_000
 
 
 def parse():
@@ -74,6 +82,9 @@ def parse():
                          "seeded references (the larger workloads)")
     ap.add_argument("--autotune", action="store_true",
                     help="correct the center planner's cost model with measured rates first")
+    ap.add_argument("--no-align-record", action="store_true",
+                    help="skip the alignment-kernel record (peptides against their 500-residue "
+                         "ancestor)")
     return ap.parse_args()
 
 
@@ -126,6 +137,15 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    """The generated peaks of the GB300s (empty if absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def dist_setup():
@@ -213,16 +233,72 @@ def workload_text(w, n, center, length=None):
     return ("%s: %d %s per GPU, %s, %d families at %.0f%% substitutions, %.1f%% indels, gap "
             "open %d / extend %d, %s center" % (w.name, n, kind, lens, w.families, 100 * w.p_sub,
                                                 100 * w.p_indel, w.gap_open, w.gap_extend,
+                                                "the named ancestor as" if w.center_seq else
                                                 "exact all-pairs" if center == "exact"
                                                 else "sampled exact (1,000 references)"))
 
 
-def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp, refs):
+def align_record(flush, stream, peak_gbs):
+    """The alignment to the center with traceback codes (the batched DP), on
+    its own: 200,000 short peptides (the 1e6-peptide workload's generator and
+    lengths) against their 500-residue common ancestor, the center the
+    workload names.  Inputs in HBM, L2 flushed before each timed call; CUDA
+    events around msa_align_to_center on the context stream, and the codes
+    kernels' own time from the library's stage events."""
+    import torch
+    from seqgen import generate, scoring
+    from paper_1704_00878_gb300 import binding as b
+    letters, offsets, w, _ = generate(ALIGN_WORKLOAD, n=ALIGN_N)
+    alph, M, _, _ = scoring(w.kind)
+    lens = np.diff(offsets)
+    dlet = torch.from_numpy(letters).cuda()
+    with b.Context(M, alph, w.gap_open, w.gap_extend, stream=stream) as h:
+        b.msa_load(h, dlet, offsets)
+        for _ in range(2):
+            b.msa_align_to_center(h, 0)
+        call_ms, kern_ms, tb_ms = [], [], []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            b.msa_align_to_center(h, 0)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            call_ms.append(ev0.elapsed_time(ev1))
+            ms, cnt = b.msa_stage_times(h)
+            kern_ms.append(ms["align_kernels"])
+            tb_ms.append(ms["traceback"])
+        cells = cnt["align_cells"]
+    k = float(np.mean(kern_ms))
+    gcups = cells / (k * 1e-3) / 1e9
+    return {"workload": "%d short peptides (lognormal lengths median 90 sigma 0.6 clipped 30-200, "
+                        "one family at 30%% substitutions, 3%% indels) against their %d-residue "
+                        "ancestor, BLOSUM62 11/1, packed int16x2 cells" % (ALIGN_N - 1, lens[0]),
+            "cells": cells, "kernel_ms": k, "traceback_ms": float(np.mean(tb_ms)),
+            "call_ms": float(np.mean(call_ms)), "gcups": gcups,
+            "gcups_with_traceback": cells / (float(np.mean(call_ms)) * 1e-3) / 1e9,
+            "roofline": {"bound": "alu", "kernel": "k_codes2 (Gotoh fill + 4-bit traceback codes, "
+                                                  "two subjects per int16x2 register)",
+                         "achieved": gcups, "peak": CODES_PEAK_GCUPS, "unit": UNIT,
+                         "frac": gcups / CODES_PEAK_GCUPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 integer lanes/clk x 2.07 GHz / (3 DPX "
+                                        "instructions at half rate + 4 two-operand ops) per cell",
+                         "hbm_bound_gcups": peak_gbs / CODES_BYTES_PER_CELL,
+                         "hbm_gbs_of_codes": gcups * CODES_BYTES_PER_CELL}}
+
+
+def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp, refs,
+                     exact_center, exact_rowsum):
     """Train the selector on exact-kernel distances (untimed), then time the
     whole step with the learned center (network embedding + exact row sums of
     its best candidates, over every sequence when the exact center is the
     all-pairs one, else over the same reference sample) against the exact
-    center's step."""
+    center's step.  Also: where the network's own pick (top 1) and the
+    methods without it (first sequence, shortest, longest, the best of as many
+    random candidates refined the same way) rank among the exact row sums,
+    and the avg SP of their MSAs."""
     import torch
     from seqgen import training_pairs
     pairs = training_pairs(n, 60000, fam, seed=8)
@@ -258,10 +334,31 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
         ms.append(ev0.elapsed_time(ev1))
     stages = b.msa_stage_times(h)[0]
     pairs_n = n * (n - 1) / 2
+
+    def avg_sp_of(center):
+        b.msa_align_to_center(h, int(center))
+        b.msa_merge_gaps(h, want_rows=False)
+        return b.msa_sp_score(h) / pairs_n
+
+    top1, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED)
+    rank = lambda i: 100.0 * float((exact_rowsum < exact_rowsum[int(i)]).mean())
+    rng = np.random.default_rng(0)
+    rand_rank = float(np.mean([100.0 * float((exact_rowsum < exact_rowsum[
+        rng.choice(n, min(cand, n), replace=False)].min()).mean()) for _ in range(100)]))
+    picks = {"exact": exact_center, "learned_refined": c, "learned_top1": top1, "first": 0,
+             "shortest": int(np.argmin(lens)), "longest": int(np.argmax(lens))}
+    compare = {name: {"center": int(i), "length": int(lens[int(i)]), "rowsum_rank_pct": rank(i),
+                      "avg_sp": (sp / pairs_n if name == "learned_refined" else
+                                 exact_sp / pairs_n if name == "exact" else avg_sp_of(i))}
+               for name, i in picks.items()}
     return {"exact_step_ms": exact_ms, "learned_step_ms": float(np.mean(ms)),
             "speedup": exact_ms / float(np.mean(ms)),
             "avg_sp_exact": exact_sp / pairs_n, "avg_sp_learned": sp / pairs_n,
             "sp_loss_pct": 100.0 * (sp - exact_sp) / exact_sp, "learned_center": c,
+            "sp_loss_top1_pct": 100.0 * (compare["learned_top1"]["avg_sp"] * pairs_n - exact_sp)
+                                / exact_sp,
+            "compare": compare,
+            "random_candidates_refined_mean_rank_pct": rand_rank,
             "selector": "4-layer conv, width 128, k 9, 64-d, bf16 on tcgen05 tensor cores",
             "train": {"pairs": int(pairs.shape[0]), "steps": 6000, "batch_pairs": 256,
                       "seconds": train_s, "loss_first": float(losses[:10].mean()),
@@ -304,6 +401,8 @@ def run_ours(args):
     center_mode = b.MSA_CENTER_EXACT_SAMPLED if refs is not None else b.MSA_CENTER_EXACT
 
     def select_exact():
+        if w.center_seq:  # the workload names its center: the 500-residue ancestor
+            return 0, 0
         return b.msa_select_center(h, center_mode, refs)
 
     def step_device():
@@ -455,8 +554,22 @@ def run_ours(args):
 
     learned = None
     if not args.no_learned:
-        learned = learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream,
-                                   total_ms / args.steps, sp, refs)
+        b.msa_load(h, dlet, offsets)
+        ex_c, _ = b.msa_select_center(h, center_mode, refs)
+        ex_rows = b.msa_center_rowsums(h).astype(np.float64)
+        ex_ms, ex_sp = total_ms / args.steps, sp
+        if w.center_seq:  # the timed step used the named center: time the selecting one
+            b.msa_align_to_center(h, ex_c)
+            b.msa_merge_gaps(h, want_rows=False)
+            ex_sp = b.msa_sp_score(h)
+            ex_ms = b.msa_stage_times(h)[0]["center"] + (total_ms / args.steps)
+        learned = learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, ex_ms, ex_sp,
+                                   refs, ex_c, ex_rows)
+        if w.center_seq:
+            learned["named_center_rowsum_rank_pct"] = 100.0 * float((ex_rows < ex_rows[0]).mean())
+    align = None
+    if not args.no_align_record and rank == 0:
+        align = align_record(flush, stream, measured_peaks().get("hbm_gbs", 6800.0))
 
     t_max = reduce_max(total_ms)
     all_cells = reduce_sum(float(cells))
@@ -473,7 +586,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
         "config": {"workload": workload_text(w, n, args.center, length),
                    "step": "encode + %s center + align with traceback + merge + rows + SP"
-                           % ("exact all-pairs" if refs is None else "sampled exact"),
+                           % ("the named (500-residue ancestor)" if w.center_seq else
+                              "exact all-pairs" if refs is None else "sampled exact"),
                    "l2": "flushed (512 MB write) before every timed step",
                    "cells_per_step": cells / args.steps, "center": c, "msa_width": W,
                    "avg_sp": sp / (n * (n - 1) / 2)},
@@ -495,6 +609,8 @@ def run_ours(args):
     }
     if learned is not None:
         line["learned_vs_exact"] = learned
+    if align is not None:
+        line["align"] = align
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(letters, offsets, alph, M, w.gap_open, w.gap_extend,
                                             args.cpu_seconds)
