@@ -164,6 +164,31 @@ int msa_select_center_refined(msa_ctx *ctx, int32_t candidates, const int64_t *r
  * selection: rowsum_out host or device int64[n]. */
 int msa_center_rowsums(msa_ctx *ctx, int64_t *rowsum_out);
 
+/* The exact center split over processes (each with its own GPU and context
+ * holding the same set): the paper spreads the center step over workers, and
+ * one allreduce-sum of per-sequence sums combines the shares.  Shard `shard`
+ * of `nshards` computes its share of the pairs of the EXACT selection (refs
+ * NULL or nref 0) or of EXACT_SAMPLED (refs: host int64[nref], distinct
+ * input indices) and writes, for every sequence i, its partial sum of pair
+ * similarities sim(i,j) = floor(2^16 S(i,j) / max(S(i,i), S(j,j))) (2^16
+ * when both self scores are 0) over the pairs it computed: sums_out host or
+ * device uint64[n], input order.  EXACT splits the all-pairs triangle into
+ * nshards contiguous query ranges (in the library's length order) of about
+ * equal DP work, each pair computed once and added to both sequences;
+ * EXACT_SAMPLED splits the references into chunks of about equal length.
+ * The elementwise sum over all shards is the same for every nshards; give it
+ * to msa_center_combine.  EINVAL for a bad shard or reference list. */
+int msa_center_partial(msa_ctx *ctx, const int64_t *refs, int64_t nref, int32_t shard,
+                       int32_t nshards, uint64_t *sums_out);
+
+/* Finish a sharded exact selection: sums (host or device uint64[n], input
+ * order) is the sum over shards of msa_center_partial; nref the reference
+ * count of EXACT_SAMPLED, 0 for EXACT.  Sets the row sums of d
+ * (msa_center_rowsums) as msa_select_center would and returns the center
+ * (lowest index on ties) and its row sum (sum_dist_out nullable). */
+int msa_center_combine(msa_ctx *ctx, const uint64_t *sums, int64_t nref, int64_t *center_out,
+                       int64_t *sum_dist_out);
+
 /* Align every loaded sequence to `center` (Figure 3's map step): affine
  * Smith-Waterman fill with 4-bit traceback codes, traceback from the best
  * cell (smallest row, then column) to a zero cell, flank rule, and one row of

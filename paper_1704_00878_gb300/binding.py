@@ -54,6 +54,10 @@ _SIGS = {
     "msa_select_center_refined": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_center_rowsums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_center_partial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "msa_center_combine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "msa_align_to_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "msa_alignment_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_debug_codes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -231,6 +235,29 @@ def msa_select_center_refined(ctx, candidates=0, refs=None):
     _check(ctx, lib().msa_select_center_refined(ctx, int(candidates), _ptr(r),
                                                 0 if r is None else r.size, _ptr(c), _ptr(s)))
     return int(c[0]), int(s[0])
+
+
+def msa_center_partial(ctx, shard, nshards, refs=None, out=None):
+    """This shard's partial similarity sums of the exact center (uint64[n])."""
+    n = msa_dims(ctx)[0]
+    res = np.zeros(n, np.uint64) if out is None else out
+    if refs is None:
+        _check(ctx, lib().msa_center_partial(ctx, None, 0, int(shard), int(nshards), _ptr(res)))
+    else:
+        r = np.ascontiguousarray(refs, dtype=np.int64)
+        _check(ctx, lib().msa_center_partial(ctx, _ptr(r), r.size, int(shard), int(nshards),
+                                             _ptr(res)))
+    return res
+
+
+def msa_center_combine(ctx, sums, nref=0):
+    """(center, its row sum) from the summed partial sums; sets the row sums."""
+    sm = np.ascontiguousarray(sums, dtype=np.uint64)
+    c = ctypes.c_int64(0)
+    v = ctypes.c_int64(0)
+    _check(ctx, lib().msa_center_combine(ctx, _ptr(sm), int(nref), ctypes.byref(c),
+                                         ctypes.byref(v)))
+    return int(c.value), int(v.value)
 
 
 def msa_center_rowsums(ctx, out=None):

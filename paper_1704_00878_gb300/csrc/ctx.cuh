@@ -125,7 +125,7 @@ struct SetView {
   const int32_t *self = nullptr;  // device: S(v, v) of every view entry
 };
 int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted,
-               const SetView *view = nullptr);
+               const SetView *view = nullptr, int q_begin = 0, int q_end = -1);
 // the device error word -> an MSA_E* code (synchronises the stream)
 int check_derr(msa_ctx *ctx);
 

@@ -446,7 +446,8 @@ int launch_plans(msa_ctx *ctx, int mode, const std::vector<ClassPlan> &plans, in
   return MSA_OK;
 }
 
-int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, const SetView *view) {
+int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, const SetView *view,
+               int q_begin, int q_end) {
   // qsorted: ascending sorted indices of the queries (modes 1, 2); mode 0 uses all.
   // With a view, indices are the view's and its first n_sub entries are the subjects.
   // The self scores (ctx->self, or the view's) must be current: the kernels
@@ -486,6 +487,14 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
   // that lowers the modelled cost per real cell; mode 0 streams see the
   // subjects from their first query on.
   const int npairs = (x1 + 1) / 2;
+  // mode 0 may run a share of the queries only, [q_begin, q_end) with even
+  // bounds (a shard of the all-pairs triangle); packed pairs [p_begin, p_end)
+  if (q_end < 0 || q_end > nq) q_end = nq;
+  if (mode != 0) { q_begin = 0; q_end = nq; }
+  if (q_begin < 0 || (q_begin & 1) || (q_end < nq && (q_end & 1)) || q_begin > q_end)
+    return fail(ctx, MSA_EINVAL, "bad query range");
+  const int p_begin = q_begin >= x1 ? npairs : q_begin / 2;
+  const int p_end = q_end >= x1 ? npairs : q_end / 2;
   const double total_len = (double)suffix[0];
   auto partner_cells = [&](int x) { return mode == 0 ? (double)suffix[x] : total_len; };
   auto partners = [&](int x) { return mode == 0 ? (double)(n - x) : (double)n; };
@@ -499,11 +508,11 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
   // within one pass (a stack over several passes pays boundary rows the
   // model does not see).
   int64_t items_single = 0;
-  for (int p = 0; p < npairs; ++p) items_single += (int64_t)(mode == 0 ? n - 2 * p : n) / 8;
+  for (int p = p_begin; p < p_end; ++p) items_single += (int64_t)(mode == 0 ? n - 2 * p : n) / 8;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
   const bool stack = mode != 2 && items_single >= 16 * 2 * 3 * (int64_t)std::max(sms, 1);
-  for (int p = 0; p < npairs;) {
+  for (int p = p_begin; p < p_end;) {
     int bv = -1, bm = 0;
     double bcost = 1e300;
     for (int v = 0; v < kNumCenterVariants; ++v) {
@@ -518,7 +527,7 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
             corr = ctx->tune_corr[b][v];
       int rows = 0;
       double real = 0;
-      for (int q = p; q < npairs && q - p < (stack ? kMaxSeg : 1); ++q) {
+      for (int q = p; q < p_end && q - p < (stack ? kMaxSeg : 1); ++q) {
         const int rq = pair_rows(qlen, x1, q, cv.R);
         if (q > p && rows + rq > GR) break;  // stacks stay within one pass
         if (center_profile_bytes(v, ctx->K, round_up_int(rows + rq, GR)) > kMaxPairedProfile) break;
@@ -550,13 +559,17 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
     p += bm;
   }
   // int32 part: single queries [x1, nq)
-  for (int x = x1; x < nq;) {
+  for (int x = std::max(x1, q_begin); x < q_end;) {
     const int v = choose_variant(ctx, qlen[x], est_at(x), false);
     if (v < 0) return fail(ctx, MSA_ERANGE, "no center kernel fits a query of length %d", qlen[x]);
     int xe = x + 1;
-    while (xe < nq && choose_variant(ctx, qlen[xe], est_at(xe), false) == v) ++xe;
+    while (xe < q_end && choose_variant(ctx, qlen[xe], est_at(xe), false) == v) ++xe;
     classes.push_back({v, x, xe});
     x = xe;
+  }
+  if (classes.empty()) {  // an empty share
+    ctx->cells[0] = 0;
+    return MSA_OK;
   }
   std::vector<ClassPlan> plans;
   std::vector<int64_t> prefix_all;
@@ -573,7 +586,7 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted, cons
   const float center_ms = ctx->stage_ms[ST_CENTER_K];
   int64_t cells = 0;
   if (mode == 0) {  // pairs q < s (the self scores are counted by their own pass)
-    for (int x = 0; x < nq; ++x) cells += (int64_t)lens[x] * suffix[x + 1];
+    for (int x = q_begin; x < q_end; ++x) cells += (int64_t)lens[x] * suffix[x + 1];
   } else {
     for (int q : qsorted) cells += (int64_t)lens[q] * suffix[0];
   }
@@ -966,6 +979,94 @@ int msa_center_rowsums(msa_ctx *ctx, int64_t *rowsum_out) {
   TRY(set_device(ctx));
   CK(cudaMemcpyAsync(rowsum_out, ctx->rowsum.p, sizeof(int64_t) * ctx->n, cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
+}
+
+int msa_center_partial(msa_ctx *ctx, const int64_t *refs, int64_t nref, int32_t shard,
+                       int32_t nshards, uint64_t *sums_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (!sums_out) return fail(ctx, MSA_EINVAL, "sums_out is NULL");
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  if (nshards < 1 || shard < 0 || shard >= nshards) return fail(ctx, MSA_EINVAL, "bad shard");
+  TRY(set_device(ctx));
+  const int n = ctx->n;
+  const bool sampled = refs && nref > 0;
+  std::vector<int32_t> qs;
+  if (sampled) TRY(reference_positions(ctx, refs, nref, qs));
+  CK(cudaMemsetAsync(ctx->pairsum.p, 0, sizeof(unsigned long long) * n, ctx->st));
+  CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+  {  // every pair's similarity needs both self scores
+    std::vector<int2> sp(n);
+    std::vector<int32_t> dst(n);
+    for (int k = 0; k < n; ++k) { sp[k] = make_int2(k, k); dst[k] = k; }
+    TRY(run_pairs(ctx, sp, dst, P<int32_t>(ctx->self)));
+  }
+  if (sampled) {
+    // the references (queries) in contiguous chunks of about equal length sum
+    std::vector<int32_t> mine;
+    int64_t total = 0, acc = 0;
+    for (int q : qs) total += ctx->len_sorted[q];
+    for (int q : qs) {
+      const int64_t mid2 = 2 * acc + ctx->len_sorted[q];  // twice the query's midpoint
+      const int owner = (int)std::min<int64_t>(nshards - 1, mid2 * nshards / std::max<int64_t>(2 * total, 1));
+      if (owner == shard) mine.push_back(q);
+      acc += ctx->len_sorted[q];
+    }
+    if (!mine.empty()) TRY(run_center(ctx, 1, mine));
+  } else {
+    // the all-pairs triangle: query x meets the sequences after it, work
+    // len[x] * (sum of the later lengths); contiguous even-aligned ranges of
+    // about equal work
+    std::vector<int64_t> suffix(n + 1, 0);
+    for (int k = n - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + ctx->len_sorted[k];
+    std::vector<double> work(n + 1, 0.0);
+    for (int k = 0; k < n; ++k) work[k + 1] = work[k] + (double)ctx->len_sorted[k] * suffix[k + 1];
+    auto cut = [&](int r) {
+      if (r <= 0) return 0;
+      if (r >= nshards) return n;
+      const double target = work[n] * r / nshards;
+      int x = (int)(std::lower_bound(work.begin(), work.end(), target) - work.begin());
+      x = std::min(n, std::max(0, x & ~1));
+      return x;
+    };
+    const int qa = cut(shard), qe = shard + 1 == nshards ? n : cut(shard + 1);
+    if (qe > qa) TRY(run_center(ctx, 0, {}, nullptr, qa, qe));
+  }
+  std::vector<unsigned long long> sorted(n), out(n);
+  CK(cudaMemcpyAsync(sorted.data(), ctx->pairsum.p, sizeof(unsigned long long) * n,
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  TRY(check_derr(ctx));
+  for (int k = 0; k < n; ++k) out[ctx->perm[k]] = sorted[k];
+  CK(cudaMemcpyAsync(sums_out, out.data(), sizeof(uint64_t) * n, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
+}
+
+int msa_center_combine(msa_ctx *ctx, const uint64_t *sums, int64_t nref, int64_t *center_out,
+                       int64_t *sum_dist_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (!sums || !center_out) return fail(ctx, MSA_EINVAL, "NULL argument");
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  if (nref < 0 || nref > ctx->n) return fail(ctx, MSA_EINVAL, "bad reference count");
+  TRY(set_device(ctx));
+  const int n = ctx->n;
+  std::vector<unsigned long long> in(n), sorted(n);
+  CK(cudaMemcpyAsync(in.data(), sums, sizeof(uint64_t) * n, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int k = 0; k < n; ++k) sorted[k] = in[ctx->perm[k]];
+  CK(cudaMemcpyAsync(ctx->pairsum.p, sorted.data(), sizeof(unsigned long long) * n,
+                     cudaMemcpyHostToDevice, ctx->st));
+  CK((++ctx->launches, launch_center_finalize)(nref > 0 ? 1 : 0, n, (int)nref,
+                            P<int32_t>(ctx->d_perm), P<unsigned long long>(ctx->pairsum),
+                            P<long long>(ctx->rowsum), ctx->dsmall + 1, ctx->dsmall + 2,
+                            P<long long>(ctx->part_val), P<long long>(ctx->part_idx), ctx->st));
+  long long h[3];
+  CK(cudaMemcpyAsync(h, ctx->dsmall, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *center_out = h[2];
+  if (sum_dist_out) *sum_dist_out = h[1];
+  ctx->have_rowsum = true;
   return MSA_OK;
 }
 
