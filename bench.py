@@ -49,6 +49,28 @@ CODES_SLOTS_PER_CELL = 3 * 2 + 4
 CODES_PEAK_GCUPS = SMS * 2 * INT_LANES * MAX_GHZ / CODES_SLOTS_PER_CELL
 CODES_BYTES_PER_CELL = 0.5   # 4-bit traceback code per cell written to HBM
 ALIGN_WORKLOAD, ALIGN_N = "short_peptides_1m", 200_000
+# the library's center kernel variants, in msa_autotune's column order:
+# (two queries per int16x2 register?, lanes per group, query rows per lane, packed)
+CENTER_VARIANTS = [(1, 8, 12, 1), (1, 8, 20, 1), (1, 8, 28, 1), (1, 16, 12, 1), (1, 16, 20, 1),
+                   (1, 16, 28, 1), (1, 32, 12, 1), (1, 32, 20, 1), (1, 32, 28, 1), (0, 32, 16, 1),
+                   (0, 32, 24, 1), (0, 8, 16, 0), (0, 16, 16, 0), (0, 32, 16, 0)]
+BUCKET_EDGES = [1, 48, 80, 112, 144, 176, 208, 256, 320, 384, 448, 512, 640, 768, 896, 1024, 1280,
+                1536, 2048, 3072, 4096, 8193]
+
+
+def tuner_choices(rates):
+    """Per timed length bucket: the fastest center variant and its rate."""
+    out = {}
+    for bk in range(rates.shape[0]):
+        if not (rates[bk] > 0).any():
+            continue
+        v = int(np.argmax(rates[bk]))
+        paired, G, R, packed = CENTER_VARIANTS[v]
+        out["%d-%d" % (BUCKET_EDGES[bk], BUCKET_EDGES[bk + 1] - 1)] = {
+            "variant": "%s G%d R%d %s" % ("query pair" if paired else "single query", G, R,
+                                          "int16x2" if packed else "int32"),
+            "gcups": float(rates[bk, v]) / 1e9}
+    return out
 
 
 def parse():
@@ -80,8 +102,9 @@ def parse():
     ap.add_argument("--center", default="exact", choices=["exact", "sampled"],
                     help="exact all-pairs center, or the sampled exact center over 1,000 "
                          "seeded references (the larger workloads)")
-    ap.add_argument("--autotune", action="store_true",
-                    help="correct the center planner's cost model with measured rates first")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuners (center variants per length bucket; alignment "
+                         "group width and int16x2 / int32 cells) and use the cost models")
     ap.add_argument("--no-align-record", action="store_true",
                     help="skip the alignment-kernel record (peptides against their 500-residue "
                          "ancestor)")
@@ -238,7 +261,7 @@ def workload_text(w, n, center, length=None):
                                                 else "sampled exact (1,000 references)"))
 
 
-def align_record(flush, stream, peak_gbs):
+def align_record(flush, stream, peak_gbs, no_tune=False):
     """The alignment to the center with traceback codes (the batched DP), on
     its own: 200,000 short peptides (the 1e6-peptide workload's generator and
     lengths) against their 500-residue common ancestor, the center the
@@ -254,6 +277,7 @@ def align_record(flush, stream, peak_gbs):
     dlet = torch.from_numpy(letters).cuda()
     with b.Context(M, alph, w.gap_open, w.gap_extend, stream=stream) as h:
         b.msa_load(h, dlet, offsets)
+        tune = None if no_tune else b.msa_align_autotune(h, 0)
         for _ in range(2):
             b.msa_align_to_center(h, 0)
         call_ms, kern_ms, tb_ms = [], [], []
@@ -273,7 +297,14 @@ def align_record(flush, stream, peak_gbs):
         cells = cnt["align_cells"]
     k = float(np.mean(kern_ms))
     gcups = cells / (k * 1e-3) / 1e9
-    return {"workload": "%d short peptides (lognormal lengths median 90 sigma 0.6 clipped 30-200, "
+    tuned = None
+    if tune is not None:
+        rates, (lanes, packed) = tune
+        tuned = {"choice": {"lanes": lanes, "cells": "int16x2" if packed else "int32"},
+                 "gcups": {"%s_G%d" % (p, 8 << g): float(rates[i, g]) / 1e9
+                           for i, p in enumerate(("int16x2", "int32")) for g in range(3)
+                           if rates[i, g] > 0}}
+    return {"autotune": tuned, "workload": "%d short peptides (lognormal lengths median 90 sigma 0.6 clipped 30-200, "
                         "one family at 30%% substitutions, 3%% indels) against their %d-residue "
                         "ancestor, BLOSUM62 11/1, packed int16x2 cells" % (ALIGN_N - 1, lens[0]),
             "cells": cells, "kernel_ms": k, "traceback_ms": float(np.mean(tb_ms)),
@@ -523,8 +554,17 @@ def run_ours(args):
     rate, per_clk = b.msa_probe_int_rate(b.MSA_PROBE_VIADDMAX_S16X2)
     b.msa_load(h, dlet, offsets)
     t0 = time.perf_counter()
-    # untimed: picks the center kernel variant per length bucket
-    tune = b.msa_autotune(h) if args.autotune else np.zeros((0, 0))
+    # untimed: the center kernel variant per length bucket, then (with the
+    # center of a first step) the alignment's group width and cell precision
+    tune = b.msa_autotune(h) if not args.no_autotune else np.zeros((0, 0))
+    align_tune = None
+    if not args.no_autotune:
+        c0, _, _ = step_device()
+        rates_a, (lanes_a, packed_a) = b.msa_align_autotune(h, c0)
+        align_tune = {"choice": {"lanes": lanes_a, "cells": "int16x2" if packed_a else "int32"},
+                      "gcups": {"%s_G%d" % (p, 8 << g): float(rates_a[i, g]) / 1e9
+                                for i, p in enumerate(("int16x2", "int32")) for g in range(3)
+                                if rates_a[i, g] > 0}}
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         step_device()
@@ -569,7 +609,8 @@ def run_ours(args):
             learned["named_center_rowsum_rank_pct"] = 100.0 * float((ex_rows < ex_rows[0]).mean())
     align = None
     if not args.no_align_record and rank == 0:
-        align = align_record(flush, stream, measured_peaks().get("hbm_gbs", 6800.0))
+        align = align_record(flush, stream, measured_peaks().get("hbm_gbs", 6800.0),
+                             args.no_autotune)
 
     t_max = reduce_max(total_ms)
     all_cells = reduce_sum(float(cells))
@@ -605,7 +646,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "device_mem_gb": b.msa_memory(h)[1] / 1e9,
         "autotune": {"seconds": tune_s, "buckets_timed": int((tune > 0).any(axis=1).sum()),
-                     "variants_timed": int((tune > 0).sum())},
+                     "variants_timed": int((tune > 0).sum()),
+                     "center_choice_per_bucket": tuner_choices(tune) if tune.size else {},
+                     "align": align_tune},
     }
     if learned is not None:
         line["learned_vs_exact"] = learned

@@ -54,6 +54,8 @@ _SIGS = {
     "msa_select_center_refined": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_center_rowsums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_align_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "msa_center_partial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "msa_center_combine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -235,6 +237,14 @@ def msa_select_center_refined(ctx, candidates=0, refs=None):
     _check(ctx, lib().msa_select_center_refined(ctx, int(candidates), _ptr(r),
                                                 0 if r is None else r.size, _ptr(c), _ptr(s)))
     return int(c[0]), int(s[0])
+
+
+def msa_align_autotune(ctx, center):
+    """(rates double[2, 3] = [packed, int32] x [8, 16, 32] lanes, (lanes, packed))."""
+    rates = np.zeros((2, 3), np.float64)
+    choice = np.zeros(2, np.int32)
+    _check(ctx, lib().msa_align_autotune(ctx, int(center), _ptr(rates), _ptr(choice)))
+    return rates, (int(choice[0]), bool(choice[1]))
 
 
 def msa_center_partial(ctx, shard, nshards, refs=None, out=None):

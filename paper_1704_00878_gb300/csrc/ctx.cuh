@@ -54,6 +54,9 @@ struct msa_ctx {
   cudaEvent_t cap_fork = nullptr, cap_join = nullptr;
   cudaGraphExec_t center_exec = nullptr;  // the last center graph and what it bakes in
   std::vector<int64_t> center_key;
+  cudaGraphExec_t align_exec = nullptr;   // the last alignment graph and what it bakes in
+  std::vector<int64_t> align_key;
+  std::vector<cudaEvent_t> align_ev;      // per code batch: fill start/end, traceback end
   bool have_rowsum = false;
 
   // alignment
@@ -85,6 +88,7 @@ struct msa_ctx {
   // times over, and the traceback of each batch waits for its fill
   size_t codes_budget = (size_t)32 << 30;
   int align_group = 0;  // lanes per subject group of the codes kernels, 0 = modelled choice
+  int align_int32 = 0;  // 1: the alignment uses int32 cells even where packed ones fit
 
   msa_detail::Selector *sel = nullptr;
 

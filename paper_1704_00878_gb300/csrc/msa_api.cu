@@ -212,7 +212,7 @@ int sat_thresh(msa_ctx *ctx) { return ctx->sat_limit - ctx->smax - ctx->o; }
 // int16 lanes hold every value of the alignment to a center of length Lc:
 // H <= Lc * smax, and the biased P = H + s + o never passes Lc * smax + smax + o.
 static bool codes_packed(msa_ctx *ctx, int Lc) {
-  if (ctx->precision == MSA_INT32 || ctx->smin + ctx->o < 0) return false;
+  if (ctx->precision == MSA_INT32 || ctx->align_int32 || ctx->smin + ctx->o < 0) return false;
   const long long top = (long long)Lc * std::max(ctx->smax, 0) + std::max(ctx->smax, 0) + ctx->o;
   return top <= std::min(ctx->sat_limit, 32767);
 }
@@ -798,6 +798,8 @@ void msa_destroy(msa_ctx *ctx) {
   cudaFree(ctx->dSymLut);
   cudaFree(ctx->dcounter);
   if (ctx->center_exec) cudaGraphExecDestroy(ctx->center_exec);
+  if (ctx->align_exec) cudaGraphExecDestroy(ctx->align_exec);
+  for (cudaEvent_t ev : ctx->align_ev) cudaEventDestroy(ev);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   if (ctx->cap_st2) cudaStreamDestroy(ctx->cap_st2);
   if (ctx->cap_fork) cudaEventDestroy(ctx->cap_fork);
@@ -1134,36 +1136,90 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   float ms_dp = 0.f, ms_tb = 0.f;
   int64_t cells = 0;
   for (int k = 0; k < n; ++k) cells += (int64_t)Lc * ctx->len_sorted[k];
-  for (auto [sb, se] : batches) {
-    stage_begin(ctx, ST_ALIGN);
-    CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
-    CodesJob job;
-    job.center = kc;
-    job.sb = sb;
-    job.se = se;
-    job.code_off = P<int64_t>(ctx->code_off) + sb;
-    job.codes = P<uint8_t>(ctx->codes);
-    job.best = P<unsigned long long>(ctx->best) + sb;
-    job.npass = npass;
-    job.counter = ctx->dcounter;
-    job.scratch = P<int2>(ctx->scratch);
-    job.scratch_cols = ctx->maxlen;
-
-    // offsets inside the batch are relative to the batch start
-    CK((++ctx->launches, launch_codes)(G, packed, ss, sc, job, grid, ctx->st));
-    stage_end(ctx, ST_ALIGN);
-    stage_begin(ctx, ST_TRACE);
-    CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
-                        P<unsigned long long>(ctx->best) + sb, sb, se, P<int32_t>(ctx->d_len),
-                        P<int32_t>(ctx->d_perm), ss.res, ss.pstart, kc, sc.M, sc.K, sc.o, sc.e, Lc,
-                        P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->seg),
-                        P<int32_t>(ctx->score), ctx->derr, ctx->st));
-    stage_end(ctx, ST_TRACE);
-    CK(cudaStreamSynchronize(ctx->st));
-    stage_collect(ctx, ST_ALIGN);
-    stage_collect(ctx, ST_TRACE);
-    ms_dp += ctx->stage_ms[ST_ALIGN];
-    ms_tb += ctx->stage_ms[ST_TRACE];
+  // All batches as one CUDA graph (captured on the context's private stream,
+  // launched on its stream, cached while the key holds): per batch the fill
+  // and the traceback, with timing events, and no host round trip between
+  // batches (the codes buffer is reused in stream order).
+  const int nb = (int)batches.size();
+  while ((int)ctx->align_ev.size() < 3 * nb) {
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreate(&ev));
+    ctx->align_ev.push_back(ev);
+  }
+  std::vector<int64_t> key = {kc, Lc, packed, G, npass, grid, smem, n, (int64_t)ss.res,
+                              (int64_t)ss.pstart, (int64_t)ss.len, (int64_t)sc.M, sc.K, sc.o, sc.e,
+                              (int64_t)ctx->codes.p, (int64_t)ctx->code_off.p, (int64_t)ctx->best.p,
+                              (int64_t)ctx->ins.p, (int64_t)ctx->occ.p, (int64_t)ctx->seg.p,
+                              (int64_t)ctx->score.p, (int64_t)ctx->scratch.p, (int64_t)ctx->derr,
+                              (int64_t)ctx->dcounter, (int64_t)ctx->d_perm.p, ctx->maxlen};
+  for (auto [sb, se] : batches) { key.push_back(sb); key.push_back(se); }
+  CK(codes_allow_smem(G, packed, smem));
+  if (!ctx->align_exec || key != ctx->align_key) {
+    if (ctx->align_exec) {
+      CK(cudaStreamSynchronize(ctx->st));
+      cudaGraphExecDestroy(ctx->align_exec);
+      ctx->align_exec = nullptr;
+      ctx->align_key.clear();
+    }
+    CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int bi = 0; bi < nb && e == cudaSuccess; ++bi) {
+      const int sb = batches[bi].first, se = batches[bi].second;
+      CodesJob job;
+      job.center = kc;
+      job.sb = sb;
+      job.se = se;
+      job.code_off = P<int64_t>(ctx->code_off) + sb;
+      job.codes = P<uint8_t>(ctx->codes);
+      job.best = P<unsigned long long>(ctx->best) + sb;
+      job.npass = npass;
+      job.counter = ctx->dcounter;
+      job.scratch = P<int2>(ctx->scratch);
+      job.scratch_cols = ctx->maxlen;
+      e = cudaEventRecordWithFlags(ctx->align_ev[3 * bi], ctx->cap_st, cudaEventRecordExternal);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->cap_st);
+      // offsets inside the batch are relative to the batch start
+      if (e == cudaSuccess) e = launch_codes(G, packed, ss, sc, job, grid, ctx->cap_st, false);
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->align_ev[3 * bi + 1], ctx->cap_st, cudaEventRecordExternal);
+      if (e == cudaSuccess)
+        e = launch_traceback(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
+                             P<unsigned long long>(ctx->best) + sb, sb, se, P<int32_t>(ctx->d_len),
+                             P<int32_t>(ctx->d_perm), ss.res, ss.pstart, kc, sc.M, sc.K, sc.o, sc.e,
+                             Lc, P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->seg),
+                             P<int32_t>(ctx->score), ctx->derr, ctx->cap_st);
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->align_ev[3 * bi + 2], ctx->cap_st, cudaEventRecordExternal);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_st, &graph);
+    if (e == cudaSuccess) e = e_end;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    CK(e);
+    ctx->align_exec = exec;
+    ctx->align_key = key;
+  }
+  ctx->launches += 2 * nb;
+  stage_begin(ctx, ST_ALIGN);
+  CK(cudaGraphLaunch(ctx->align_exec, ctx->st));
+  stage_end(ctx, ST_ALIGN);
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_ALIGN);
+  bool split = true;
+  for (int bi = 0; bi < nb && split; ++bi) {
+    float a = 0.f, t = 0.f;
+    if (cudaEventElapsedTime(&a, ctx->align_ev[3 * bi], ctx->align_ev[3 * bi + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&t, ctx->align_ev[3 * bi + 1], ctx->align_ev[3 * bi + 2]) == cudaSuccess) {
+      ms_dp += a;
+      ms_tb += t;
+    } else {
+      cudaGetLastError();
+      split = false;
+    }
+  }
+  if (!split) {  // no per-batch split: the whole graph counts as the fill
+    ms_dp = ctx->stage_ms[ST_ALIGN];
+    ms_tb = 0.f;
   }
   ctx->stage_ms[ST_ALIGN] = ms_dp;
   ctx->stage_ms[ST_ALIGN_K] = ms_dp;
@@ -1232,7 +1288,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     job.counter = ctx->dcounter;
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
-    CK((++ctx->launches, launch_codes)(G, packed, seqset(ctx), scoring(ctx), job, grid, ctx->st));
+    CK((++ctx->launches, launch_codes)(G, packed, seqset(ctx), scoring(ctx), job, grid, ctx->st, true));
     std::vector<uint8_t> raw(bytes), out((size_t)Lc * Ls);
     CK(cudaMemcpyAsync(raw.data(), cb.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -1400,6 +1456,41 @@ int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out) {
 int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes) {
   if (!ctx || limit_bytes < 0) return MSA_EINVAL;
   ctx->dev_limit = (size_t)limit_bytes;
+  return MSA_OK;
+}
+
+int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t *choice_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (ctx->n == 0) return fail(ctx, MSA_ESTATE, "no sequences loaded");
+  if (center < 0 || center >= ctx->n) return fail(ctx, MSA_EINVAL, "center index out of range");
+  TRY(set_device(ctx));
+  const int Lc = ctx->len_sorted[ctx->inv[center]];
+  ctx->align_int32 = 0;
+  const bool can_pack = codes_packed(ctx, Lc);
+  double rates[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  double best = -1.0;
+  int best_g = 32, best_i32 = 0;
+  for (int i32 = 0; i32 < 2; ++i32) {
+    if (i32 == 0 && !can_pack) continue;
+    for (int gi = 0; gi < 3; ++gi) {
+      const int G = 8 << gi;
+      ctx->align_int32 = i32;
+      ctx->align_group = G;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the second run is timed
+        TRY(msa_align_to_center(ctx, center, nullptr));
+        ms = ctx->stage_ms[ST_ALIGN_K] + ctx->stage_ms[ST_TRACE];
+      }
+      const double r = ms > 0.f ? (double)ctx->cells[1] / (ms * 1e-3) : 0.0;
+      rates[i32][gi] = r;
+      if (r > best) { best = r; best_g = G; best_i32 = i32; }
+    }
+  }
+  ctx->align_group = best_g;
+  ctx->align_int32 = best_i32;
+  ctx->aligned = false;
+  if (rates_out) memcpy(rates_out, rates, sizeof rates);
+  if (choice_out) { choice_out[0] = best_g; choice_out[1] = best_i32 ? 0 : 1; }
   return MSA_OK;
 }
 

@@ -62,6 +62,9 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
                             int Lc, uint16_t *__restrict__ ins, uint8_t *__restrict__ occ,
                             int32_t *__restrict__ seg, int32_t *__restrict__ score,
                             unsigned *err) {
+  __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
+  for (int i = threadIdx.x; i < K * K; i += blockDim.x) sM[i] = M[i];
+  __syncthreads();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= se - sb) return;
   const int k = sb + x;
@@ -93,7 +96,7 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
         if (v < 0) break;
         const uint32_t src = code_at(c, Ls, i, j) & 3u;
         if (src == 1) {
-          v -= M[rc[i - 1] * K + rs[j - 1]];
+          v -= sM[rc[i - 1] * K + rs[j - 1]];
           oc[i] = 1; --i; --j;
         } else if (src == 0) {
           break;  // a positive score with no source: inconsistent codes

@@ -1157,13 +1157,22 @@ int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_
   return best_g;
 }
 
+cudaError_t codes_allow_smem(int G, bool packed, int smem) {
+  codes_fn fn = codes_kernel(G, packed);
+  if (!fn) return cudaErrorInvalidValue;
+  if (smem <= 40 * 1024) return cudaSuccess;  // static shared memory counts too
+  return cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc, const CodesJob &job,
-                         int grid, cudaStream_t st) {
+                         int grid, cudaStream_t st, bool set_smem) {
   codes_fn fn = codes_kernel(G, packed);
   if (!fn) return cudaErrorInvalidValue;
   const int smem = codes_smem_bytes(sc.K, job.npass * G * kCodesR);
-  if (smem > 40 * 1024)  // static shared memory counts too
-    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (set_smem) {
+    const cudaError_t e = codes_allow_smem(G, packed, smem);
+    if (e != cudaSuccess) return e;
+  }
   fn<<<grid, codes_threads(packed), smem, st>>>(ss, sc, job);
   return cudaGetLastError();
 }

@@ -90,8 +90,11 @@ int pairs_rows(int G);
 // G = threads per subject group (8, 16 or 32; codes_group picks it from the
 // center length and the subject lengths); 16 center rows per thread.  packed: each group carries two
 // subjects in int16 lanes (the caller checks that every cell value fits).
+// set_smem = false: the caller has already raised the kernel's dynamic
+// shared-memory limit with codes_allow_smem (required while capturing).
 cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc, const CodesJob &job,
-                         int grid, cudaStream_t st);
+                         int grid, cudaStream_t st, bool set_smem = true);
+cudaError_t codes_allow_smem(int G, bool packed, int smem);
 int codes_smem_bytes(int K, int rows_alloc);
 int codes_grid(int G, bool packed, int smem);
 int codes_threads(bool packed);  // threads per CTA of the codes kernels

@@ -323,6 +323,21 @@ def test_autotuned_selection_is_unchanged():
     assert (rows == orow).all() and c == oc
 
 
+def test_autotuned_alignment_is_unchanged():
+    """The alignment tuner times every group width in packed and int32 cells
+    and keeps the fastest; the MSA is the oracle's whatever it keeps."""
+    b = binding()
+    letters, offsets, w, alph, M = workload("batched_uneven_10k", n=120, seed=14)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    center = 11
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        rates, (lanes, packed) = b.msa_align_autotune(h, center)
+        out = run_pipeline(b, h, letters, offsets, center)
+    assert (rates > 0).sum() == 6 and lanes in (8, 16, 32)
+    check_against_oracle(prob, center, *out)
+
+
 def test_short_peptides_against_their_center():
     """Peptides cut from a 500-residue ancestor (which is sequence 0):
     sampled exact center (240 references: enough work that the short
