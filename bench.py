@@ -48,6 +48,11 @@ ALU_PEAK_GCUPS = SMS * INT_LANES * MAX_GHZ / OPS_PER_CELL
 CODES_SLOTS_PER_CELL = 3 * 2 + 4
 CODES_PEAK_GCUPS = SMS * 2 * INT_LANES * MAX_GHZ / CODES_SLOTS_PER_CELL
 CODES_BYTES_PER_CELL = 0.5   # 4-bit traceback code per cell written to HBM
+# DRAM bytes read + written per cell by the codes kernel, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum = 75.4 + 522.7 MB for 1.007e9
+# cells of 20,000 peptides against the 500-residue center); the traffic grows
+# with the cells, so a launch's traffic is this times its cells
+CODES_TRAFFIC_PER_CELL = (75.4e6 + 522.7e6) / 1.006925e9
 ALIGN_WORKLOAD, ALIGN_N = "short_peptides_1m", 200_000
 # the library's center kernel variants, in msa_autotune's column order:
 # (two queries per int16x2 register?, lanes per group, query rows per lane, packed)
@@ -313,7 +318,10 @@ def align_record(flush, stream, peak_gbs, no_tune=False):
             "roofline": {"bound": "alu", "kernel": "k_codes2 (Gotoh fill + 4-bit traceback codes, "
                                                   "two subjects per int16x2 register)",
                          "achieved": gcups, "peak": CODES_PEAK_GCUPS, "unit": UNIT,
-                         "frac": gcups / CODES_PEAK_GCUPS, "traffic": None,
+                         "frac": gcups / CODES_PEAK_GCUPS,
+                         "traffic": cells * CODES_TRAFFIC_PER_CELL,
+                         "traffic_note": "bytes per launch, the ncu per-cell DRAM traffic of "
+                                         "20,000 peptides scaled to this launch's cells",
                          "peak_source": "152 SMs x 128 integer lanes/clk x 2.07 GHz / (3 DPX "
                                         "instructions at half rate + 4 two-operand ops) per cell",
                          "hbm_bound_gcups": peak_gbs / CODES_BYTES_PER_CELL,
