@@ -61,6 +61,10 @@ def lib():
                                          ctypes.c_int]
         L.orc_exact_center.restype = i64
         L.orc_exact_center.argtypes = [P, P, i64, P, i64, P, i32, i32, i32, P, ctypes.c_int]
+        L.orc_anchored.restype = ctypes.c_int
+        L.orc_anchored.argtypes = [P, i32, P, i32, P, i32, i32, i32, i32, P, P, P]
+        L.orc_anchored_all.restype = ctypes.c_int
+        L.orc_anchored_all.argtypes = [P, P, i64, i64, P, i32, i32, i32, i32, P, P, P, ctypes.c_int]
         L.orc_default_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -223,6 +227,36 @@ def center_rowsums(prob, cands, refs=None, threads=0):
     if rc != 0:
         raise MemoryError("oracle center row sums")
     return out
+
+
+def anchored(c, x, M, o, e, k):
+    """Anchored alignment of x to the center c (the trie path for similar
+    sequences): (ins uint16[Lc+1], occ uint8[Lc+1], seg (score, i1, j1, i2, j2))."""
+    c = np.ascontiguousarray(c, dtype=np.uint8)
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    M = np.ascontiguousarray(M, dtype=np.int8)
+    ins = np.zeros(c.size + 1, dtype=np.uint16)
+    occ = np.zeros(c.size + 1, dtype=np.uint8)
+    seg = np.zeros(5, dtype=np.int32)
+    rc = lib().orc_anchored(_p(c), c.size, _p(x), x.size, _p(M), M.shape[0], o, e, k,
+                            _p(ins), _p(occ), _p(seg))
+    if rc != 0:
+        raise RuntimeError("oracle anchored alignment failed")
+    return ins, occ, tuple(int(v) for v in seg)
+
+
+def anchored_all(prob, center, k, threads=0):
+    """Every row aligned to the center by the anchored path: (seg, ins, occ)."""
+    lc = prob.length(center)
+    ins = np.zeros((prob.n, lc + 1), dtype=np.uint16)
+    occ = np.zeros((prob.n, lc + 1), dtype=np.uint8)
+    seg = np.zeros((prob.n, 5), dtype=np.int32)
+    rc = lib().orc_anchored_all(_p(prob.res), _p(prob.off), prob.n, int(center), _p(prob.M),
+                                prob.K, prob.o, prob.e, int(k), _p(ins), _p(occ), _p(seg),
+                                threads)
+    if rc != 0:
+        raise RuntimeError("oracle anchored alignment failed")
+    return seg, ins, occ
 
 
 def msa(prob, center, threads=0):

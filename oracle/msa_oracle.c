@@ -432,3 +432,194 @@ int64_t orc_exact_center(const uint8_t *res, const int64_t *off, int64_t n,
     if (!rowsum) free(rs);
     return bestc;
 }
+
+/* ====================================================================== */
+/*
+ * Anchored alignment of similar sequences (the paper's trie path for similar
+ * nucleotides: the center's segments are indexed, matched segments of the
+ * other sequence are skipped and only the unmatched stretches are aligned).
+ * Reading:
+ *   - segments: the center cut into S = floor(Lc / k) non-overlapping pieces
+ *     c[s k .. s k + k), s = 0..S-1 (a shorter tail is no segment);
+ *   - matches: every (s, p) with x[p .. p + k) equal to segment s;
+ *   - chain: matches (s_1, p_1), ..., (s_T, p_T) with s increasing and
+ *     p_{t+1} >= p_t + k, as many as possible; matches are ordered by (s, p)
+ *     and each takes as predecessor the first compatible match (in that
+ *     order) of the longest chain ending before it; the chain ends at the
+ *     first match of the longest chain;
+ *   - between consecutive anchors the unmatched stretches of the center and
+ *     of the sequence are aligned globally (Gotoh with W_k = o + (k-1)e, the
+ *     end cells' gap runs charged from the stretch's edge, traceback from the
+ *     end: diagonal, then F, then E; a gap extends only when strictly
+ *     better);
+ *   - before the first anchor and after the last the flank rule of the local
+ *     path applies (prefix right-aligned, suffix left-aligned, no gaps,
+ *     surplus sequence residues in slot 0 / slot Lc);
+ *   - no anchor: the Smith-Waterman alignment (orc_sw + orc_traceback).
+ * Output as orc_traceback's: ins[0..Lc], occ[0..Lc]; seg = {score, i1, j1,
+ * i2, j2} with the anchored region c[i1+1..i2] x x[j1+1..j2] (first anchor's
+ * start to last anchor's end) and score its affine score, or the
+ * Smith-Waterman segment when there is no anchor.  Returns 0, -1 on error.
+ */
+
+/* Global affine alignment of c[0..lc) with x[0..lx); adds its columns to
+ * ins/occ at center offset a (c[i] is center residue a+i+1) and returns the
+ * score (INT32_MIN on error). */
+static int32_t orc_global_stretch(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
+                                  const int8_t *M, int32_t K, int32_t o, int32_t e,
+                                  int32_t a, uint16_t *ins, uint8_t *occ)
+{
+    if (lc == 0 && lx == 0) return 0;
+    size_t w = (size_t)lx + 1, cells = ((size_t)lc + 1) * w;
+    int32_t *H = malloc(cells * sizeof(int32_t));
+    int32_t *E = malloc(cells * sizeof(int32_t));
+    int32_t *F = malloc(cells * sizeof(int32_t));
+    if (!H || !E || !F) { free(H); free(E); free(F); return INT32_MIN; }
+    H[0] = 0; E[0] = ORC_NEG; F[0] = ORC_NEG;
+    for (int32_t j = 1; j <= lx; j++) {       /* x residues against gaps */
+        E[j] = -(o + (j - 1) * e); H[j] = E[j]; F[j] = ORC_NEG;
+    }
+    for (int32_t i = 1; i <= lc; i++) {       /* c residues against gaps */
+        size_t at = (size_t)i * w;
+        F[at] = -(o + (i - 1) * e); H[at] = F[at]; E[at] = ORC_NEG;
+        for (int32_t j = 1; j <= lx; j++) {
+            at = (size_t)i * w + j;
+            E[at] = max2(H[at - 1] - o, E[at - 1] - e);
+            F[at] = max2(H[at - w] - o, F[at - w] - e);
+            H[at] = max2(H[at - w - 1] + M[c[i - 1] * K + x[j - 1]], max2(E[at], F[at]));
+        }
+    }
+    int32_t score = H[(size_t)lc * w + lx];
+    int32_t i = lc, j = lx, state = 0;  /* 0 = H, 1 = F (c residue vs gap), 2 = E (x residue inserted) */
+    while (i > 0 || j > 0) {
+        size_t at = (size_t)i * w + j;
+        if (state == 0) {
+            if (i == 0) state = 2;
+            else if (j == 0) state = 1;
+            else {
+                int32_t dv = H[at - w - 1] + M[c[i - 1] * K + x[j - 1]];
+                if (H[at] == dv) { occ[a + i] = 1; i--; j--; continue; }
+                state = H[at] == F[at] ? 1 : 2;
+            }
+        }
+        if (state == 1) {                     /* F(i,j): from F(i-1,j) - e or H(i-1,j) - o */
+            int ext = i > 1 && F[at - w] - e > H[at - w] - o;
+            if (j == 0) ext = i > 1;          /* the edge column is one gap run */
+            i--;
+            state = ext ? 1 : 0;
+        } else {                              /* E(i,j): from E(i,j-1) - e or H(i,j-1) - o */
+            int ext = j > 1 && E[at - 1] - e > H[at - 1] - o;
+            if (i == 0) ext = j > 1;          /* the edge row is one gap run */
+            ins[a + i]++;
+            j--;
+            state = ext ? 2 : 0;
+        }
+    }
+    free(H); free(E); free(F);
+    return score;
+}
+
+int orc_anchored(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
+                 const int8_t *M, int32_t K, int32_t o, int32_t e, int32_t k,
+                 uint16_t *ins, uint8_t *occ, int32_t *seg)
+{
+    memset(ins, 0, sizeof(uint16_t) * ((size_t)lc + 1));
+    memset(occ, 0, (size_t)lc + 1);
+    int32_t S = k > 0 ? lc / k : 0;
+    /* matches in (s, p) order */
+    int64_t cap = 16, nm = 0;
+    int32_t *ms = malloc(sizeof(int32_t) * cap), *mp = malloc(sizeof(int32_t) * cap);
+    if (!ms || !mp) { free(ms); free(mp); return -1; }
+    for (int32_t s = 0; s < S; s++)
+        for (int32_t p = 0; p + k <= lx; p++) {
+            if (memcmp(c + (size_t)s * k, x + p, (size_t)k) != 0) continue;
+            if (nm == cap) {
+                cap *= 2;
+                int32_t *a1 = realloc(ms, sizeof(int32_t) * cap), *a2 = realloc(mp, sizeof(int32_t) * cap);
+                if (!a1 || !a2) { free(a1 ? a1 : ms); free(a2 ? a2 : mp); return -1; }
+                ms = a1; mp = a2;
+            }
+            ms[nm] = s; mp[nm] = p; nm++;
+        }
+    if (nm == 0) {                            /* no anchor: the local path */
+        free(ms); free(mp);
+        uint8_t *codes = malloc((size_t)lc * lx + 1);
+        int32_t end[2];
+        if (!codes) return -1;
+        int32_t best = orc_sw(c, lc, x, lx, M, K, o, e, codes, end);
+        int rc = best < 0 ? -1 : orc_traceback(codes, lc, lx, best, end[0], end[1], ins, occ, seg + 1);
+        seg[0] = best;
+        free(codes);
+        return rc;
+    }
+    /* longest chain: len[m] = 1 + len of the first compatible predecessor of
+     * the longest chains before it */
+    int32_t *len = malloc(sizeof(int32_t) * nm), *pred = malloc(sizeof(int32_t) * nm);
+    if (!len || !pred) { free(ms); free(mp); free(len); free(pred); return -1; }
+    int64_t endm = 0;
+    for (int64_t m = 0; m < nm; m++) {
+        len[m] = 1; pred[m] = -1;
+        for (int64_t q = 0; q < m; q++)
+            if (ms[q] < ms[m] && mp[q] + k <= mp[m] && len[q] + 1 > len[m]) {
+                len[m] = len[q] + 1; pred[m] = (int32_t)q;
+            }
+        if (len[m] > len[endm]) endm = m;
+    }
+    int32_t T = len[endm];
+    int32_t *cs = malloc(sizeof(int32_t) * T), *cp = malloc(sizeof(int32_t) * T);
+    if (!cs || !cp) { free(ms); free(mp); free(len); free(pred); free(cs); free(cp); return -1; }
+    for (int64_t m = endm, t = T - 1; m >= 0; m = pred[m], t--) { cs[t] = ms[m]; cp[t] = mp[m]; }
+    int32_t score = 0;
+    for (int32_t t = 0; t < T; t++) {
+        int32_t ca = cs[t] * k, xa = cp[t];   /* anchor t: c[ca..ca+k) = x[xa..xa+k) */
+        for (int32_t u = 0; u < k; u++) { occ[ca + u + 1] = 1; score += M[c[ca + u] * K + x[xa + u]]; }
+        if (t + 1 < T) {                      /* the stretch up to the next anchor */
+            int32_t cb = ca + k, xb = xa + k, ce = cs[t + 1] * k, xe = cp[t + 1];
+            int32_t v = orc_global_stretch(c + cb, ce - cb, x + xb, xe - xb, M, K, o, e, cb, ins, occ);
+            if (v == INT32_MIN) { score = INT32_MIN; break; }
+            score += v;
+        }
+    }
+    int32_t i1 = cs[0] * k, j1 = cp[0], i2 = cs[T - 1] * k + k, j2 = cp[T - 1] + k;
+    free(ms); free(mp); free(len); free(pred); free(cs); free(cp);
+    if (score == INT32_MIN) return -1;
+    /* flanks as on the local path */
+    int32_t kk = i1 < j1 ? i1 : j1;
+    for (int32_t t = 0; t < kk; t++) occ[i1 - t] = 1;
+    if (j1 > i1) ins[0] += (uint16_t)(j1 - i1);
+    int32_t ra = lc - i2, rb = lx - j2;
+    kk = ra < rb ? ra : rb;
+    for (int32_t t = 1; t <= kk; t++) occ[i2 + t] = 1;
+    if (rb > ra) ins[lc] += (uint16_t)(rb - ra);
+    seg[0] = score; seg[1] = i1; seg[2] = j1; seg[3] = i2; seg[4] = j2;
+    return 0;
+}
+
+typedef struct {
+    orc_seqs q; int64_t center; int32_t lc, k;
+    uint16_t *ins; uint8_t *occ; int32_t *seg; atomic_int err;
+} anchored_job;
+
+static void anchored_task(void *ctx, int64_t t)
+{
+    anchored_job *j = ctx;
+    const orc_seqs *q = &j->q;
+    const uint8_t *c = q->res + q->off[j->center];
+    const uint8_t *s = q->res + q->off[t];
+    int32_t ls = (int32_t)(q->off[t + 1] - q->off[t]);
+    if (orc_anchored(c, j->lc, s, ls, q->M, q->K, q->o, q->e, j->k,
+                     j->ins + (size_t)t * (j->lc + 1), j->occ + (size_t)t * (j->lc + 1),
+                     j->seg + 5 * t) != 0)
+        atomic_store(&j->err, 1);
+}
+
+/* Every sequence aligned to the center by orc_anchored (rows as orc_align_all). */
+int orc_anchored_all(const uint8_t *res, const int64_t *off, int64_t n, int64_t center,
+                     const int8_t *M, int32_t K, int32_t o, int32_t e, int32_t k,
+                     uint16_t *ins, uint8_t *occ, int32_t *seg, int threads)
+{
+    anchored_job j = { { res, off, M, K, o, e }, center,
+                       (int32_t)(off[center + 1] - off[center]), k, ins, occ, seg, 0 };
+    orc_parallel_for(n, threads, anchored_task, &j);
+    return atomic_load(&j.err) ? -1 : 0;
+}

@@ -36,6 +36,20 @@ MUTATIONS = {
 }
 
 
+# mistakes in the anchored alignment (the trie path), caught by
+# tests/test_oracle_anchored.py
+ANCHORED_MUTATIONS = {
+    "chain_last_predecessor": ("mp[q] + k <= mp[m] && len[q] + 1 > len[m]",
+                               "mp[q] + k <= mp[m] && len[q] + 1 >= len[m]"),
+    "anchors_may_overlap": ("mp[q] + k <= mp[m] && len[q] + 1 > len[m]",
+                            "mp[q] <= mp[m] && len[q] + 1 > len[m]"),
+    "stretch_F_before_diagonal": ("if (H[at] == dv) { occ[a + i] = 1; i--; j--; continue; }",
+                                  "if (H[at] == dv && H[at] != F[at]) { occ[a + i] = 1; i--; j--; continue; }"),
+    "stretch_edge_gap_uncharged_open": ("F[at] = -(o + (i - 1) * e); H[at] = F[at]; E[at] = ORC_NEG;",
+                                        "F[at] = -(i * e); H[at] = F[at]; E[at] = ORC_NEG;"),
+}
+
+
 # mistakes in the fp64 network oracle, caught by tests/test_net_oracle.py
 NET_MUTATIONS = {
     "pool_drops_scale": ("dy4 = np.tile(de / np.sqrt(L), (L, 1))", "dy4 = np.tile(de, (L, 1))"),
@@ -63,6 +77,12 @@ def _run_mutated(tmp_path, rel_src, old, new, pins, name):
 def test_planted_mistake_is_caught(name, tmp_path):
     old, new = MUTATIONS[name]
     _run_mutated(tmp_path, "oracle/msa_oracle.c", old, new, "tests/test_oracle_pins.py", name)
+
+
+@pytest.mark.parametrize("name", sorted(ANCHORED_MUTATIONS))
+def test_planted_anchored_mistake_is_caught(name, tmp_path):
+    old, new = ANCHORED_MUTATIONS[name]
+    _run_mutated(tmp_path, "oracle/msa_oracle.c", old, new, "tests/test_oracle_anchored.py", name)
 
 
 @pytest.mark.parametrize("name", sorted(NET_MUTATIONS))
