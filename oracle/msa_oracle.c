@@ -586,7 +586,7 @@ int orc_anchored(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
     /* flanks as on the local path */
     int32_t kk = i1 < j1 ? i1 : j1;
     for (int32_t t = 0; t < kk; t++) occ[i1 - t] = 1;
-    if (j1 > i1) ins[0] += (uint16_t)(j1 - i1);
+    if (j1 > i1) ins[0] = (uint16_t)(ins[0] + (j1 - i1));
     int32_t ra = lc - i2, rb = lx - j2;
     kk = ra < rb ? ra : rb;
     for (int32_t t = 1; t <= kk; t++) occ[i2 + t] = 1;
