@@ -196,6 +196,36 @@ int msa_center_combine(msa_ctx *ctx, const uint64_t *sums, int64_t nref, int64_t
  * device int32[n]. */
 int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out);
 
+/* Align every loaded sequence to `center` by anchors (the paper's trie path
+ * for similar nucleotides, Methods: the center's segments are indexed,
+ * matched segments of each sequence are skipped and only the unmatched
+ * stretches are aligned).  The center is cut into floor(Lc / k)
+ * non-overlapping segments of k residues; every exact occurrence of a
+ * segment in a sequence is a match; the anchors are the longest chain of
+ * matches with increasing segment and sequence positions at least k apart
+ * (matches ordered by (segment, position); each takes the first compatible
+ * match of the longest chains before it as predecessor; the chain ends at
+ * the first longest); the stretches between consecutive anchors are aligned
+ * globally (Gotoh with W as in msa_params, traceback from the end: diagonal,
+ * then center residue vs gap, then inserted residue; a gap extends only when
+ * strictly better); the residues before the first and after the last anchor
+ * follow msa_align_to_center's flank rule.  A sequence with no match, with
+ * more matches than the smallest power of two >= max(64, 2 * segments), or
+ * with a stretch between consecutive anchors longer than 80 residues on
+ * either side is aligned by msa_align_to_center's Smith-Waterman path
+ * instead.  The results are read
+ * as after msa_align_to_center (msa_alignment_info, msa_merge_gaps, ...);
+ * seg = {score of the anchored region, i1, j1, i2, j2} with the region
+ * center[i1+1..i2] x seq[j1+1..j2] from the first anchor's start to the last
+ * anchor's end.  k: 1 .. 64 / ceil(log2(alphabet)) (32 for DNA, 12 for
+ * proteins); ERANGE when the segments' tables do not fit shared memory
+ * (about 2,700 segments).
+ * scores_out: nullable, host or device int32[n]; fallback_out: nullable,
+ * host int64, the number of sequences the local path aligned.  ERANGE for a
+ * sequence of 8192 residues or more. */
+int msa_align_anchored(msa_ctx *ctx, int64_t center, int32_t k, int32_t *scores_out,
+                       int64_t *fallback_out);
+
 /* Results of the last msa_align_to_center, each nullable, host or device:
  *   seg_out int32[n][5] = {score, i1, j1, i2, j2}: the local segment is
  *     center[i1+1..i2] x seq[j1+1..j2] (all 0 when the score is 0);

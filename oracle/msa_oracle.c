@@ -455,7 +455,13 @@ int64_t orc_exact_center(const uint8_t *res, const int64_t *off, int64_t n,
  *   - before the first anchor and after the last the flank rule of the local
  *     path applies (prefix right-aligned, suffix left-aligned, no gaps,
  *     surplus sequence residues in slot 0 / slot Lc);
- *   - no anchor: the Smith-Waterman alignment (orc_sw + orc_traceback).
+ *   - the local path instead (the Smith-Waterman alignment, orc_sw +
+ *     orc_traceback) when there is no match, when there are more matches
+ *     than ORC_ANCH_CAP(S) = the smallest power of two >= max(64, 2 S), or
+ *     when a stretch between consecutive anchors is longer than
+ *     ORC_ANCH_BOX = 80 residues on either side (the anchored path aligns
+ *     only short unmatched stretches; longer ones are left to the local
+ *     alignment of the whole pair).
  * Output as orc_traceback's: ins[0..Lc], occ[0..Lc]; seg = {score, i1, j1,
  * i2, j2} with the anchored region c[i1+1..i2] x x[j1+1..j2] (first anchor's
  * start to last anchor's end) and score its affine score, or the
@@ -519,6 +525,29 @@ static int32_t orc_global_stretch(const uint8_t *c, int32_t lc, const uint8_t *x
     return score;
 }
 
+#define ORC_ANCH_BOX 80
+
+static int64_t orc_anch_cap(int32_t S)
+{
+    int64_t cap = 64;
+    while (cap < 2 * (int64_t)S) cap *= 2;
+    return cap;
+}
+
+static int orc_local_row(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
+                         const int8_t *M, int32_t K, int32_t o, int32_t e,
+                         uint16_t *ins, uint8_t *occ, int32_t *seg)
+{
+    uint8_t *codes = malloc((size_t)lc * lx + 1);
+    int32_t end[2];
+    if (!codes) return -1;
+    int32_t best = orc_sw(c, lc, x, lx, M, K, o, e, codes, end);
+    int rc = best < 0 ? -1 : orc_traceback(codes, lc, lx, best, end[0], end[1], ins, occ, seg + 1);
+    seg[0] = best;
+    free(codes);
+    return rc;
+}
+
 int orc_anchored(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
                  const int8_t *M, int32_t K, int32_t o, int32_t e, int32_t k,
                  uint16_t *ins, uint8_t *occ, int32_t *seg)
@@ -541,16 +570,9 @@ int orc_anchored(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
             }
             ms[nm] = s; mp[nm] = p; nm++;
         }
-    if (nm == 0) {                            /* no anchor: the local path */
+    if (nm == 0 || nm > orc_anch_cap(S)) {   /* no anchor, or too many matches: the local path */
         free(ms); free(mp);
-        uint8_t *codes = malloc((size_t)lc * lx + 1);
-        int32_t end[2];
-        if (!codes) return -1;
-        int32_t best = orc_sw(c, lc, x, lx, M, K, o, e, codes, end);
-        int rc = best < 0 ? -1 : orc_traceback(codes, lc, lx, best, end[0], end[1], ins, occ, seg + 1);
-        seg[0] = best;
-        free(codes);
-        return rc;
+        return orc_local_row(c, lc, x, lx, M, K, o, e, ins, occ, seg);
     }
     /* longest chain: len[m] = 1 + len of the first compatible predecessor of
      * the longest chains before it */
@@ -569,6 +591,11 @@ int orc_anchored(const uint8_t *c, int32_t lc, const uint8_t *x, int32_t lx,
     int32_t *cs = malloc(sizeof(int32_t) * T), *cp = malloc(sizeof(int32_t) * T);
     if (!cs || !cp) { free(ms); free(mp); free(len); free(pred); free(cs); free(cp); return -1; }
     for (int64_t m = endm, t = T - 1; m >= 0; m = pred[m], t--) { cs[t] = ms[m]; cp[t] = mp[m]; }
+    for (int32_t t = 0; t + 1 < T; t++)      /* a long stretch: the local path */
+        if (cs[t + 1] * k - (cs[t] * k + k) > ORC_ANCH_BOX || cp[t + 1] - (cp[t] + k) > ORC_ANCH_BOX) {
+            free(ms); free(mp); free(len); free(pred); free(cs); free(cp);
+            return orc_local_row(c, lc, x, lx, M, K, o, e, ins, occ, seg);
+        }
     int32_t score = 0;
     for (int32_t t = 0; t < T; t++) {
         int32_t ca = cs[t] * k, xa = cp[t];   /* anchor t: c[ca..ca+k) = x[xa..xa+k) */

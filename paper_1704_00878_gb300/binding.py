@@ -54,6 +54,8 @@ _SIGS = {
     "msa_select_center_refined": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_center_rowsums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_align_anchored": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "msa_align_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "msa_center_partial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -237,6 +239,15 @@ def msa_select_center_refined(ctx, candidates=0, refs=None):
     _check(ctx, lib().msa_select_center_refined(ctx, int(candidates), _ptr(r),
                                                 0 if r is None else r.size, _ptr(c), _ptr(s)))
     return int(c[0]), int(s[0])
+
+
+def msa_align_anchored(ctx, center, k, scores=None):
+    """Anchored alignment to `center` (segments of k residues); returns the
+    number of sequences the Smith-Waterman path aligned instead."""
+    fb = ctypes.c_int64(0)
+    _check(ctx, lib().msa_align_anchored(ctx, int(center), int(k), _ptr(scores),
+                                         ctypes.byref(fb)))
+    return int(fb.value)
 
 
 def msa_align_autotune(ctx, center):

@@ -132,6 +132,11 @@ int run_center(msa_ctx *ctx, int mode, const std::vector<int32_t> &qsorted,
                const SetView *view = nullptr, int q_begin = 0, int q_end = -1);
 // the device error word -> an MSA_E* code (synchronises the stream)
 int check_derr(msa_ctx *ctx);
+// cell precision and lanes per group of the alignment to a center of length Lc
+bool align_packed(msa_ctx *ctx, int Lc);
+int align_lanes(msa_ctx *ctx, int Lc, bool packed);
+SeqSet seqset(msa_ctx *ctx);
+Scoring scoring(msa_ctx *ctx);
 
 }  // namespace msa_detail
 

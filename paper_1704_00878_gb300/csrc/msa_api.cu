@@ -225,6 +225,9 @@ static int align_group(msa_ctx *ctx, int Lc, bool packed) {
   return codes_group(Lc, packed, ctx->K, ctx->n, ctx->n ? total / ctx->n : 0.0, ctx->maxlen);
 }
 
+bool align_packed(msa_ctx *ctx, int Lc) { return codes_packed(ctx, Lc); }
+int align_lanes(msa_ctx *ctx, int Lc, bool packed) { return align_group(ctx, Lc, packed); }
+
 bool use_packed(msa_ctx *ctx, int Lq) {
   if (ctx->precision == MSA_INT32 || ctx->smin + ctx->o < 0) return false;
   if (ctx->precision == MSA_INT16) return true;
