@@ -104,9 +104,13 @@ def parse():
                     help="time selector training steps alone (256 pairs per step; profiling cases)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-center comparison")
-    ap.add_argument("--center", default="exact", choices=["exact", "sampled"],
-                    help="exact all-pairs center, or the sampled exact center over 1,000 "
-                         "seeded references (the larger workloads)")
+    ap.add_argument("--center", default="exact", choices=["exact", "sampled", "first"],
+                    help="exact all-pairs center, the sampled exact center over 1,000 "
+                         "seeded references (the larger workloads), or the first sequence "
+                         "(the paper's center for similar nucleotides)")
+    ap.add_argument("--anchored", type=int, default=0, metavar="K",
+                    help="with --only-align: time the anchored path for similar sequences "
+                         "(K-residue center segments) beside the Smith-Waterman path")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuners (center variants per length bucket; alignment "
                          "group width and int16x2 / int32 cells) and use the cost models")
@@ -440,7 +444,7 @@ def run_ours(args):
     center_mode = b.MSA_CENTER_EXACT_SAMPLED if refs is not None else b.MSA_CENTER_EXACT
 
     def select_exact():
-        if w.center_seq:  # the workload names its center: the 500-residue ancestor
+        if w.center_seq or args.center == "first":  # a named center, or the first sequence
             return 0, 0
         return b.msa_select_center(h, center_mode, refs)
 
@@ -508,8 +512,54 @@ def run_ours(args):
         b.msa_set_align_group(h, args.align_group)
     if args.only_align:
         lens = np.diff(offsets)
-        center = 0 if w.center_seq else int(np.argsort(lens, kind="stable")[len(lens) // 2])
+        center = 0 if (w.center_seq or args.center == "first") else \
+            int(np.argsort(lens, kind="stable")[len(lens) // 2])
         b.msa_load(h, dlet, offsets)
+        if args.anchored:
+            # the anchored path against the Smith-Waterman path, same center: the
+            # alignment alone, and the whole MSA (alignment + merged rows + SP)
+            rows = {}
+
+            def run(align_fn):
+                out = {}
+                for _ in range(max(1, args.warmup)):
+                    align_fn()
+                    _, W = b.msa_merge_gaps(h, want_rows=False)
+                    if rows.get("W") != W:
+                        rows.clear()
+                        rows.update(W=W, buf=torch.empty((n, W), dtype=torch.uint8,
+                                                         device="cuda"))
+                t_al, t_msa = [], []
+                for _ in range(3):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    ev[0].record(stream)
+                    r = align_fn()
+                    ev[1].record(stream)
+                    _, W = b.msa_merge_gaps(h, want_rows=False)
+                    if rows["W"] != W:
+                        raise SystemExit("alignment width changed between runs")
+                    b.msa_merge_gaps(h, out=rows["buf"])
+                    sp = b.msa_sp_score(h)
+                    ev[2].record(stream)
+                    torch.cuda.synchronize()
+                    t_al.append(ev[0].elapsed_time(ev[1]))
+                    t_msa.append(ev[0].elapsed_time(ev[2]))
+                out.update(align_ms=float(np.median(t_al)), msa_ms=float(np.median(t_msa)),
+                           msa_width=W, avg_sp=sp / (n * (n - 1) / 2))
+                return r, out
+
+            nf, rec_a = run(lambda: b.msa_align_anchored(h, center, args.anchored))
+            _, rec_s = run(lambda: b.msa_align_to_center(h, center))
+            print(json.dumps({"only_align": True, "n": n, "center": center,
+                              "Lc": int(lens[center]), "k": args.anchored,
+                              "residues": int(lens.sum()),
+                              "full_matrix_cells": int(lens[center]) * int(lens.sum()),
+                              "anchored": dict(rec_a, local_path_sequences=nf),
+                              "smith_waterman": rec_s}))
+            ctx.close()
+            return
         for _ in range(max(1, args.warmup)):
             b.msa_align_to_center(h, center)
         ms, cnt = b.msa_stage_times(h)
