@@ -310,8 +310,9 @@ def align_record(flush, stream, peak_gbs, no_tune=False):
     if tune is not None:
         rates, (lanes, packed) = tune
         tuned = {"choice": {"lanes": lanes, "cells": "int16x2" if packed else "int32"},
-                 "gcups": {"%s_G%d" % (p, 8 << g): float(rates[i, g]) / 1e9
-                           for i, p in enumerate(("int16x2", "int32")) for g in range(3)
+                 "gcups": {"%s_G%d" % (p, G): float(rates[i, g]) / 1e9
+                           for i, p in enumerate(("int16x2", "int32"))
+                           for g, G in enumerate(b.ALIGN_LANES)
                            if rates[i, g] > 0}}
     return {"autotune": tuned, "workload": "%d short peptides (lognormal lengths median 90 sigma 0.6 clipped 30-200, "
                         "one family at 30%% substitutions, 3%% indels) against their %d-residue "
@@ -620,8 +621,9 @@ def run_ours(args):
         c0, _, _ = step_device()
         rates_a, (lanes_a, packed_a) = b.msa_align_autotune(h, c0)
         align_tune = {"choice": {"lanes": lanes_a, "cells": "int16x2" if packed_a else "int32"},
-                      "gcups": {"%s_G%d" % (p, 8 << g): float(rates_a[i, g]) / 1e9
-                                for i, p in enumerate(("int16x2", "int32")) for g in range(3)
+                      "gcups": {"%s_G%d" % (p, G): float(rates_a[i, g]) / 1e9
+                                for i, p in enumerate(("int16x2", "int32"))
+                                for g, G in enumerate(b.ALIGN_LANES)
                                 if rates_a[i, g] > 0}}
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):

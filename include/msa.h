@@ -382,19 +382,22 @@ int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes);
 int msa_set_codes_budget(msa_ctx *ctx, int64_t bytes);
 
 /* Autotuner of the alignment to a center (no counterpart in the paper): times
- * msa_align_to_center(center) with subject groups of 8, 16 and 32 lanes, in
+ * msa_align_to_center(center) with subject groups of 1, 2, 4, 8, 16 and 32
+ * lanes (1 lane: the inter-sequence mode, every lane aligning its own
+ * subjects; more lanes: an anti-diagonal wavefront over the group), in
  * packed int16x2 cells (where they fit the center's length) and in int32
  * cells, and keeps the fastest shape and precision for later alignments on
  * this context (msa_set_align_group overrides the shape).  rates_out
- * (nullable, host double[2][3]): cells per second, [packed, int32] x
- * [8, 16, 32] lanes (fill and traceback), 0 where not timed; choice_out
+ * (nullable, host double[2][6]): cells per second, [packed, int32] x
+ * [1, 2, 4, 8, 16, 32] lanes (fill and traceback), 0 where not timed; choice_out
  * (nullable, host int32[2]): {lanes, 1 if packed}.  The results do not
  * depend on the choice.  Leaves no alignment behind (align again). */
 int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t *choice_out);
 
-/* Lanes per subject group of the alignment kernels (8, 16 or 32; each lane
- * holds 16 center rows, so a pass covers 16 x lanes rows), or 0 for the
- * choice of the library's cost model (the default).  A tuning knob: the
+/* Lanes per subject group of the alignment kernels (1, 2, 4, 8, 16 or 32;
+ * each lane holds 16 center rows, so a pass covers 16 x lanes rows; with 1
+ * lane every lane aligns its own subjects, pass after pass), or 0 for the
+ * choice of the library's cost model among 8, 16 and 32 (the default).  A tuning knob: the
  * result does not depend on it.  EINVAL for any other value. */
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes);
 

@@ -250,9 +250,12 @@ def msa_align_anchored(ctx, center, k, scores=None):
     return int(fb.value)
 
 
+ALIGN_LANES = (1, 2, 4, 8, 16, 32)  # lanes per subject group of the alignment kernels
+
+
 def msa_align_autotune(ctx, center):
-    """(rates double[2, 3] = [packed, int32] x [8, 16, 32] lanes, (lanes, packed))."""
-    rates = np.zeros((2, 3), np.float64)
+    """(rates double[2, 6] = [packed, int32] x [1, 2, 4, 8, 16, 32] lanes, (lanes, packed))."""
+    rates = np.zeros((2, len(ALIGN_LANES)), np.float64)
     choice = np.zeros(2, np.int32)
     _check(ctx, lib().msa_align_autotune(ctx, int(center), _ptr(rates), _ptr(choice)))
     return rates, (int(choice[0]), bool(choice[1]))
@@ -360,10 +363,10 @@ def msa_set_memory_limit(ctx, limit_bytes):
 
 
 def msa_set_align_group(ctx, lanes):
-    """Lanes per subject group of the alignment kernels (8, 16, 32; 0 = modelled)."""
+    """Lanes per subject group of the alignment kernels (1, 2, 4, 8, 16, 32; 0 = modelled)."""
     rc = lib().msa_set_align_group(ctx, int(lanes))
     if rc != MSA_OK:
-        raise MSAError(rc, "align group must be 0, 8, 16 or 32")
+        raise MSAError(rc, "align group must be 0 or one of %s" % (ALIGN_LANES,))
 
 
 def msa_set_codes_budget(ctx, nbytes):

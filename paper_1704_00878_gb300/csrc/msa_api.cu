@@ -1470,13 +1470,13 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
   const int Lc = ctx->len_sorted[ctx->inv[center]];
   ctx->align_int32 = 0;
   const bool can_pack = codes_packed(ctx, Lc);
-  double rates[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  double rates[2][kAlignWidths] = {};
   double best = -1.0;
   int best_g = 32, best_i32 = 0;
   for (int i32 = 0; i32 < 2; ++i32) {
     if (i32 == 0 && !can_pack) continue;
-    for (int gi = 0; gi < 3; ++gi) {
-      const int G = 8 << gi;
+    for (int gi = 0; gi < kAlignWidths; ++gi) {
+      const int G = 1 << gi;
       ctx->align_int32 = i32;
       ctx->align_group = G;
       float ms = 0.f;
@@ -1498,7 +1498,7 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
 }
 
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes) {
-  if (!ctx || (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32)) return MSA_EINVAL;
+  if (!ctx || lanes < 0 || lanes > 32 || (lanes & (lanes - 1)) != 0) return MSA_EINVAL;
   ctx->align_group = lanes;
   return MSA_OK;
 }

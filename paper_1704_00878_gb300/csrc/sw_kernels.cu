@@ -678,10 +678,16 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
   for (int k = 0; k < steps; ++k) {
     const int kk = k & (G - 1);
     if (kk == 0 && k > 0) { cur = nxt; nxt = residue_at(rs, Ls, k + G + t, pc); }
-    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
-    uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
-    int hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
-    int fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    // one lane per subject (G = 1) has no neighbour: it reads its own column
+    // and the boundary row of its previous pass
+    uint32_t r0 = cur, rin = 0;
+    int hin = 0, fin = 0;
+    if constexpr (G > 1) {
+      r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
+      rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
+      hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
+      fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    }
     if (t == 0) {
       rin = r0;
       if (scr_in != nullptr && k < Ls) {
@@ -734,7 +740,7 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
   }
 }
 
-// Groups of G lanes (G in {8, 16, 32}, chosen from the center length), each
+// Groups of G lanes (G in {1, 2, 4, 8, 16, 32}; one lane per subject at G = 1), each
 // aligning one subject at a time; the groups of a warp fetch their subjects
 // together and run the warp's longest subject's number of columns.
 template <int G>
@@ -863,10 +869,13 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
   for (int k = 0; k < steps; ++k) {
     const int kk = k & (G - 1);
     if (kk == 0 && k > 0) { cur = nxt; nxt = fetch(k + G + t); }
-    const uint32_t r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
-    uint32_t rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
-    uint32_t hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
-    uint32_t fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    uint32_t r0 = cur, rin = 0, hin = 0, fin = 0;
+    if constexpr (G > 1) {
+      r0 = __shfl_sync(MSA_FULL_MASK, cur, base_lane + kk);
+      rin = __shfl_up_sync(MSA_FULL_MASK, resv, 1);
+      hin = __shfl_up_sync(MSA_FULL_MASK, hbot, 1);
+      fin = __shfl_up_sync(MSA_FULL_MASK, fbot, 1);
+    }
     const int2 sv = sv0;
     sv0 = sv1;
     if (scr_in != nullptr && k + 2 < Lw) sv1 = scr_in[k + 2];
@@ -1122,8 +1131,15 @@ int codes_smem_bytes(int K, int rows_alloc) {
 
 typedef void (*codes_fn)(SeqSet, Scoring, CodesJob);
 static codes_fn codes_kernel(int G, bool packed) {
-  if (packed) return G == 8 ? k_codes2<8> : (G == 16 ? k_codes2<16> : (G == 32 ? k_codes2<32> : nullptr));
-  return G == 8 ? k_codes<8> : (G == 16 ? k_codes<16> : (G == 32 ? k_codes<32> : nullptr));
+  switch (G) {
+    case 1: return packed ? k_codes2<1> : k_codes<1>;
+    case 2: return packed ? k_codes2<2> : k_codes<2>;
+    case 4: return packed ? k_codes2<4> : k_codes<4>;
+    case 8: return packed ? k_codes2<8> : k_codes<8>;
+    case 16: return packed ? k_codes2<16> : k_codes<16>;
+    case 32: return packed ? k_codes2<32> : k_codes<32>;
+    default: return nullptr;
+  }
 }
 
 

@@ -100,6 +100,8 @@ int codes_grid(int G, bool packed, int smem);
 int codes_threads(bool packed);  // threads per CTA of the codes kernels
 int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_len);
 constexpr int kCodesR = 16;
+// lanes per subject the alignment kernels come in: 1, 2, 4, 8, 16, 32
+constexpr int kAlignWidths = 6;
 constexpr int kCodes2Threads = 256;  // packed codes kernel threads per CTA
 constexpr int kPairsR = 16;
 constexpr int kCenterThreads = 256;

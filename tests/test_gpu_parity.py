@@ -112,19 +112,23 @@ def test_sampled_center():
 
 # ------------------------------------------------------------- alignment + merge
 
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4])
 @pytest.mark.parametrize("precision", [0, 2])
-def test_codes_and_best_cells_bitexact(precision):
+def test_codes_and_best_cells_bitexact(precision, lanes):
     """Codes of every cell: int16 lanes carrying two subjects (automatic
     precision; odd sorted positions are recomputed in the high lane) and
-    int32 cells.  Both extension bits match everywhere; the source bits
-    match wherever H > 0 (the oracle's source is nonzero): where H = 0 the
-    traceback stops on the score it carries, so the packed kernel stores no
-    zero source there (1, 2 or 3 instead)."""
+    int32 cells, with the modelled group width and with 1 (every lane its
+    own subjects, the center in 16-row passes), 2 and 4 lanes per group.
+    Both extension bits match everywhere; the source bits match wherever
+    H > 0 (the oracle's source is nonzero): where H = 0 the traceback stops
+    on the score it carries, so the packed kernel stores no zero source
+    there (1, 2 or 3 instead)."""
     b = binding()
     letters, offsets, w, alph, M = workload("plain_protein_200", n=13, seed=2)
     prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
     center = 4
     with make_ctx(alph, M, w.gap_open, w.gap_extend, precision=precision) as h:
+        b.msa_set_align_group(h, lanes)
         b.msa_load(h, letters, offsets)
         b.msa_align_to_center(h, center)
         seg, _, _ = b.msa_alignment_info(h)
@@ -165,7 +169,8 @@ def test_msa_long_center_multipass():
     check_against_oracle(prob, center, *out)
 
 
-@pytest.mark.parametrize("budget,lanes", [(1, 8), (300_000, 32), (300_000, 16)])
+@pytest.mark.parametrize("budget,lanes", [(1, 8), (300_000, 32), (300_000, 16), (1, 1),
+                                          (300_000, 1), (300_000, 2), (300_000, 4)])
 def test_msa_in_code_batches(budget, lanes):
     """Codes budgets that split the alignment into one subject per batch and
     into a few batches, with each group width of the alignment kernels, give
@@ -178,8 +183,9 @@ def test_msa_in_code_batches(budget, lanes):
         b.msa_set_align_group(h, lanes)
         with pytest.raises(b.MSAError):
             b.msa_set_codes_budget(h, 0)
-        with pytest.raises(b.MSAError):
-            b.msa_set_align_group(h, 12)
+        for bad in (12, 3, 64, -1):
+            with pytest.raises(b.MSAError):
+                b.msa_set_align_group(h, bad)
         out = run_pipeline(b, h, letters, offsets, 7)
     check_against_oracle(prob, 7, *out)
 
@@ -334,7 +340,7 @@ def test_autotuned_alignment_is_unchanged():
         b.msa_load(h, letters, offsets)
         rates, (lanes, packed) = b.msa_align_autotune(h, center)
         out = run_pipeline(b, h, letters, offsets, center)
-    assert (rates > 0).sum() == 6 and lanes in (8, 16, 32)
+    assert rates.shape == (2, 6) and (rates > 0).sum() == 12 and lanes in b.ALIGN_LANES
     check_against_oracle(prob, center, *out)
 
 
