@@ -374,7 +374,7 @@ int msa_memory(msa_ctx *ctx, int64_t *bytes_out, int64_t *peak_out);
 int msa_set_memory_limit(msa_ctx *ctx, int64_t limit_bytes);
 
 /* Device memory msa_align_to_center may hold for traceback codes at once
- * (0.5 byte per DP cell; default 32 GiB, and at most half the free device
+ * (about 0.5 byte per DP cell; default 32 GiB, and at most half the free device
  * memory and half of what a memory limit leaves).  The alignment runs in
  * batches of subjects whose codes fit, each batch's traceback after its fill;
  * a budget below one subject's codes gives one subject per batch.  The

@@ -289,10 +289,10 @@ int align_subset_local(msa_ctx *ctx, int kc, const std::vector<int32_t> &subj, f
   const int Lc = vlen[nv - 1];
   const bool packed = align_packed(ctx, Lc);
   const int R = kCodesR, G = align_lanes(ctx, Lc, packed);
-  const int nblk = (Lc + R - 1) / R, npass = (Lc + G * R - 1) / (G * R);
+  const int npass = (Lc + G * R - 1) / (G * R);
   std::vector<int64_t> offs(nv, 0);
   int64_t acc = 0;
-  for (int v = 0; v + 1 < nv; ++v) { offs[v] = acc; acc += (int64_t)nblk * vlen[v] * 8; }
+  for (int v = 0; v + 1 < nv; ++v) { offs[v] = acc; acc += (int64_t)code_words(vlen[v], Lc, G) * 8; }
   DevBuf vs, vl, vp, vo;
   auto cleanup = [&]() { for (DevBuf *b : {&vs, &vl, &vp, &vo}) release(ctx, *b); };
   int rc = [&]() -> int {
@@ -330,7 +330,7 @@ int align_subset_local(msa_ctx *ctx, int kc, const std::vector<int32_t> &subj, f
     CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(vo),
                                            P<unsigned long long>(ctx->best), 0, nv - 1,
                                            P<int32_t>(vl), P<int32_t>(vp), vss.res, vss.pstart,
-                                           nv - 1, sc.M, sc.K, sc.o, sc.e, Lc,
+                                           nv - 1, sc.M, sc.K, sc.o, sc.e, Lc, G,
                                            P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ),
                                            P<int32_t>(ctx->seg), P<int32_t>(ctx->score),
                                            ctx->derr, ctx->st));
@@ -449,12 +449,12 @@ extern "C" int msa_align_anchored(msa_ctx *ctx, int64_t center, int32_t k, int32
       CK(cudaStreamSynchronize(ctx->st));
       std::sort(fb.begin(), fb.end());  // sorted positions ascend in length
       // chunks whose codes fit the budget
-      const int nblk = (Lc + kCodesR - 1) / kCodesR;
-      size_t budget = std::max<size_t>(ctx->codes_budget, (size_t)nblk * ctx->maxlen * 8);
+      const int G = align_lanes(ctx, Lc, align_packed(ctx, Lc));
+      size_t budget = std::max<size_t>(ctx->codes_budget, code_words(ctx->maxlen, Lc, G) * 8);
       size_t acc = 0;
       std::vector<int32_t> part;
       for (size_t x = 0; x <= fb.size(); ++x) {
-        const size_t sz = x < fb.size() ? (size_t)nblk * ctx->len_sorted[fb[x]] * 8 : 0;
+        const size_t sz = x < fb.size() ? code_words(ctx->len_sorted[fb[x]], Lc, G) * 8 : 0;
         if (x == fb.size() || (acc + sz > budget && !part.empty())) {
           if (!part.empty()) TRY(align_subset_local(ctx, kc, part, ms_local));
           part.clear();

@@ -107,6 +107,23 @@ __host__ __device__ __forceinline__ int best_key_col(unsigned long long k) {
   return k ? 16383 - (int)(k & 16383u) : 0;
 }
 
+// Traceback codes of one subject of length L against a center of Lc rows,
+// aligned by groups of G lanes, each lane holding one block of 16 center rows
+// at a time: 8-byte words (16 rows x 4 bits), one row of S = L + G - 1
+// rounded up to a multiple of 4 words per block, block b's column j in slot
+// j + (b mod G) -- the wavefront step at which its lane computes it -- so
+// every lane of a group fills the same 32-byte chunk of its row in the same
+// four steps and writes it whole; slots outside the matrix hold no code.
+__host__ __device__ __forceinline__ int code_row_words(int L, int G) { return (L + G - 1 + 3) & ~3; }
+__host__ __device__ __forceinline__ size_t code_words(int L, int Lc, int G) {
+  return (size_t)((Lc + 15) >> 4) * (size_t)code_row_words(L, G);
+}
+// word of center row i0 (0-based) and column j0 (0-based)
+__host__ __device__ __forceinline__ size_t code_word(int i0, int j0, int L, int G) {
+  const int b = i0 >> 4;
+  return (size_t)b * (size_t)code_row_words(L, G) + (size_t)(j0 + b % G);
+}
+
 // Device-side error word bits (ctx->d_err).
 #define MSA_DERR_LETTER   1u   // a letter outside the alphabet
 #define MSA_DERR_TRACE    2u   // inconsistent traceback codes

@@ -1088,7 +1088,6 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   ctx->Lc = Lc;
   const bool packed = codes_packed(ctx, Lc);
   const int R = kCodesR, G = align_group(ctx, Lc, packed);
-  const int nblk = (Lc + R - 1) / R;
   const int npass = (Lc + G * R - 1) / (G * R);
   const size_t row = (size_t)Lc + 1;
   TRY(ensure(ctx, ctx->ins, sizeof(uint16_t) * row * n));
@@ -1104,7 +1103,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   CK(cudaMemGetInfo(&free_b, &total_b));
   size_t budget = std::min(ctx->codes_budget, free_b / 2);
   if (ctx->dev_limit) budget = std::min(budget, ctx->dev_limit > ctx->dev_bytes ? (ctx->dev_limit - ctx->dev_bytes) / 2 : 0);
-  size_t max_one = (size_t)nblk * ctx->maxlen * 8;
+  size_t max_one = code_words(ctx->maxlen, Lc, G) * 8;
   if (budget < max_one) budget = max_one;
   std::vector<std::pair<int, int>> batches;
   std::vector<int64_t> offs(n);
@@ -1113,7 +1112,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
     int b = 0;
     size_t acc = 0;
     for (int k = 0; k < n; ++k) {
-      const size_t sz = (size_t)nblk * ctx->len_sorted[k] * 8;
+      const size_t sz = code_words(ctx->len_sorted[k], Lc, G) * 8;
       if (acc + sz > budget && k > b) {
         batches.push_back({b, k});
         biggest = std::max(biggest, acc);
@@ -1188,7 +1187,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
         e = launch_traceback(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
                              P<unsigned long long>(ctx->best) + sb, sb, se, P<int32_t>(ctx->d_len),
                              P<int32_t>(ctx->d_perm), ss.res, ss.pstart, kc, sc.M, sc.K, sc.o, sc.e,
-                             Lc, P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->seg),
+                             Lc, G, P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->seg),
                              P<int32_t>(ctx->score), ctx->derr, ctx->cap_st);
       if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->align_ev[3 * bi + 2], ctx->cap_st, cudaEventRecordExternal);
     }
@@ -1260,12 +1259,12 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
   const int ks = ctx->inv[seq], kc = ctx->inv[ctx->center];
   const int Lc = ctx->Lc, Ls = ctx->len_sorted[ks];
   const bool packed = codes_packed(ctx, Lc);
-  const int R = kCodesR, G = align_group(ctx, Lc, packed), nblk = (Lc + R - 1) / R;
+  const int R = kCodesR, G = align_group(ctx, Lc, packed);
   const int npass = (Lc + G * R - 1) / (G * R);
   const bool high = packed && (ks & 1) && ks + 1 < ctx->n;
   const int se = high ? ks + 2 : ks + 1;
-  const size_t bytes = (size_t)nblk * Ls * 8;
-  const size_t bytes_all = high ? bytes + (size_t)nblk * ctx->len_sorted[ks + 1] * 8 : bytes;
+  const size_t bytes = code_words(Ls, Lc, G) * 8;
+  const size_t bytes_all = high ? bytes + code_words(ctx->len_sorted[ks + 1], Lc, G) * 8 : bytes;
   DevBuf cb, ob, bb;
   auto cleanup = [&]() { for (DevBuf *b : {&cb, &ob, &bb}) release(ctx, *b); };
   int rc = [&]() -> int {
@@ -1297,7 +1296,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     CK(cudaStreamSynchronize(ctx->st));
     for (int i = 0; i < Lc; ++i)
       for (int j = 0; j < Ls; ++j) {
-        const size_t at = ((size_t)(i >> 4) * Ls + j) * 8 + ((i & 15) >> 1);
+        const size_t at = code_word(i, j, Ls, G) * 8 + ((i & 15) >> 1);
         out[(size_t)i * Ls + j] = (raw[at] >> ((i & 1) * 4)) & 15;
       }
     CK(cudaMemcpyAsync(codes_out, out.data(), out.size(), cudaMemcpyDefault, ctx->st));

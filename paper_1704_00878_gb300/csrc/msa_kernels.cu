@@ -48,9 +48,10 @@ __global__ void k_encode(const uint8_t *__restrict__ letters, const int64_t *__r
 // H(i-1, j) = v + o (opened), and likewise for E along the row.  In state H the
 // walk stops where v = 0 (the paper's "cell with score of zero"), so the codes
 // need a source only where H > 0.
-__device__ __forceinline__ uint32_t code_at(const uint8_t *__restrict__ c, int Ls, int i, int j) {
+__device__ __forceinline__ uint32_t code_at(const uint8_t *__restrict__ c, int Ls, int G, int i,
+                                            int j) {
   const int r = i - 1;
-  const size_t at = ((size_t)(r >> 4) * Ls + (j - 1)) * 8 + ((r & 15) >> 1);
+  const size_t at = code_word(r, j - 1, Ls, G) * 8 + ((r & 15) >> 1);
   return (c[at] >> ((r & 1) * 4)) & 15u;
 }
 
@@ -59,7 +60,7 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
                             const int32_t *__restrict__ len, const int32_t *__restrict__ perm,
                             const uint8_t *__restrict__ res, const int64_t *__restrict__ pstart,
                             int center, const int8_t *__restrict__ M, int K, int o, int e,
-                            int Lc, uint16_t *__restrict__ ins, uint8_t *__restrict__ occ,
+                            int Lc, int G, uint16_t *__restrict__ ins, uint8_t *__restrict__ occ,
                             int32_t *__restrict__ seg, int32_t *__restrict__ score,
                             unsigned *err) {
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
@@ -94,7 +95,7 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
       if (state == 0) {
         if (v == 0) { ok = true; break; }
         if (v < 0) break;
-        const uint32_t src = code_at(c, Ls, i, j) & 3u;
+        const uint32_t src = code_at(c, Ls, G, i, j) & 3u;
         if (src == 1) {
           v -= sM[rc[i - 1] * K + rs[j - 1]];
           oc[i] = 1; --i; --j;
@@ -104,12 +105,12 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
           state = src == 2 ? 1 : 2;
         }
       } else if (state == 1) {
-        const bool ext = (code_at(c, Ls, i, j) >> 3) & 1u;
+        const bool ext = (code_at(c, Ls, G, i, j) >> 3) & 1u;
         v += ext ? e : o;
         state = ext ? 1 : 0;
         --i;
       } else {
-        const bool ext = (code_at(c, Ls, i, j) >> 2) & 1u;
+        const bool ext = (code_at(c, Ls, G, i, j) >> 2) & 1u;
         in[i] = (uint16_t)(in[i] + 1);
         v += ext ? e : o;
         state = ext ? 2 : 0;
@@ -356,7 +357,7 @@ cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
                              const unsigned long long *best,
                              int sb, int se, const int32_t *len, const int32_t *perm,
                              const uint8_t *res, const int64_t *pstart, int center,
-                             const int8_t *M, int K, int o, int e, int Lc,
+                             const int8_t *M, int K, int o, int e, int Lc, int G,
                              uint16_t *ins, uint8_t *occ, int32_t *seg, int32_t *score,
                              unsigned *err, cudaStream_t st) {
   const int cnt = se - sb;
@@ -364,7 +365,7 @@ cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
   const int threads = 128;
   k_traceback<<<(cnt + threads - 1) / threads, threads, 0, st>>>(codes, code_off, best, sb, se, len,
                                                                  perm, res, pstart, center, M, K, o,
-                                                                 e, Lc, ins, occ, seg, score, err);
+                                                                 e, Lc, G, ins, occ, seg, score, err);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
                              const unsigned long long *best,
                              int sb, int se, const int32_t *len, const int32_t *perm,
                              const uint8_t *res, const int64_t *pstart, int center,
-                             const int8_t *M, int K, int o, int e, int Lc,
+                             const int8_t *M, int K, int o, int e, int Lc, int G,
                              uint16_t *ins, uint8_t *occ, int32_t *seg, int32_t *score,
                              unsigned *err, cudaStream_t st);
 

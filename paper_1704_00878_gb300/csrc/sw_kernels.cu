@@ -656,6 +656,24 @@ __global__ void __launch_bounds__(256) k_pairs(SeqSet ss, Scoring sc, PairJob jo
 //   H  = vibmax(0, M - o)          -> H == 0    (source 0, the stop)
 //   E*'= vibmax(H, E* - e)         -> E extended for the next column
 //   best row value = vibmax(best, H) -> a strictly larger H moves the column
+// Four code words (slots k-3 .. k of a block row, 32-byte aligned) in one
+// 32-byte chunk.
+__device__ __forceinline__ void store_chunk(uint2 *p, uint2 w0, uint2 w1, uint2 w2, uint2 w3) {
+  uint4 *q = reinterpret_cast<uint4 *>(p);
+  q[0] = make_uint4(w0.x, w0.y, w1.x, w1.y);
+  q[1] = make_uint4(w2.x, w2.y, w3.x, w3.y);
+}
+
+// The words of the last, partial chunk after a pass of `steps` steps (the
+// newest m = steps mod 4 words sit in w[4-m..3]).
+__device__ __forceinline__ void flush_chunk(uint2 *cout, bool wr, int steps, int slots, uint2 w0,
+                                            uint2 w1, uint2 w2, uint2 w3) {
+  const int m = steps & 3, k0 = steps - m;
+  if (m == 0 || !wr || cout == nullptr || k0 >= slots) return;
+  for (int s = m; s < 4; ++s) { w0 = w1; w1 = w2; w2 = w3; w3 = make_uint2(0, 0); }
+  store_chunk(cout + k0, w0, w1, w2, w3);
+}
+
 template <int G>
 __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int stride,
                                            const uint8_t *__restrict__ rs, int Ls, int Lw, int t,
@@ -671,6 +689,9 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
   int hbot = 0, fbot = 0, htop_prev = 0;
   const uint32_t pc = (uint32_t)padc;
   uint32_t resv = pc;
+  // the last four steps' code words (column k - t at slot k of the block row)
+  uint2 q0 = make_uint2(0, 0), q1 = q0, q2 = q0, q3 = q0;
+  const int slots = Ls + G - 1;
   uint32_t cur = residue_at(rs, Ls, t, pc), nxt = residue_at(rs, Ls, G + t, pc);
   const int8_t *pb = prof + t * R;
   const bool wr = blk < nblk;
@@ -731,9 +752,11 @@ __device__ __forceinline__ void codes_pass(const int8_t *__restrict__ prof, int 
     emask = enew;
     hbot = H[R - 1];
     fbot = f;
-    if (wr && j >= 0 && j < Ls) cout[j] = make_uint2(lo, hi);
+    q0 = q1; q1 = q2; q2 = q3; q3 = make_uint2(lo, hi);
+    if ((k & 3) == 3 && wr && cout != nullptr && k - 3 < slots) store_chunk(cout + (k - 3), q0, q1, q2, q3);
     if (scr_out != nullptr && t == G - 1 && j >= 0 && j < Ls) scr_out[j] = make_int2(hbot, fbot);
   }
+  flush_chunk(cout, wr, steps, slots, q0, q1, q2, q3);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     if (rb[r] > bv) { bv = rb[r]; bi = blk * R + r + 1; bj = rj[r] + 1; }
@@ -785,7 +808,7 @@ __global__ void __launch_bounds__(256) k_codes(SeqSet ss, Scoring sc, CodesJob j
       int2 *sout = p + 1 < job.npass ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
       const int blk = p * G + t;
       codes_pass<G>(smem + p * G * R, stride, rs, Ls, Lw, t, base_lane, blk, nblk, padc, sc.o, sc.e,
-                    sin, sout, valid ? cbase + (size_t)blk * Ls : nullptr, bv, bi, bj);
+                    sin, sout, valid ? cbase + (size_t)blk * code_row_words(Ls, G) : nullptr, bv, bi, bj);
       __syncwarp();
     }
     // best cell over the group: largest H, then smallest row, then smallest column
@@ -856,6 +879,9 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
   for (int r = 0; r < R; ++r) { H[r] = 0; E[r] = 0; rb[r] = 0; rj[r] = 0; }
   uint32_t hbot = 0, fbot = 0, htop_prev = 0;
   uint32_t resv = pc | (pc << 8);
+  // the last four steps' code words of each subject (slot k of the block row)
+  uint2 a0 = make_uint2(0, 0), a1 = a0, a2 = a0, a3 = a0, b0 = a0, b1 = a0, b2 = a0, b3 = a0;
+  const int slotsA = LA + G - 1, slotsB = LB + G - 1;
   uint32_t cur = fetch(t), nxt = fetch(G + t);
   int2 sv0 = make_int2(0, 0), sv1 = make_int2(0, 0);
   if (scr_in != nullptr) {
@@ -918,12 +944,18 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
     });
     hbot = H[R - 1];
     fbot = f;
-    if (wr && j >= 0) {
-      if (j < LA) coutA[j] = make_uint2(__byte_perm(acc[0], acc[1], 0x5410), __byte_perm(acc[2], acc[3], 0x5410));
-      if (j < LB) coutB[j] = make_uint2(__byte_perm(acc[0], acc[1], 0x7632), __byte_perm(acc[2], acc[3], 0x7632));
+    a0 = a1; a1 = a2; a2 = a3;
+    a3 = make_uint2(__byte_perm(acc[0], acc[1], 0x5410), __byte_perm(acc[2], acc[3], 0x5410));
+    b0 = b1; b1 = b2; b2 = b3;
+    b3 = make_uint2(__byte_perm(acc[0], acc[1], 0x7632), __byte_perm(acc[2], acc[3], 0x7632));
+    if ((k & 3) == 3 && wr) {
+      if (coutA != nullptr && k - 3 < slotsA) store_chunk(coutA + (k - 3), a0, a1, a2, a3);
+      if (coutB != nullptr && k - 3 < slotsB) store_chunk(coutB + (k - 3), b0, b1, b2, b3);
     }
     if (scr_out != nullptr && t == G - 1 && j >= 0 && j < Lw) scr_out[j] = make_int2((int)hbot, (int)fbot);
   }
+  flush_chunk(coutA, wr, steps, slotsA, a0, a1, a2, a3);
+  flush_chunk(coutB, wr, steps, slotsB, b0, b1, b2, b3);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int va = C::lane0((int)rb[r]), vb = C::lane1((int)rb[r]);
@@ -983,8 +1015,8 @@ __global__ void __launch_bounds__(kCodes2Threads, 1) k_codes2(SeqSet ss, Scoring
       int2 *sout = p + 1 < job.npass ? scr + (size_t)(p & 1) * job.scratch_cols : nullptr;
       const int blk = p * G + t;
       codes_pass2<G>(smem + p * G * R, stride, rA, LA, rB, LB, Lw, t, base_lane, blk, nblk, padc,
-                     sc.o, sc.e, sin, sout, cA ? cA + (size_t)blk * LA : nullptr,
-                     cB ? cB + (size_t)blk * LB : nullptr, bv, bi, bj);
+                     sc.o, sc.e, sin, sout, cA ? cA + (size_t)blk * code_row_words(LA, G) : nullptr,
+                     cB ? cB + (size_t)blk * code_row_words(LB, G) : nullptr, bv, bi, bj);
       __syncwarp();
     }
 #pragma unroll
