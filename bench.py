@@ -49,10 +49,10 @@ CODES_SLOTS_PER_CELL = 3 * 2 + 4
 CODES_PEAK_GCUPS = SMS * 2 * INT_LANES * MAX_GHZ / CODES_SLOTS_PER_CELL
 CODES_BYTES_PER_CELL = 0.5   # 4-bit traceback code per cell written to HBM
 # DRAM bytes read + written per cell by the codes kernel, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum = 75.4 + 522.7 MB for 1.007e9
-# cells of 20,000 peptides against the 500-residue center); the traffic grows
-# with the cells, so a launch's traffic is this times its cells
-CODES_TRAFFIC_PER_CELL = (75.4e6 + 522.7e6) / 1.006925e9
+# (dram__bytes_read.sum + dram__bytes_write.sum = 10.6 + 528.5 MB for 1.007e9
+# cells of 20,000 peptides against the 500-residue center, 8-lane groups); the
+# traffic grows with the cells, so a launch's traffic is this times its cells
+CODES_TRAFFIC_PER_CELL = (10.6e6 + 528.5e6) / 1.006925e9
 ALIGN_WORKLOAD, ALIGN_N = "short_peptides_1m", 200_000
 # the library's center kernel variants, in msa_autotune's column order:
 # (two queries per int16x2 register?, lanes per group, query rows per lane, packed)
