@@ -85,6 +85,32 @@ def test_planted_anchored_mistake_is_caught(name, tmp_path):
     _run_mutated(tmp_path, "oracle/msa_oracle.c", old, new, "tests/test_oracle_anchored.py", name)
 
 
+# mistakes in the tree oracle, caught by tests/test_oracle_nj.py
+TREE_MUTATIONS = {
+    "q_sign_of_r_j": ("Q = (m - 2) * sub - r[:, None] - r[None, :]",
+                      "Q = (m - 2) * sub - r[:, None] + r[None, :]"),
+    "q_factor_m_minus_1": ("Q = (m - 2) * sub - r[:, None] - r[None, :]",
+                           "Q = (m - 1) * sub - r[:, None] - r[None, :]"),
+    "pairs_include_diagonal": ("Q[np.tril_indices(m)] = big", "Q[np.tril_indices(m, -1)] = big"),
+    "branch_lengths_swapped": ("bl_i = float((m - 2) * dij + int(r[x]) - int(r[y])) / den",
+                               "bl_i = float((m - 2) * dij - int(r[x]) + int(r[y])) / den"),
+    "update_not_halved": ("(int(D[i, k]) + int(D[j, k]) - dij) >> 1",
+                          "(int(D[i, k]) + int(D[j, k]) - dij)"),
+    "update_keeps_dij": ("(int(D[i, k]) + int(D[j, k]) - dij) >> 1",
+                         "(int(D[i, k]) + int(D[j, k])) >> 1"),
+    "gap_columns_compared": ("both = res & res[a]", "both = res | res[a]"),
+    "distance_rounds_up": ("(DSCALE * mism) // np.maximum(comp, 1)",
+                           "-((-DSCALE * mism) // np.maximum(comp, 1))"),
+    "empty_pair_near": ("np.maximum(comp, 1), DSCALE)", "np.maximum(comp, 1), 0)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TREE_MUTATIONS))
+def test_planted_tree_mistake_is_caught(name, tmp_path):
+    old, new = TREE_MUTATIONS[name]
+    _run_mutated(tmp_path, "oracle/nj.py", old, new, "tests/test_oracle_nj.py", name)
+
+
 @pytest.mark.parametrize("name", sorted(NET_MUTATIONS))
 def test_planted_network_mistake_is_caught(name, tmp_path):
     old, new = NET_MUTATIONS[name]
