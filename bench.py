@@ -54,6 +54,9 @@ CODES_BYTES_PER_CELL = 0.5   # 4-bit traceback code per cell written to HBM
 # traffic grows with the cells, so a launch's traffic is this times its cells
 CODES_TRAFFIC_PER_CELL = (10.6e6 + 528.5e6) / 1.006925e9
 ALIGN_WORKLOAD, ALIGN_N = "short_peptides_1m", 200_000
+# distance kernel of the tree: 9 integer instructions per 32-bit word of both
+# rows (4 columns: xor, nonzero test, residue mask, two counter updates)
+TREE_PEAK_TCPS = 152 * 128 * 2.07e9 / (9 / 4) / 1e12
 # the library's center kernel variants, in msa_autotune's column order:
 # (two queries per int16x2 register?, lanes per group, query rows per lane, packed)
 CENTER_VARIANTS = [(1, 8, 12, 1), (1, 8, 20, 1), (1, 8, 28, 1), (1, 16, 12, 1), (1, 16, 20, 1),
@@ -114,6 +117,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuners (center variants per length bucket; alignment "
                          "group width and int16x2 / int32 cells) and use the cost models")
+    ap.add_argument("--no-tree-record", action="store_true",
+                    help="skip the neighbour-joining tree of the step's MSA")
     ap.add_argument("--no-align-record", action="store_true",
                     help="skip the alignment-kernel record (peptides against their 500-residue "
                          "ancestor)")
@@ -331,6 +336,46 @@ def align_record(flush, stream, peak_gbs, no_tune=False):
                                         "instructions at half rate + 4 two-operand ops) per cell",
                          "hbm_bound_gcups": peak_gbs / CODES_BYTES_PER_CELL,
                          "hbm_gbs_of_codes": gcups * CODES_BYTES_PER_CELL}}
+
+
+def tree_record(b, h, n, W, stream, peak_gbs, cpu_n=600):
+    """The neighbour-joining tree of the step's MSA (already merged on the
+    device): the distance kernel (column pairs per second against its integer
+    issue bound) and the joins (bytes of the matrix the Q minimum reads, per
+    second), CUDA events on the context stream; the oracle's NJ on the first
+    `cpu_n` rows' distances beside it."""
+    import torch
+    from oracle import nj as T
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    d = torch.empty((n, n), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    b.msa_tree_distances(h, d)
+    ev[1].record(stream)
+    joins, lengths = b.msa_nj(h, d)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    dist_ms, nj_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    col_pairs = n * (n + 1) / 2 * W  # tiles on and above the diagonal
+    # matrix bytes the Q minimum reads: the active pairs of every join
+    nj_bytes = sum(m * (m - 1) / 2 for m in range(3, n + 1)) * 8
+    sub = d[:cpu_n, :cpu_n].cpu().numpy()
+    t0 = time.perf_counter()
+    T.nj(sub)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "NJ tree of the step's %d-row MSA (%d columns), fixed-point p-distances"
+                        % (n, W),
+            "distances_ms": dist_ms, "nj_ms": nj_ms, "joins": int(len(joins)),
+            "column_pairs_per_s": col_pairs / (dist_ms * 1e-3),
+            "distances_roofline": {"bound": "alu", "kernel": "k_pdist",
+                                   "achieved": col_pairs / (dist_ms * 1e-3) / 1e12,
+                                   "peak": TREE_PEAK_TCPS, "unit": "T column pairs/s",
+                                   "frac": col_pairs / (dist_ms * 1e-3) / 1e12 / TREE_PEAK_TCPS,
+                                   "peak_source": "152 SMs x 128 integer lanes/clk x 2.07 GHz / "
+                                                  "9 instructions per 4 column pairs"},
+            "nj_matrix_gbs": nj_bytes / (nj_ms * 1e-3) / 1e9, "hbm_peak_gbs": peak_gbs,
+            "cpu_oracle_nj": {"rows": int(sub.shape[0]), "seconds": cpu_s,
+                              "kind": "oracle", "cores": 1}}
 
 
 def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact_sp, refs,
@@ -667,6 +712,12 @@ def run_ours(args):
                                    refs, ex_c, ex_rows)
         if w.center_seq:
             learned["named_center_rowsum_rank_pct"] = 100.0 * float((ex_rows < ex_rows[0]).mean())
+    tree = None
+    if not args.no_tree_record and rank == 0:
+        b.msa_load(h, dlet, offsets)
+        b.msa_align_to_center(h, c)
+        _, Wt = b.msa_merge_gaps(h, want_rows=False)
+        tree = tree_record(b, h, n, Wt, stream, measured_peaks().get("hbm_gbs", 6800.0))
     align = None
     if not args.no_align_record and rank == 0:
         align = align_record(flush, stream, measured_peaks().get("hbm_gbs", 6800.0),
@@ -714,6 +765,8 @@ def run_ours(args):
         line["learned_vs_exact"] = learned
     if align is not None:
         line["align"] = align
+    if tree is not None:
+        line["tree"] = tree
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(letters, offsets, alph, M, w.gap_open, w.gap_extend,
                                             args.cpu_seconds)

@@ -354,7 +354,8 @@ int msa_dims(msa_ctx *ctx, int64_t *dims_out);
 /* Device milliseconds of the stages of the last calls, CUDA events on the
  * context stream: [0] encode, [1] center selection, [2] align DP, [3]
  * traceback, [4] merge, [5] rows, [6] SP, [7] center DP kernels alone, [8]
- * align DP kernels alone, [9] selector (embedding or training).  counters_out (nullable, int64[3]): DP cells of the
+ * align DP kernels alone, [9] selector (embedding or training), [10] tree
+ * (distances and neighbour joining).  counters_out (nullable, int64[3]): DP cells of the
  * last center selection, DP cells of the last alignment, kernels launched by
  * this context since msa_create. */
 int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_out);
@@ -400,6 +401,37 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
  * choice of the library's cost model among 8, 16 and 32 (the default).  A tuning knob: the
  * result does not depend on it.  EINVAL for any other value. */
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes);
+
+/* Distances between the rows of the merged MSA for the phylogenetic tree
+ * (the paper's section on NJ trees, Figure 4: the tree is built from the
+ * MSA; the paper names no distance).  Reading: the p-distance over the
+ * columns where both rows hold a residue (a gap in either row: the column is
+ * not compared), in fixed point d = floor(2^20 * mismatches / compared), and
+ * 2^20 when no column is compared.  Requires msa_merge_gaps.  dist_out: host
+ * or device int64[n * n], row-major, input order.  ESTATE before a merge. */
+int msa_tree_distances(msa_ctx *ctx, int64_t *dist_out);
+
+/* Neighbour joining (Saitou and Nei, the method the paper's tree section
+ * cites) of an n x n integer distance matrix `dist` (host or device int64,
+ * row-major, symmetric, zero diagonal; |entries| and every joined distance
+ * within 2^40, else ERANGE).  Reading, with m nodes active: r_i = sum of
+ * d(i, k) over the active k; the active pair i < j of smallest
+ * Q = (m - 2) d(i, j) - r_i - r_j joins, ties to the smallest i, then the
+ * smallest j, where slots are numbered as the input rows and a new node
+ * takes the slot of i; branch lengths ((m - 2) d(i, j) + r_i - r_j) /
+ * (2 (m - 2)) to i and ((m - 2) d(i, j) - r_i + r_j) / (2 (m - 2)) to j, one
+ * double division of two int64 values each; the new node's distances
+ * floor((d(i, k) + d(j, k) - d(i, j)) / 2); the last two nodes join at the
+ * middle of their edge (the root).  Node ids: rows 0 .. n-1, join t creates
+ * node n + t.  joins_out: host or device int32[(n - 1) * 2] (children of node
+ * n + t), lengths_out: host or device double[(n - 1) * 2] (their branch
+ * lengths); both may be null for n = 1.  n: 1 .. 65536. */
+int msa_nj(msa_ctx *ctx, const int64_t *dist, int64_t n, int32_t *joins_out, double *lengths_out);
+
+/* The neighbour-joining tree of the merged MSA: msa_tree_distances then
+ * msa_nj on the device, without a host round trip.  ESTATE before a merge,
+ * ERANGE beyond 65,536 sequences. */
+int msa_nj_tree(msa_ctx *ctx, int32_t *joins_out, double *lengths_out);
 
 /* Self-test of the bounded waits of the tensor-core convolution (no
  * counterpart in the paper): runs one small convolution whose loads are

@@ -20,7 +20,7 @@ MSA_CENTER_LEARNED_REFINED = 4
 MSA_MAX_LEN = 8192
 
 STAGES = ("encode", "center", "align_dp", "traceback", "merge", "rows", "sp", "center_kernels",
-          "align_kernels", "selector")
+          "align_kernels", "selector", "tree")
 
 
 class MSAError(RuntimeError):
@@ -77,6 +77,10 @@ _SIGS = {
     "msa_set_codes_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "msa_set_align_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "msa_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_tree_distances": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_nj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                              ctypes.c_void_p]),
+    "msa_nj_tree": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
     "msa_selector_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -348,6 +352,37 @@ def msa_sp_score(ctx):
     v = np.zeros(1, np.int64)
     _check(ctx, lib().msa_sp_score(ctx, _ptr(v)))
     return int(v[0])
+
+
+def msa_tree_distances(ctx, out=None):
+    """Fixed-point p-distances int64[n, n] of the merged MSA's rows."""
+    n = msa_dims(ctx)[0]
+    d = np.zeros((n, n), np.int64) if out is None else out
+    _check(ctx, lib().msa_tree_distances(ctx, _ptr(d)))
+    return d
+
+
+def msa_nj(ctx, dist):
+    """Neighbour joining of an int64[n, n] matrix (host array or device
+    tensor): (joins int32[n-1, 2], lengths float64[n-1, 2])."""
+    n = int(dist.shape[0])
+    joins = np.zeros((max(n - 1, 0), 2), np.int32)
+    lengths = np.zeros((max(n - 1, 0), 2), np.float64)
+    if isinstance(dist, np.ndarray):
+        dist = np.ascontiguousarray(dist, dtype=np.int64)
+    elif getattr(dist, "dtype", None) is not None and str(dist.dtype) != "torch.int64":
+        raise ValueError("distances must be int64")
+    _check(ctx, lib().msa_nj(ctx, _ptr(dist), n, _ptr(joins), _ptr(lengths)))
+    return joins, lengths
+
+
+def msa_nj_tree(ctx):
+    """The neighbour-joining tree of the merged MSA: (joins, lengths) as msa_nj."""
+    n = msa_dims(ctx)[0]
+    joins = np.zeros((max(n - 1, 0), 2), np.int32)
+    lengths = np.zeros((max(n - 1, 0), 2), np.float64)
+    _check(ctx, lib().msa_nj_tree(ctx, _ptr(joins), _ptr(lengths)))
+    return joins, lengths
 
 
 def msa_memory(ctx):

@@ -129,6 +129,7 @@ __host__ __device__ __forceinline__ size_t code_word(int i0, int j0, int L, int 
 #define MSA_DERR_TRACE    2u   // inconsistent traceback codes
 #define MSA_DERR_OVERFLOW 4u   // overflow list full
 #define MSA_DERR_TIMEOUT_TC 8u // a tensor-core convolution gave up waiting on an mbarrier
+#define MSA_DERR_RANGE   16u   // a tree distance beyond its bound
 
 static inline int round_up_int(int x, int m) { return (x + m - 1) / m * m; }
 static inline int64_t round_up_i64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -17,10 +17,11 @@ struct DevBuf {
 
 enum Stage {
   ST_ENCODE = 0, ST_CENTER, ST_ALIGN, ST_TRACE, ST_MERGE, ST_ROWS, ST_SP, ST_CENTER_K, ST_ALIGN_K,
-  ST_SELECTOR, ST_N
+  ST_SELECTOR, ST_TREE, ST_N
 };
 
 struct Selector;  // the learned center selector (selector.cu)
+constexpr int kMaxTreeRows = 65536;  // rows of a neighbour-joining tree
 void selector_free(msa_ctx *ctx, Selector *s);
 
 }  // namespace msa_detail

@@ -1,0 +1,478 @@
+// tree.cu -- the neighbour-joining tree over the MSA (the paper's section on
+// NJ trees, Figure 4, citing Saitou and Nei): fixed-point p-distances between
+// the merged rows, then neighbour joining on those integers.
+//
+// Distances: a CTA takes a 64 x 64 tile of row pairs (tiles on and above the
+// diagonal), stages 256 columns of its 2 x 64 rows in shared memory and
+// compares four columns per 32-bit word: x = a ^ b, a byte is nonzero iff
+// ((x & 0x7f7f7f7f) + 0x7f7f7f7f | x) has its top bit set; the residue flags
+// are the same test against '-' in every byte; per pair two SWAR byte
+// counters (compared, mismatched) gather up to 64 words before they are
+// summed into 32-bit totals.
+//
+// Neighbour joining: the matrix stays on the device (int64, positions in
+// ascending slot order); every join is two launches -- the minimum of Q over
+// the active pairs (one warp per row, lanes along it, the last CTA to finish
+// reduces the CTAs' minima) and the join itself (one CTA: branch lengths,
+// the new node's row and column, the row sums updated in place).  When half
+// the positions are inactive the matrix is packed to the active ones, which
+// keeps the work of a join near m^2 / 2.  No launch waits on another.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace msa_detail {
+namespace {
+
+constexpr int kTile = 64;    // rows per side of a distance tile
+constexpr int kWords = 64;   // 32-bit words (4 columns) per staged chunk
+constexpr long long kDScale = 1LL << 20;
+constexpr long long kDLimit = 1LL << 40;  // |distance| bound of the joins
+constexpr int kArgThreads = 256;
+constexpr int kJoinThreads = 1024;
+
+// 0x80 in every byte of w that is nonzero
+__device__ __forceinline__ uint32_t bytes_nonzero(uint32_t w) {
+  return (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;
+}
+
+// sum of the four bytes of a SWAR counter
+__device__ __forceinline__ uint32_t byte_sum(uint32_t c) {
+  c = (c & 0x00ff00ffu) + ((c >> 8) & 0x00ff00ffu);
+  return (c & 0xffffu) + (c >> 16);
+}
+
+__global__ void __launch_bounds__(256) k_pdist(const uint8_t *__restrict__ msa, int n, int64_t W,
+                                               long long *__restrict__ D) {
+  const int ta = blockIdx.y, tb = blockIdx.x;
+  if (tb < ta) return;
+  __shared__ uint32_t sA[kTile][kWords + 1], sB[kTile][kWords + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int a0 = ta * kTile, b0 = tb * kTile;
+  constexpr uint32_t kGap4 = 0x2d2d2d2du;  // "----"
+  uint32_t comp[4][4] = {}, mism[4][4] = {};
+  const int64_t nwords = (W + 3) / 4;
+  for (int64_t w0 = 0; w0 < nwords; w0 += kWords) {
+    __syncthreads();
+    // stage 64 rows x 256 columns of each side; columns past W and rows past n are gaps
+    for (int idx = threadIdx.x; idx < kTile * kWords; idx += 256) {
+      const int r = idx / kWords, w = idx - r * kWords;
+      const int64_t c0 = (w0 + w) * 4;
+      uint32_t va = kGap4, vb = kGap4;
+      const int ra = a0 + r, rb = b0 + r;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t c = c0 + u;
+        if (c < W) {
+          if (ra < n) va = (va & ~(0xffu << (8 * u))) | ((uint32_t)msa[(size_t)ra * W + c] << (8 * u));
+          if (rb < n) vb = (vb & ~(0xffu << (8 * u))) | ((uint32_t)msa[(size_t)rb * W + c] << (8 * u));
+        }
+      }
+      sA[r][w] = va;
+      sB[r][w] = vb;
+    }
+    __syncthreads();
+    uint32_t cc[4][4] = {}, cm[4][4] = {};  // byte counters: at most 64 per byte
+#pragma unroll 4
+    for (int w = 0; w < kWords; ++w) {
+      uint32_t a[4], fa[4], b[4], fb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = sA[ty + 16 * i][w];
+        fa[i] = bytes_nonzero(a[i] ^ kGap4);
+        b[i] = sB[tx + 16 * i][w];
+        fb[i] = bytes_nonzero(b[i] ^ kGap4);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t both = fa[i] & fb[j];
+          cc[i][j] += both >> 7;
+          cm[i][j] += (bytes_nonzero(a[i] ^ b[j]) & both) >> 7;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        comp[i][j] += byte_sum(cc[i][j]);
+        mism[i][j] += byte_sum(cm[i][j]);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a >= n || b >= n) continue;
+      const long long d = comp[i][j] ? ((long long)mism[i][j] * kDScale) / comp[i][j] : kDScale;
+      D[(size_t)a * n + b] = d;
+      if (ta != tb) D[(size_t)b * n + a] = d;
+    }
+}
+
+struct Pick {
+  long long q, xy;  // Q, then position pair x * 2^32 + y (x < y)
+};
+__device__ __forceinline__ bool pick_less(const Pick &u, const Pick &v) {
+  return u.q < v.q || (u.q == v.q && u.xy < v.xy);
+}
+__device__ __forceinline__ Pick warp_min(Pick p) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Pick o;
+    o.q = __shfl_xor_sync(MSA_FULL_MASK, p.q, off);
+    o.xy = __shfl_xor_sync(MSA_FULL_MASK, p.xy, off);
+    if (pick_less(o, p)) p = o;
+  }
+  return p;
+}
+__device__ __forceinline__ Pick block_min(Pick p, Pick *sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  p = warp_min(p);
+  if (lane == 0) sh[w] = p;
+  __syncthreads();
+  if (w == 0) {
+    p = lane < nw ? sh[lane] : Pick{LLONG_MAX, LLONG_MAX};
+    p = warp_min(p);
+  }
+  return p;  // valid in warp 0
+}
+
+// The active pair of smallest Q = (m - 2) d(x, y) - r_x - r_y, ties to the
+// smallest x, then y (positions ascend with the slots).  The last CTA to
+// finish reduces every CTA's minimum into sel = {x, y}.
+__global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__restrict__ D, int P,
+                                                           const long long *__restrict__ r,
+                                                           const uint8_t *__restrict__ act, int m,
+                                                           Pick *__restrict__ part,
+                                                           unsigned *__restrict__ ticket,
+                                                           int *__restrict__ sel) {
+  __shared__ Pick sh[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const long long f = m - 2;
+  Pick best{LLONG_MAX, LLONG_MAX};
+  for (int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < P; x += warps) {
+    if (!act[x]) continue;
+    const long long rx = r[x];
+    const long long *row = D + (size_t)x * P;
+    for (int y = x + 1 + lane; y < P; y += 32) {
+      if (!act[y]) continue;
+      const Pick c{f * row[y] - rx - r[y], ((long long)x << 32) | (long long)y};
+      if (pick_less(c, best)) best = c;
+    }
+  }
+  best = block_min(best, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = best;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  Pick p{LLONG_MAX, LLONG_MAX};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const Pick o{__ldcg(&part[b].q), __ldcg(&part[b].xy)};  // written by other CTAs
+    if (pick_less(o, p)) p = o;
+  }
+  __syncthreads();
+  p = block_min(p, sh);
+  if (threadIdx.x == 0) {
+    sel[0] = (int)(p.xy >> 32);
+    sel[1] = (int)(p.xy & 0xffffffffLL);
+    *ticket = 0;
+  }
+}
+
+// Join t of the positions sel = {x, y} (x < y): branch lengths, the new
+// node n + t in position x, its distances floor((d(x,k) + d(y,k) - d(x,y)) / 2),
+// the row sums, y retired.  One CTA.
+__global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict__ D, int P,
+                                                          long long *__restrict__ r,
+                                                          uint8_t *__restrict__ act,
+                                                          int *__restrict__ node, int m,
+                                                          const int *__restrict__ sel, int t, int n,
+                                                          int *__restrict__ joins,
+                                                          double *__restrict__ lengths,
+                                                          unsigned *__restrict__ err) {
+  __shared__ long long part[32];
+  const int x = sel[0], y = sel[1];
+  const long long dxy = D[(size_t)x * P + y], rx = r[x], ry = r[y];
+  if (threadIdx.x == 0) {
+    const long long f = m - 2;
+    const double den = (double)(2 * f);
+    lengths[2 * t] = (double)(f * dxy + rx - ry) / den;
+    lengths[2 * t + 1] = (double)(f * dxy - rx + ry) / den;
+    joins[2 * t] = node[x];
+    joins[2 * t + 1] = node[y];
+  }
+  long long sum = 0;
+  bool bad = false;
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    if (!act[k] || k == x || k == y) continue;
+    const long long dxk = D[(size_t)x * P + k], dyk = D[(size_t)y * P + k];
+    const long long dn = (dxk + dyk - dxy) >> 1;
+    bad |= dn > kDLimit || dn < -kDLimit;
+    D[(size_t)x * P + k] = dn;
+    D[(size_t)k * P + x] = dn;
+    r[k] += dn - dxk - dyk;
+    sum += dn;
+  }
+  if (bad) atomicOr(err, MSA_DERR_RANGE);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(MSA_FULL_MASK, sum, off);
+  if (lane == 0) part[w] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += part[i];
+    r[x] = s;
+    node[x] = n + t;
+    act[y] = 0;
+  }
+}
+
+// Positions of the active entries, ascending (one CTA; P <= 65536).
+__global__ void __launch_bounds__(1024) k_nj_index(const uint8_t *__restrict__ act, int P,
+                                                   int *__restrict__ idx) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < P; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int a = k < P && act[k] ? 1 : 0;
+    int incl = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(MSA_FULL_MASK, incl, d);
+      if (lane >= d) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int v = wsum[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int u = __shfl_up_sync(MSA_FULL_MASK, v, d);
+        if (lane >= d) v += u;
+      }
+      wsum[lane] = v;
+    }
+    __syncthreads();
+    const int before = carry + (w > 0 ? wsum[w - 1] : 0) + incl - a;
+    if (a) idx[before] = k;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wsum[31];
+    __syncthreads();
+  }
+}
+
+// The matrix, row sums and node ids packed to the m active positions.
+__global__ void k_nj_pack(const long long *__restrict__ D, int P, const long long *__restrict__ r,
+                          const int *__restrict__ node, const int *__restrict__ idx, int m,
+                          long long *__restrict__ D2, long long *__restrict__ r2,
+                          int *__restrict__ node2, uint8_t *__restrict__ act2) {
+  const int u = blockIdx.y;
+  const int su = idx[u];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m; v += gridDim.x * blockDim.x)
+    D2[(size_t)u * m + v] = D[(size_t)su * P + idx[v]];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    r2[u] = r[su];
+    node2[u] = node[su];
+    act2[u] = 1;
+  }
+}
+
+// The root: the two active positions joined at the middle of their edge.
+__global__ void k_nj_root(const long long *__restrict__ D, int P, const uint8_t *__restrict__ act,
+                          const int *__restrict__ node, int t, int *__restrict__ joins,
+                          double *__restrict__ lengths) {
+  if (threadIdx.x != 0) return;
+  int a = -1, b = -1;
+  for (int k = 0; k < P; ++k)
+    if (act[k]) {
+      if (a < 0) a = k;
+      else { b = k; break; }
+    }
+  if (a < 0 || b < 0) return;
+  const double half = (double)D[(size_t)a * P + b] / 2.0;
+  joins[2 * t] = node[a];
+  joins[2 * t + 1] = node[b];
+  lengths[2 * t] = half;
+  lengths[2 * t + 1] = half;
+}
+
+// Row sums (one warp per row), node ids, every position active.
+__global__ void k_nj_init(long long *__restrict__ r, const long long *__restrict__ D, int n,
+                          int *__restrict__ node, uint8_t *__restrict__ act) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    long long s = 0;
+    for (int j = lane; j < n; j += 32) s += j == k ? 0 : D[(size_t)k * n + j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(MSA_FULL_MASK, s, off);
+    if (lane == 0) {
+      r[k] = s;
+      node[k] = k;
+      act[k] = 1;
+    }
+  }
+}
+
+int tree_distances(msa_ctx *ctx, DevBuf &D) {
+  if (!ctx->merged) return fail(ctx, MSA_ESTATE, "merge the alignment first");
+  const int n = ctx->n;
+  TRY(ensure(ctx, D, sizeof(long long) * (size_t)n * n));
+  const int T = (n + kTile - 1) / kTile;
+  ++ctx->launches;
+  k_pdist<<<dim3(T, T), 256, 0, ctx->st>>>(P<uint8_t>(ctx->msa), n, ctx->W, P<long long>(D));
+  CK(cudaGetLastError());
+  return MSA_OK;
+}
+
+// Neighbour joining of the n x n matrix in D (device, int64, consumed).
+int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *lengths_out) {
+  if (n < 2) return MSA_OK;
+  DevBuf D2, r, r2, node, node2, act, act2, idx, part, sel, joins, lengths;
+  auto cleanup = [&]() {
+    for (DevBuf *b : {&D2, &r, &r2, &node, &node2, &act, &act2, &idx, &part, &sel, &joins, &lengths})
+      release(ctx, *b);
+  };
+  int rc = [&]() -> int {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
+    const int grid = std::max(1, sms) * 4;
+    TRY(ensure(ctx, r, sizeof(long long) * n));
+    TRY(ensure(ctx, node, sizeof(int) * n));
+    TRY(ensure(ctx, act, (size_t)n));
+    TRY(ensure(ctx, idx, sizeof(int) * n));
+    TRY(ensure(ctx, part, sizeof(Pick) * grid));
+    TRY(ensure(ctx, sel, sizeof(int) * 2 + sizeof(unsigned)));
+    TRY(ensure(ctx, joins, sizeof(int) * 2 * (size_t)(n - 1)));
+    TRY(ensure(ctx, lengths, sizeof(double) * 2 * (size_t)(n - 1)));
+    unsigned *ticket = reinterpret_cast<unsigned *>(P<int>(sel) + 2);
+    CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), ctx->st));
+    CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+    ++ctx->launches;
+    k_nj_init<<<grid, 256, 0, ctx->st>>>(P<long long>(r), P<long long>(D), n, P<int>(node),
+                                         P<uint8_t>(act));
+    CK(cudaGetLastError());
+    DevBuf *cD = &D, *cR = &r, *cN = &node, *cA = &act;
+    DevBuf *oD = &D2, *oR = &r2, *oN = &node2, *oA = &act2;
+    int Pn = n, m = n, t = 0;
+    while (m > 2) {
+      ctx->launches += 2;
+      k_nj_argmin<<<grid, kArgThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
+                                                     P<uint8_t>(*cA), m, P<Pick>(part), ticket,
+                                                     P<int>(sel));
+      CK(cudaGetLastError());
+      k_nj_join<<<1, kJoinThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
+                                                 P<uint8_t>(*cA), P<int>(*cN), m, P<int>(sel), t, n,
+                                                 P<int>(joins), P<double>(lengths), ctx->derr);
+      CK(cudaGetLastError());
+      --m;
+      ++t;
+      if (m > 2 && Pn >= 512 && m <= Pn / 2) {  // pack to the active positions
+        TRY(ensure(ctx, *oD, sizeof(long long) * (size_t)m * m));
+        TRY(ensure(ctx, *oR, sizeof(long long) * m));
+        TRY(ensure(ctx, *oN, sizeof(int) * m));
+        TRY(ensure(ctx, *oA, (size_t)m));
+        ctx->launches += 2;
+        k_nj_index<<<1, 1024, 0, ctx->st>>>(P<uint8_t>(*cA), Pn, P<int>(idx));
+        CK(cudaGetLastError());
+        k_nj_pack<<<dim3((m + 255) / 256, m), 256, 0, ctx->st>>>(
+            P<long long>(*cD), Pn, P<long long>(*cR), P<int>(*cN), P<int>(idx), m, P<long long>(*oD),
+            P<long long>(*oR), P<int>(*oN), P<uint8_t>(*oA));
+        CK(cudaGetLastError());
+        std::swap(cD, oD);
+        std::swap(cR, oR);
+        std::swap(cN, oN);
+        std::swap(cA, oA);
+        Pn = m;
+      }
+    }
+    ++ctx->launches;
+    k_nj_root<<<1, 32, 0, ctx->st>>>(P<long long>(*cD), Pn, P<uint8_t>(*cA), P<int>(*cN), t,
+                                      P<int>(joins), P<double>(lengths));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(joins_out, joins.p, sizeof(int) * 2 * (size_t)(n - 1), cudaMemcpyDefault,
+                       ctx->st));
+    CK(cudaMemcpyAsync(lengths_out, lengths.p, sizeof(double) * 2 * (size_t)(n - 1),
+                       cudaMemcpyDefault, ctx->st));
+    TRY(check_derr(ctx));
+    return MSA_OK;
+  }();
+  cleanup();
+  return rc;
+}
+
+}  // namespace
+}  // namespace msa_detail
+
+using namespace msa_detail;
+
+int msa_tree_distances(msa_ctx *ctx, int64_t *dist_out) {
+  if (!ctx || !dist_out) return MSA_EINVAL;
+  TRY(set_device(ctx));
+  DevBuf D;
+  int rc = [&]() -> int {
+    stage_begin(ctx, ST_TREE);
+    TRY(tree_distances(ctx, D));
+    stage_end(ctx, ST_TREE);
+    const size_t n = ctx->n;
+    CK(cudaMemcpyAsync(dist_out, D.p, sizeof(long long) * n * n, cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_TREE);
+    return MSA_OK;
+  }();
+  release(ctx, D);
+  return rc;
+}
+
+int msa_nj(msa_ctx *ctx, const int64_t *dist, int64_t n, int32_t *joins_out, double *lengths_out) {
+  if (!ctx || !dist || n < 1 || n > kMaxTreeRows || ((!joins_out || !lengths_out) && n > 1))
+    return MSA_EINVAL;
+  TRY(set_device(ctx));
+  DevBuf D;
+  int rc = [&]() -> int {
+    TRY(ensure(ctx, D, sizeof(long long) * (size_t)n * n));
+    CK(cudaMemcpyAsync(D.p, dist, sizeof(long long) * (size_t)n * n, cudaMemcpyDefault, ctx->st));
+    stage_begin(ctx, ST_TREE);
+    TRY(nj_device(ctx, D, (int)n, joins_out, lengths_out));
+    stage_end(ctx, ST_TREE);
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_TREE);
+    return MSA_OK;
+  }();
+  release(ctx, D);
+  return rc;
+}
+
+int msa_nj_tree(msa_ctx *ctx, int32_t *joins_out, double *lengths_out) {
+  if (!ctx) return MSA_EINVAL;
+  if (ctx->n > 1 && (!joins_out || !lengths_out)) return MSA_EINVAL;
+  if (ctx->n > kMaxTreeRows) return fail(ctx, MSA_ERANGE, "more than %d sequences", kMaxTreeRows);
+  TRY(set_device(ctx));
+  DevBuf D;
+  int rc = [&]() -> int {
+    stage_begin(ctx, ST_TREE);
+    TRY(tree_distances(ctx, D));
+    TRY(nj_device(ctx, D, ctx->n, joins_out, lengths_out));
+    stage_end(ctx, ST_TREE);
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_TREE);
+    return MSA_OK;
+  }();
+  release(ctx, D);
+  return rc;
+}
