@@ -3,6 +3,7 @@
 // merge of inserted spaces into the "longest" center, MSA rows, the
 // sum-of-pairs cost, and the distance row sums of center selection.
 #include "msa_kernels.cuh"
+#include <algorithm>
 #include <climits>
 
 namespace {
@@ -220,6 +221,68 @@ __global__ void k_rows(const uint8_t *__restrict__ res, const int64_t *__restric
   }
 }
 
+// The same rows assembled in shared memory, one warp per row: the warp fills
+// the row with '-' (16-byte stores), each lane writes its slots' residues
+// (inserted ones left-justified, then the center column's), and the warp
+// copies the row out with 16-byte stores where the row's bytes cover a whole
+// aligned chunk (byte stores at the two ragged ends, which neighbour other
+// rows).  `rowbytes` = W rounded up to 16, plus 16.
+__global__ void k_rows_staged(const uint8_t *__restrict__ res, const int64_t *__restrict__ pstart,
+                              const int32_t *__restrict__ inv, const uint16_t *__restrict__ ins,
+                              const uint8_t *__restrict__ occ, const int32_t *__restrict__ off,
+                              int n, int Lc, int64_t W, int rowbytes,
+                              const char *__restrict__ letters, uint8_t *__restrict__ out) {
+  extern __shared__ __align__(16) uint8_t srows[];
+  __shared__ char sl[MSA_MAX_ALPHABET + 1];
+  if (threadIdx.x < MSA_MAX_ALPHABET + 1) sl[threadIdx.x] = letters[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  uint8_t *buf = srows + (size_t)(threadIdx.x >> 5) * rowbytes;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const uint4 gaps = make_uint4(0x2d2d2d2du, 0x2d2d2d2du, 0x2d2d2d2du, 0x2d2d2d2du);
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += warps) {
+    uint8_t *row = out + (size_t)t * W;
+    // the row starts a = row mod 16 bytes into the buffer, so buffer and
+    // global chunks line up
+    const int a = (int)((uintptr_t)row & 15);
+    for (int c = lane; c < rowbytes / 16; c += 32) reinterpret_cast<uint4 *>(buf)[c] = gaps;
+    __syncwarp();
+    const uint8_t *s = res + pstart[inv[t]];
+    const uint16_t *in = ins + (size_t)t * (Lc + 1);
+    const uint8_t *oc = occ + (size_t)t * (Lc + 1);
+    int carry = 0;
+    for (int base = 0; base <= Lc; base += 32) {
+      const int j = base + lane;
+      int ni = 0, no = 0;
+      if (j <= Lc) { ni = in[j]; no = j < Lc ? oc[j + 1] : 0; }
+      const int cnt = ni + no;
+      int incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(MSA_FULL_MASK, incl, d);
+        if (lane >= d) incl += v;
+      }
+      if (j <= Lc) {
+        const int k0 = carry + incl - cnt;
+        uint8_t *dst = buf + a + off[j];
+        for (int u = 0; u < ni; ++u) dst[u] = (uint8_t)sl[s[k0 + u]];
+        if (no) buf[a + off[j] + (j < Lc ? (off[j + 1] - off[j] - 1) : 0)] = (uint8_t)sl[s[k0 + ni]];
+      }
+      carry += __shfl_sync(MSA_FULL_MASK, incl, 31);
+    }
+    __syncwarp();
+    // copy out: bytes [0, W) of the row sit at buf[a .. a + W)
+    const int64_t first = a ? 16 - a : 0;           // bytes before the first aligned chunk
+    const int64_t nfull = W > first ? (W - first) / 16 : 0;
+    const int64_t tail0 = first + nfull * 16;       // first byte after the last full chunk
+    for (int64_t c = lane; c < nfull; c += 32)
+      reinterpret_cast<uint4 *>(row + first)[c] = reinterpret_cast<const uint4 *>(buf + a + first)[c];
+    if (lane < first && lane < W) row[lane] = buf[a + lane];
+    for (int64_t x = tail0 + lane; x < W; x += 32) row[x] = buf[a + x];
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------- SP
 // Per column symbol counts (letters and '-'), accumulated over row chunks.
 __global__ void k_sp_count(const uint8_t *__restrict__ msa, int n, int64_t W,
@@ -386,6 +449,17 @@ cudaError_t launch_rows(const uint8_t *res, const int64_t *pstart, const int32_t
                         const uint16_t *ins, const uint8_t *occ, const int32_t *G,
                         const int32_t *off, int n, int Lc, int64_t W, const char *letters,
                         uint8_t *out, cudaStream_t st) {
+  const int64_t rowbytes = (W + 15) / 16 * 16 + 16;
+  if (rowbytes <= 96 * 1024) {  // rows staged in shared memory, 1-8 warps per CTA
+    const int warps = (int)std::max<int64_t>(1, std::min<int64_t>(8, (96 * 1024) / rowbytes));
+    const int smem = warps * (int)rowbytes;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute((const void *)k_rows_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int blocks = blocks_for((int64_t)n * 32, warps * 32, 8192);
+    k_rows_staged<<<blocks, warps * 32, smem, st>>>(res, pstart, inv, ins, occ, off, n, Lc, W,
+                                                    (int)rowbytes, letters, out);
+    return cudaGetLastError();
+  }
   const int threads = 256;
   const int blocks = blocks_for((int64_t)n * 32, threads, 8192);
   k_rows<<<blocks, threads, 0, st>>>(res, pstart, inv, ins, occ, G, off, n, Lc, W, letters, out);

@@ -13,10 +13,11 @@
 // Neighbour joining: the matrix stays on the device (int64, positions in
 // ascending slot order); every join is two launches -- the minimum of Q over
 // the active pairs (one warp per row, lanes along it, the last CTA to finish
-// reduces the CTAs' minima) and the join itself (one CTA: branch lengths,
-// the new node's row and column, the row sums updated in place).  When half
-// the positions are inactive the matrix is packed to the active ones, which
-// keeps the work of a join near m^2 / 2.  No launch waits on another.
+// reduces the CTAs' minima) and the join itself (CTAs over the rows: branch lengths,
+// the new node's row and column, the row sums updated in place; the last
+// CTA to finish adds up the new node's row sum).  When a quarter of the
+// positions are inactive the matrix is packed to the active ones, which keeps
+// the work of a join near m^2 / 2.  No launch waits on another.
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -161,10 +162,23 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__re
     if (!act[x]) continue;
     const long long rx = r[x];
     const long long *row = D + (size_t)x * P;
-    for (int y = x + 1 + lane; y < P; y += 32) {
-      if (!act[y]) continue;
-      const Pick c{f * row[y] - rx - r[y], ((long long)x << 32) | (long long)y};
-      if (pick_less(c, best)) best = c;
+    // four independent loads per lane in flight
+    for (int y0 = x + 1 + lane; y0 < P; y0 += 128) {
+      long long dv[4], rv[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int y = y0 + 32 * u;
+        ok[u] = y < P && act[y];
+        dv[u] = ok[u] ? row[y] : 0;
+        rv[u] = ok[u] ? r[y] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int y = y0 + 32 * u;
+        const Pick c{f * dv[u] - rx - rv[u], ((long long)x << 32) | (long long)y};
+        if (ok[u] && pick_less(c, best)) best = c;
+      }
     }
   }
   best = block_min(best, sh);
@@ -192,7 +206,8 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__re
 
 // Join t of the positions sel = {x, y} (x < y): branch lengths, the new
 // node n + t in position x, its distances floor((d(x,k) + d(y,k) - d(x,y)) / 2),
-// the row sums, y retired.  One CTA.
+// the row sums, y retired.  CTAs take ranges of k; the last CTA to finish
+// adds up their sums into r_x (every CTA has read r_x by then).
 __global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict__ D, int P,
                                                           long long *__restrict__ r,
                                                           uint8_t *__restrict__ act,
@@ -200,11 +215,14 @@ __global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict_
                                                           const int *__restrict__ sel, int t, int n,
                                                           int *__restrict__ joins,
                                                           double *__restrict__ lengths,
+                                                          long long *__restrict__ part,
+                                                          unsigned *__restrict__ ticket,
                                                           unsigned *__restrict__ err) {
-  __shared__ long long part[32];
+  __shared__ long long wsum[kJoinThreads / 32];
+  __shared__ bool last;
   const int x = sel[0], y = sel[1];
   const long long dxy = D[(size_t)x * P + y], rx = r[x], ry = r[y];
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     const long long f = m - 2;
     const double den = (double)(2 * f);
     lengths[2 * t] = (double)(f * dxy + rx - ry) / den;
@@ -214,7 +232,7 @@ __global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict_
   }
   long long sum = 0;
   bool bad = false;
-  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
     if (!act[k] || k == x || k == y) continue;
     const long long dxk = D[(size_t)x * P + k], dyk = D[(size_t)y * P + k];
     const long long dn = (dxk + dyk - dxy) >> 1;
@@ -228,15 +246,24 @@ __global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict_
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(MSA_FULL_MASK, sum, off);
-  if (lane == 0) part[w] = sum;
+  if (lane == 0) wsum[w] = sum;
   __syncthreads();
   if (threadIdx.x == 0) {
     long long s = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += part[i];
-    r[x] = s;
-    node[x] = n + t;
-    act[y] = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += wsum[i];
+    part[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  long long s = 0;
+  for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&part[b]);
+  r[x] = s;
+  node[x] = n + t;
+  act[y] = 0;
+  *ticket = 0;
 }
 
 // Positions of the active entries, ascending (one CTA; P <= 65536).
@@ -343,25 +370,28 @@ int tree_distances(msa_ctx *ctx, DevBuf &D) {
 // Neighbour joining of the n x n matrix in D (device, int64, consumed).
 int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *lengths_out) {
   if (n < 2) return MSA_OK;
-  DevBuf D2, r, r2, node, node2, act, act2, idx, part, sel, joins, lengths;
+  DevBuf D2, r, r2, node, node2, act, act2, idx, part, jpart, sel, joins, lengths;
   auto cleanup = [&]() {
-    for (DevBuf *b : {&D2, &r, &r2, &node, &node2, &act, &act2, &idx, &part, &sel, &joins, &lengths})
+    for (DevBuf *b : {&D2, &r, &r2, &node, &node2, &act, &act2, &idx, &part, &jpart, &sel, &joins,
+                      &lengths})
       release(ctx, *b);
   };
   int rc = [&]() -> int {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
-    const int grid = std::max(1, sms) * 4;
+    const int grid = std::max(1, sms) * 8;
+    const int jmax = std::max(1, sms);  // CTAs of a join
     TRY(ensure(ctx, r, sizeof(long long) * n));
     TRY(ensure(ctx, node, sizeof(int) * n));
     TRY(ensure(ctx, act, (size_t)n));
     TRY(ensure(ctx, idx, sizeof(int) * n));
     TRY(ensure(ctx, part, sizeof(Pick) * grid));
-    TRY(ensure(ctx, sel, sizeof(int) * 2 + sizeof(unsigned)));
+    TRY(ensure(ctx, sel, sizeof(int) * 2 + 2 * sizeof(unsigned)));
+    TRY(ensure(ctx, jpart, sizeof(long long) * jmax));
     TRY(ensure(ctx, joins, sizeof(int) * 2 * (size_t)(n - 1)));
     TRY(ensure(ctx, lengths, sizeof(double) * 2 * (size_t)(n - 1)));
     unsigned *ticket = reinterpret_cast<unsigned *>(P<int>(sel) + 2);
-    CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), ctx->st));
+    CK(cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned), ctx->st));
     CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
     ++ctx->launches;
     k_nj_init<<<grid, 256, 0, ctx->st>>>(P<long long>(r), P<long long>(D), n, P<int>(node),
@@ -372,17 +402,21 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
     int Pn = n, m = n, t = 0;
     while (m > 2) {
       ctx->launches += 2;
-      k_nj_argmin<<<grid, kArgThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
+      // a warp per row at least: small matrices take few CTAs
+      const int agrid = std::max(1, std::min(grid, (Pn + kArgThreads / 32 - 1) / (kArgThreads / 32)));
+      k_nj_argmin<<<agrid, kArgThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
                                                      P<uint8_t>(*cA), m, P<Pick>(part), ticket,
                                                      P<int>(sel));
       CK(cudaGetLastError());
-      k_nj_join<<<1, kJoinThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
-                                                 P<uint8_t>(*cA), P<int>(*cN), m, P<int>(sel), t, n,
-                                                 P<int>(joins), P<double>(lengths), ctx->derr);
+      const int jgrid = std::max(1, std::min(jmax, (Pn + kJoinThreads - 1) / kJoinThreads));
+      k_nj_join<<<jgrid, kJoinThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
+                                                     P<uint8_t>(*cA), P<int>(*cN), m, P<int>(sel), t,
+                                                     n, P<int>(joins), P<double>(lengths),
+                                                     P<long long>(jpart), ticket + 1, ctx->derr);
       CK(cudaGetLastError());
       --m;
       ++t;
-      if (m > 2 && Pn >= 512 && m <= Pn / 2) {  // pack to the active positions
+      if (m > 2 && Pn >= 512 && 4 * m <= 3 * Pn) {  // pack to the active positions
         TRY(ensure(ctx, *oD, sizeof(long long) * (size_t)m * m));
         TRY(ensure(ctx, *oR, sizeof(long long) * m));
         TRY(ensure(ctx, *oN, sizeof(int) * m));
