@@ -313,10 +313,11 @@ def align_record(flush, stream, peak_gbs, no_tune=False):
     gcups = cells / (k * 1e-3) / 1e9
     tuned = None
     if tune is not None:
-        rates, (lanes, packed) = tune
-        tuned = {"choice": {"lanes": lanes, "cells": "int16x2" if packed else "int32"},
+        rates, (lanes, packed, cta) = tune
+        tuned = {"choice": {"lanes": lanes, "cells": "int16x2" if packed else "int32",
+                            "threads": cta},
                  "gcups": {"%s_G%d" % (p, G): float(rates[i, g]) / 1e9
-                           for i, p in enumerate(("int16x2", "int32"))
+                           for i, p in enumerate(("int16x2", "int32", "int16x2_t384"))
                            for g, G in enumerate(b.ALIGN_LANES)
                            if rates[i, g] > 0}}
     return {"autotune": tuned, "workload": "%d short peptides (lognormal lengths median 90 sigma 0.6 clipped 30-200, "
@@ -669,10 +670,11 @@ def run_ours(args):
     align_tune = None
     if not args.no_autotune:
         c0, _, _ = step_device()
-        rates_a, (lanes_a, packed_a) = b.msa_align_autotune(h, c0)
-        align_tune = {"choice": {"lanes": lanes_a, "cells": "int16x2" if packed_a else "int32"},
+        rates_a, (lanes_a, packed_a, cta_a) = b.msa_align_autotune(h, c0)
+        align_tune = {"choice": {"lanes": lanes_a, "cells": "int16x2" if packed_a else "int32",
+                                 "threads": cta_a},
                       "gcups": {"%s_G%d" % (p, G): float(rates_a[i, g]) / 1e9
-                                for i, p in enumerate(("int16x2", "int32"))
+                                for i, p in enumerate(("int16x2", "int32", "int16x2_t384"))
                                 for g, G in enumerate(b.ALIGN_LANES)
                                 if rates_a[i, g] > 0}}
     tune_s = time.perf_counter() - t0

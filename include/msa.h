@@ -387,12 +387,15 @@ int msa_set_codes_budget(msa_ctx *ctx, int64_t bytes);
  * lanes (1 lane: the inter-sequence mode, every lane aligning its own
  * subjects; more lanes: an anti-diagonal wavefront over the group), in
  * packed int16x2 cells (where they fit the center's length) and in int32
- * cells, and keeps the fastest shape and precision for later alignments on
- * this context (msa_set_align_group overrides the shape).  rates_out
- * (nullable, host double[2][6]): cells per second, [packed, int32] x
- * [1, 2, 4, 8, 16, 32] lanes (fill and traceback), 0 where not timed; choice_out
- * (nullable, host int32[2]): {lanes, 1 if packed}.  The results do not
- * depend on the choice.  Leaves no alignment behind (align again). */
+ * cells, the packed kernel also in 384-thread CTAs (8 to 32 lanes), and keeps
+ * the fastest shape, precision and CTA size for later alignments on this
+ * context (msa_set_align_group and msa_set_align_threads override them).
+ * rates_out (nullable, host double[3][6]): cells per second (fill and
+ * traceback), rows [packed, int32, packed in 384-thread CTAs] x
+ * [1, 2, 4, 8, 16, 32] lanes, 0 where not timed; choice_out
+ * (nullable, host int32[3]): {lanes, 1 if packed, threads per CTA}.  The
+ * results do not depend on the choice.  Leaves no alignment behind (align
+ * again). */
 int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t *choice_out);
 
 /* Lanes per subject group of the alignment kernels (1, 2, 4, 8, 16 or 32;
@@ -401,6 +404,11 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
  * choice of the library's cost model among 8, 16 and 32 (the default).  A tuning knob: the
  * result does not depend on it.  EINVAL for any other value. */
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes);
+
+/* Threads per CTA of the packed alignment kernel with groups of 8 lanes or
+ * more: 256 (the default; 0 means the same) or 384.  A tuning knob: the result
+ * does not depend on it.  EINVAL for any other value. */
+int msa_set_align_threads(msa_ctx *ctx, int32_t threads);
 
 /* Distances between the rows of the merged MSA for the phylogenetic tree
  * (the paper's section on NJ trees, Figure 4: the tree is built from the

@@ -78,6 +78,7 @@ _SIGS = {
     "msa_set_align_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "msa_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_tree_distances": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_set_align_threads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "msa_nj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                               ctypes.c_void_p]),
     "msa_nj_tree": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -258,11 +259,19 @@ ALIGN_LANES = (1, 2, 4, 8, 16, 32)  # lanes per subject group of the alignment k
 
 
 def msa_align_autotune(ctx, center):
-    """(rates double[2, 6] = [packed, int32] x [1, 2, 4, 8, 16, 32] lanes, (lanes, packed))."""
-    rates = np.zeros((2, len(ALIGN_LANES)), np.float64)
-    choice = np.zeros(2, np.int32)
+    """(rates double[3, 6] = [packed, int32, packed in 384-thread CTAs] x
+    [1, 2, 4, 8, 16, 32] lanes, (lanes, packed, threads per CTA))."""
+    rates = np.zeros((3, len(ALIGN_LANES)), np.float64)
+    choice = np.zeros(3, np.int32)
     _check(ctx, lib().msa_align_autotune(ctx, int(center), _ptr(rates), _ptr(choice)))
-    return rates, (int(choice[0]), bool(choice[1]))
+    return rates, (int(choice[0]), bool(choice[1]), int(choice[2]))
+
+
+def msa_set_align_threads(ctx, threads):
+    """Threads per CTA of the packed alignment kernel (256 or 384; 0 = 256)."""
+    rc = lib().msa_set_align_threads(ctx, int(threads))
+    if rc != MSA_OK:
+        raise MSAError(rc, "align threads must be 0, 256 or 384")
 
 
 def msa_center_partial(ctx, shard, nshards, refs=None, out=None):

@@ -309,9 +309,10 @@ int align_subset_local(msa_ctx *ctx, int kc, const std::vector<int32_t> &subj, f
     const SeqSet vss{P<uint8_t>(ctx->res), P<int64_t>(vs), P<int32_t>(vl), nv};
     const Scoring sc = scoring(ctx);
     const int smem = codes_smem_bytes(ctx->K, npass * G * R);
-    const int grid = codes_grid(G, packed, smem);
+    const int cta = align_cta(ctx, G, packed);
+    const int grid = codes_grid(G, packed, smem, cta);
     if (npass > 1)
-      TRY(ensure(ctx, ctx->scratch, (size_t)grid * (codes_threads(packed) / G) * 2 * ctx->maxlen * sizeof(int2)));
+      TRY(ensure(ctx, ctx->scratch, (size_t)grid * (codes_threads(packed, cta) / G) * 2 * ctx->maxlen * sizeof(int2)));
     CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
     CodesJob job;
     job.center = nv - 1;
@@ -326,7 +327,7 @@ int align_subset_local(msa_ctx *ctx, int kc, const std::vector<int32_t> &subj, f
     job.scratch_cols = ctx->maxlen;
     cudaEvent_t e0 = ctx->ev[2 * ST_TRACE], e1 = ctx->ev[2 * ST_TRACE + 1];
     CK(cudaEventRecord(e0, ctx->st));
-    CK((++ctx->launches, launch_codes)(G, packed, vss, sc, job, grid, ctx->st, true));
+    CK((++ctx->launches, launch_codes)(G, packed, vss, sc, job, grid, ctx->st, true, cta));
     CK((++ctx->launches, launch_traceback)(P<uint8_t>(ctx->codes), P<int64_t>(vo),
                                            P<unsigned long long>(ctx->best), 0, nv - 1,
                                            P<int32_t>(vl), P<int32_t>(vp), vss.res, vss.pstart,

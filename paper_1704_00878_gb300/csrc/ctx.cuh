@@ -90,6 +90,7 @@ struct msa_ctx {
   size_t codes_budget = (size_t)32 << 30;
   int align_group = 0;  // lanes per subject group of the codes kernels, 0 = modelled choice
   int align_int32 = 0;  // 1: the alignment uses int32 cells even where packed ones fit
+  int align_threads = 0;  // CTA size of the packed codes kernel, 0 = kCodes2Threads
 
   msa_detail::Selector *sel = nullptr;
 
@@ -136,6 +137,8 @@ int check_derr(msa_ctx *ctx);
 // cell precision and lanes per group of the alignment to a center of length Lc
 bool align_packed(msa_ctx *ctx, int Lc);
 int align_lanes(msa_ctx *ctx, int Lc, bool packed);
+// CTA size of the codes kernel for this group width and precision
+int align_cta(msa_ctx *ctx, int G, bool packed);
 SeqSet seqset(msa_ctx *ctx);
 Scoring scoring(msa_ctx *ctx);
 

@@ -227,6 +227,10 @@ static int align_group(msa_ctx *ctx, int Lc, bool packed) {
 }
 
 bool align_packed(msa_ctx *ctx, int Lc) { return codes_packed(ctx, Lc); }
+int align_cta(msa_ctx *ctx, int G, bool packed) {
+  return packed && G >= 8 && ctx->align_threads == kCodes2WideThreads ? kCodes2WideThreads
+                                                                      : kCodes2Threads;
+}
 int align_lanes(msa_ctx *ctx, int Lc, bool packed) { return align_group(ctx, Lc, packed); }
 
 bool use_packed(msa_ctx *ctx, int Lq) {
@@ -1133,9 +1137,10 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   const SeqSet ss = seqset(ctx);
   const Scoring sc = scoring(ctx);
   const int smem = codes_smem_bytes(ctx->K, npass * G * R);
-  const int grid = codes_grid(G, packed, smem);
+  const int cta = align_cta(ctx, G, packed);
+  const int grid = codes_grid(G, packed, smem, cta);
   if (npass > 1)
-    TRY(ensure(ctx, ctx->scratch, (size_t)grid * (codes_threads(packed) / G) * 2 * ctx->maxlen * sizeof(int2)));
+    TRY(ensure(ctx, ctx->scratch, (size_t)grid * (codes_threads(packed, cta) / G) * 2 * ctx->maxlen * sizeof(int2)));
   float ms_dp = 0.f, ms_tb = 0.f;
   int64_t cells = 0;
   for (int k = 0; k < n; ++k) cells += (int64_t)Lc * ctx->len_sorted[k];
@@ -1149,14 +1154,14 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
     CK(cudaEventCreate(&ev));
     ctx->align_ev.push_back(ev);
   }
-  std::vector<int64_t> key = {kc, Lc, packed, G, npass, grid, smem, n, (int64_t)ss.res,
+  std::vector<int64_t> key = {kc, Lc, packed, G, cta, npass, grid, smem, n, (int64_t)ss.res,
                               (int64_t)ss.pstart, (int64_t)ss.len, (int64_t)sc.M, sc.K, sc.o, sc.e,
                               (int64_t)ctx->codes.p, (int64_t)ctx->code_off.p, (int64_t)ctx->best.p,
                               (int64_t)ctx->ins.p, (int64_t)ctx->occ.p, (int64_t)ctx->seg.p,
                               (int64_t)ctx->score.p, (int64_t)ctx->scratch.p, (int64_t)ctx->derr,
                               (int64_t)ctx->dcounter, (int64_t)ctx->d_perm.p, ctx->maxlen};
   for (auto [sb, se] : batches) { key.push_back(sb); key.push_back(se); }
-  CK(codes_allow_smem(G, packed, smem));
+  CK(codes_allow_smem(G, packed, smem, cta));
   if (!ctx->align_exec || key != ctx->align_key) {
     if (ctx->align_exec) {
       CK(cudaStreamSynchronize(ctx->st));
@@ -1182,7 +1187,7 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
       e = cudaEventRecordWithFlags(ctx->align_ev[3 * bi], ctx->cap_st, cudaEventRecordExternal);
       if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->cap_st);
       // offsets inside the batch are relative to the batch start
-      if (e == cudaSuccess) e = launch_codes(G, packed, ss, sc, job, grid, ctx->cap_st, false);
+      if (e == cudaSuccess) e = launch_codes(G, packed, ss, sc, job, grid, ctx->cap_st, false, cta);
       if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->align_ev[3 * bi + 1], ctx->cap_st, cudaEventRecordExternal);
       if (e == cudaSuccess)
         e = launch_traceback(P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + sb,
@@ -1277,8 +1282,9 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
     const int smem = codes_smem_bytes(ctx->K, npass * G * R);
     const int grid = 1;
+    const int cta = align_cta(ctx, G, packed);
     if (npass > 1)
-      TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, packed, smem) * (codes_threads(packed) / G) *
+      TRY(ensure(ctx, ctx->scratch, (size_t)codes_grid(G, packed, smem, cta) * (codes_threads(packed, cta) / G) *
                                         2 * ctx->maxlen * sizeof(int2)));
     CodesJob job;
     job.center = kc;
@@ -1291,7 +1297,7 @@ int msa_debug_codes(msa_ctx *ctx, int64_t seq, uint8_t *codes_out) {
     job.counter = ctx->dcounter;
     job.scratch = P<int2>(ctx->scratch);
     job.scratch_cols = ctx->maxlen;
-    CK((++ctx->launches, launch_codes)(G, packed, seqset(ctx), scoring(ctx), job, grid, ctx->st, true));
+    CK((++ctx->launches, launch_codes)(G, packed, seqset(ctx), scoring(ctx), job, grid, ctx->st, true, cta));
     std::vector<uint8_t> raw(bytes), out((size_t)Lc * Ls);
     CK(cudaMemcpyAsync(raw.data(), cb.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -1470,30 +1476,47 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
   const int Lc = ctx->len_sorted[ctx->inv[center]];
   ctx->align_int32 = 0;
   const bool can_pack = codes_packed(ctx, Lc);
-  double rates[2][kAlignWidths] = {};
+  // rows: packed cells in 256-thread CTAs, int32 cells, packed cells in
+  // 384-thread CTAs (groups of 8 lanes and more)
+  double rates[3][kAlignWidths] = {};
   double best = -1.0;
-  int best_g = 32, best_i32 = 0;
-  for (int i32 = 0; i32 < 2; ++i32) {
+  int best_g = 32, best_i32 = 0, best_cta = 0;
+  for (int row = 0; row < 3; ++row) {
+    const int i32 = row == 1 ? 1 : 0;
     if (i32 == 0 && !can_pack) continue;
     for (int gi = 0; gi < kAlignWidths; ++gi) {
       const int G = 1 << gi;
+      if (row == 2 && G < 8) continue;
       ctx->align_int32 = i32;
       ctx->align_group = G;
+      ctx->align_threads = row == 2 ? kCodes2WideThreads : 0;
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {  // the second run is timed
         TRY(msa_align_to_center(ctx, center, nullptr));
         ms = ctx->stage_ms[ST_ALIGN_K] + ctx->stage_ms[ST_TRACE];
       }
       const double r = ms > 0.f ? (double)ctx->cells[1] / (ms * 1e-3) : 0.0;
-      rates[i32][gi] = r;
-      if (r > best) { best = r; best_g = G; best_i32 = i32; }
+      rates[row][gi] = r;
+      if (r > best) { best = r; best_g = G; best_i32 = i32; best_cta = ctx->align_threads; }
     }
   }
   ctx->align_group = best_g;
   ctx->align_int32 = best_i32;
+  ctx->align_threads = best_cta;
   ctx->aligned = false;
   if (rates_out) memcpy(rates_out, rates, sizeof rates);
-  if (choice_out) { choice_out[0] = best_g; choice_out[1] = best_i32 ? 0 : 1; }
+  if (choice_out) {
+    choice_out[0] = best_g;
+    choice_out[1] = best_i32 ? 0 : 1;
+    choice_out[2] = align_cta(ctx, best_g, !best_i32);
+  }
+  return MSA_OK;
+}
+
+int msa_set_align_threads(msa_ctx *ctx, int32_t threads) {
+  if (!ctx || (threads != 0 && threads != kCodes2Threads && threads != kCodes2WideThreads))
+    return MSA_EINVAL;
+  ctx->align_threads = threads == kCodes2Threads ? 0 : threads;
   return MSA_OK;
 }
 

@@ -964,14 +964,16 @@ __device__ __forceinline__ void codes_pass2(const int8_t *__restrict__ prof, int
   }
 }
 
-// kCodes2Threads threads per CTA; the kernel holds ~150 registers per thread
-// (one CTA, 8 warps, per SM; 12 warps in 384-thread CTAs measured slower, and
-// so did running several subject pairs back to back along one group's columns
-// to share the wavefront ramp: the lanes leave a pair at different steps, so
-// the per-pair bookkeeping runs once per lane).
-template <int G>
-__global__ void __launch_bounds__(kCodes2Threads, 1) k_codes2(SeqSet ss, Scoring sc, CodesJob job) {
-  constexpr int R = kCodesR, NT = kCodes2Threads, NG = NT / G, GPW = 32 / G;
+// NT threads per CTA, one CTA per SM: 256 (8 warps, ~210 registers) or 384
+// (12 warps, registers capped near 160 without spills; faster on many short
+// subjects, slower where few long ones leave the last warps' work unbalanced
+// -- the alignment tuner times both).  Running several subject pairs back to
+// back along one group's columns to share the wavefront ramp measured slower:
+// the lanes leave a pair at different steps, so the per-pair bookkeeping runs
+// once per lane.
+template <int G, int NT>
+__global__ void __launch_bounds__(NT, 1) k_codes2(SeqSet ss, Scoring sc, CodesJob job) {
+  constexpr int R = kCodesR, NG = NT / G, GPW = 32 / G;
   extern __shared__ __align__(16) int8_t smem[];
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
   const int K = sc.K, padc = K;
@@ -1162,24 +1164,32 @@ int codes_smem_bytes(int K, int rows_alloc) {
 }
 
 typedef void (*codes_fn)(SeqSet, Scoring, CodesJob);
-static codes_fn codes_kernel(int G, bool packed) {
+static codes_fn codes_kernel(int G, bool packed, int threads) {
+  if (packed && threads == kCodes2WideThreads) {
+    switch (G) {
+      case 8: return k_codes2<8, kCodes2WideThreads>;
+      case 16: return k_codes2<16, kCodes2WideThreads>;
+      case 32: return k_codes2<32, kCodes2WideThreads>;
+      default: return nullptr;
+    }
+  }
+  if (threads != kCodes2Threads) return nullptr;
   switch (G) {
-    case 1: return packed ? k_codes2<1> : k_codes<1>;
-    case 2: return packed ? k_codes2<2> : k_codes<2>;
-    case 4: return packed ? k_codes2<4> : k_codes<4>;
-    case 8: return packed ? k_codes2<8> : k_codes<8>;
-    case 16: return packed ? k_codes2<16> : k_codes<16>;
-    case 32: return packed ? k_codes2<32> : k_codes<32>;
+    case 1: return packed ? k_codes2<1, kCodes2Threads> : k_codes<1>;
+    case 2: return packed ? k_codes2<2, kCodes2Threads> : k_codes<2>;
+    case 4: return packed ? k_codes2<4, kCodes2Threads> : k_codes<4>;
+    case 8: return packed ? k_codes2<8, kCodes2Threads> : k_codes<8>;
+    case 16: return packed ? k_codes2<16, kCodes2Threads> : k_codes<16>;
+    case 32: return packed ? k_codes2<32, kCodes2Threads> : k_codes<32>;
     default: return nullptr;
   }
 }
 
+int codes_threads(bool packed, int threads) { return packed ? threads : 256; }
 
-int codes_threads(bool packed) { return packed ? kCodes2Threads : 256; }
-
-int codes_grid(int G, bool packed, int smem) {
-  codes_fn fn = codes_kernel(G, packed);
-  return fn ? occupancy_grid((const void *)fn, codes_threads(packed), smem) : 0;
+int codes_grid(int G, bool packed, int smem, int threads) {
+  codes_fn fn = codes_kernel(G, packed, threads);
+  return fn ? occupancy_grid((const void *)fn, codes_threads(packed, threads), smem) : 0;
 }
 
 // Group size for a center of length Lc.  A group of G lanes spends
@@ -1205,23 +1215,23 @@ int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_
   return best_g;
 }
 
-cudaError_t codes_allow_smem(int G, bool packed, int smem) {
-  codes_fn fn = codes_kernel(G, packed);
+cudaError_t codes_allow_smem(int G, bool packed, int smem, int threads) {
+  codes_fn fn = codes_kernel(G, packed, threads);
   if (!fn) return cudaErrorInvalidValue;
   if (smem <= 40 * 1024) return cudaSuccess;  // static shared memory counts too
   return cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc, const CodesJob &job,
-                         int grid, cudaStream_t st, bool set_smem) {
-  codes_fn fn = codes_kernel(G, packed);
+                         int grid, cudaStream_t st, bool set_smem, int threads) {
+  codes_fn fn = codes_kernel(G, packed, threads);
   if (!fn) return cudaErrorInvalidValue;
   const int smem = codes_smem_bytes(sc.K, job.npass * G * kCodesR);
   if (set_smem) {
-    const cudaError_t e = codes_allow_smem(G, packed, smem);
+    const cudaError_t e = codes_allow_smem(G, packed, smem, threads);
     if (e != cudaSuccess) return e;
   }
-  fn<<<grid, codes_threads(packed), smem, st>>>(ss, sc, job);
+  fn<<<grid, codes_threads(packed, threads), smem, st>>>(ss, sc, job);
   return cudaGetLastError();
 }
 

@@ -87,21 +87,24 @@ cudaError_t launch_pairs(int G, const SeqSet &ss, const Scoring &sc, const PairJ
 int pairs_grid(int G);
 int pairs_rows(int G);
 
-// G = threads per subject group (8, 16 or 32; codes_group picks it from the
+// G = threads per subject group (1, 2, 4, 8, 16 or 32; codes_group picks 8-32 from the
 // center length and the subject lengths); 16 center rows per thread.  packed: each group carries two
 // subjects in int16 lanes (the caller checks that every cell value fits).
 // set_smem = false: the caller has already raised the kernel's dynamic
 // shared-memory limit with codes_allow_smem (required while capturing).
+// threads: CTA size of the packed kernel (kCodes2Threads or, for G >= 8,
+// kCodes2WideThreads); the int32 kernel always runs kCodes2Threads.
 cudaError_t launch_codes(int G, bool packed, const SeqSet &ss, const Scoring &sc, const CodesJob &job,
-                         int grid, cudaStream_t st, bool set_smem = true);
-cudaError_t codes_allow_smem(int G, bool packed, int smem);
+                         int grid, cudaStream_t st, bool set_smem = true, int threads = 256);
+cudaError_t codes_allow_smem(int G, bool packed, int smem, int threads = 256);
 int codes_smem_bytes(int K, int rows_alloc);
-int codes_grid(int G, bool packed, int smem);
-int codes_threads(bool packed);  // threads per CTA of the codes kernels
+int codes_grid(int G, bool packed, int smem, int threads = 256);
+int codes_threads(bool packed, int threads = 256);  // threads per CTA of the codes kernels
 int codes_group(int Lc, bool packed, int K, int64_t n, double mean_len, int max_len);
 constexpr int kCodesR = 16;
 // lanes per subject the alignment kernels come in: 1, 2, 4, 8, 16, 32
 constexpr int kAlignWidths = 6;
-constexpr int kCodes2Threads = 256;  // packed codes kernel threads per CTA
+constexpr int kCodes2Threads = 256;      // codes kernel threads per CTA
+constexpr int kCodes2WideThreads = 384;  // the packed kernel's wider CTA
 constexpr int kPairsR = 16;
 constexpr int kCenterThreads = 256;

@@ -169,18 +169,23 @@ def test_msa_long_center_multipass():
     check_against_oracle(prob, center, *out)
 
 
-@pytest.mark.parametrize("budget,lanes", [(1, 8), (300_000, 32), (300_000, 16), (1, 1),
-                                          (300_000, 1), (300_000, 2), (300_000, 4)])
-def test_msa_in_code_batches(budget, lanes):
+@pytest.mark.parametrize("budget,lanes,cta", [(1, 8, 256), (300_000, 32, 256), (300_000, 16, 256),
+                                              (1, 1, 256), (300_000, 1, 256), (300_000, 2, 256),
+                                              (300_000, 4, 256), (1, 8, 384), (300_000, 16, 384),
+                                              (300_000, 32, 384)])
+def test_msa_in_code_batches(budget, lanes, cta):
     """Codes budgets that split the alignment into one subject per batch and
-    into a few batches, with each group width of the alignment kernels, give
-    the same MSA as the oracle."""
+    into a few batches, with each group width and CTA size of the alignment
+    kernels, give the same MSA as the oracle."""
     b = binding()
     letters, offsets, w, alph, M = workload("plain_protein_200", n=60, seed=12)
     prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
         b.msa_set_codes_budget(h, budget)
         b.msa_set_align_group(h, lanes)
+        b.msa_set_align_threads(h, cta)
+        with pytest.raises(b.MSAError):
+            b.msa_set_align_threads(h, 512)
         with pytest.raises(b.MSAError):
             b.msa_set_codes_budget(h, 0)
         for bad in (12, 3, 64, -1):
@@ -338,9 +343,10 @@ def test_autotuned_alignment_is_unchanged():
     center = 11
     with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
         b.msa_load(h, letters, offsets)
-        rates, (lanes, packed) = b.msa_align_autotune(h, center)
+        rates, (lanes, packed, cta) = b.msa_align_autotune(h, center)
         out = run_pipeline(b, h, letters, offsets, center)
-    assert rates.shape == (2, 6) and (rates > 0).sum() == 12 and lanes in b.ALIGN_LANES
+    assert rates.shape == (3, 6) and (rates > 0).sum() == 15 and lanes in b.ALIGN_LANES
+    assert cta in (256, 384) and (cta == 256 or (packed and lanes >= 8))
     check_against_oracle(prob, center, *out)
 
 
