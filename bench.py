@@ -117,6 +117,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuners (center variants per length bucket; alignment "
                          "group width and int16x2 / int32 cells) and use the cost models")
+    ap.add_argument("--align-threads", type=int, default=0,
+                    help="threads per CTA of the packed alignment kernel (256 or 384)")
+    ap.add_argument("--only-tree", action="store_true",
+                    help="time the neighbour-joining tree of the workload's MSA only")
     ap.add_argument("--no-tree-record", action="store_true",
                     help="skip the neighbour-joining tree of the step's MSA")
     ap.add_argument("--no-align-record", action="store_true",
@@ -562,6 +566,20 @@ def run_ours(args):
 
     if args.align_group:
         b.msa_set_align_group(h, args.align_group)
+    if args.align_threads:
+        b.msa_set_align_threads(h, args.align_threads)
+    if args.only_tree:
+        lens = np.diff(offsets)
+        center = int(np.argsort(lens, kind="stable")[len(lens) // 2])
+        b.msa_load(h, dlet, offsets)
+        b.msa_align_to_center(h, center)
+        _, Wt = b.msa_merge_gaps(h, want_rows=False)
+        for _ in range(max(1, args.warmup)):
+            rec = tree_record(b, h, n, Wt, stream, measured_peaks().get("hbm_gbs", 6800.0),
+                              cpu_n=min(n, 300))
+        print(json.dumps(dict(rec, only_tree=True)))
+        ctx.close()
+        return
     if args.only_align:
         lens = np.diff(offsets)
         center = 0 if (w.center_seq or args.center == "first") else \
