@@ -10,10 +10,12 @@
 // every (segment, position) match; the warp sorts the matches and runs the
 // longest-chain recurrence (a match's predecessor is the first compatible
 // match of the longest chains before it: increasing segment, sequence
-// positions at least k apart); each lane then aligns the stretches between
-// consecutive anchors globally (Gotoh, W = open + (n-1) extend, codes in
-// local memory, traceback from the end: diagonal, then F, then E; a gap
-// extends only when strictly better) and writes the inserted-space row.  The
+// positions at least k apart); the lanes mark the anchors, then the warp
+// aligns the stretches between consecutive anchors one after another,
+// globally (Gotoh, W = open + (n-1) extend; lanes over the stretch's center
+// rows in an anti-diagonal wavefront, codes in shared memory, traceback from
+// the end: diagonal, then F, then E; a gap extends only when strictly better)
+// and writes the inserted-space row.  The
 // flanks follow the local path's rule.  A subject with no match, more
 // matches than the warp holds (the smallest power of two >= max(64, 2S)), or
 // a stretch longer than kBoxSide on either side goes to the Smith-Waterman
@@ -31,7 +33,6 @@ namespace {
 
 constexpr int kAnchThreads = 256, kAnchWarps = kAnchThreads / 32;
 constexpr int kBoxSide = 80;                         // longest stretch side a lane aligns
-constexpr int kBoxBytes = (kBoxSide * kBoxSide + 1) / 2;  // 4-bit codes
 constexpr int kNeg = -(1 << 29);                      // stands for minus infinity
 constexpr int kPosBits = 13;                          // match = segment << 13 | position
 
@@ -50,61 +51,100 @@ struct AnchJob {
   unsigned long long *counter;
 };
 
-__device__ __forceinline__ int code_get(const uint8_t *c, int at) { return (c[at >> 1] >> ((at & 1) * 4)) & 15; }
+// Per-warp workspace of the stretch aligner: one code byte per cell and two
+// ping-pong rows (H and F of a pass's bottom row) for stretches of more than
+// 32 center residues.
+constexpr int kRowInts = 2 * (kBoxSide + 1);
+constexpr int kStretchBytes = kBoxSide * kBoxSide + 2 * kRowInts * 4;
 
-// Global affine alignment of the stretch c[0..lc) x x[0..lx) (center residue
-// cb + i + 1 is c[i]); writes its columns to the row and returns its score.
-__device__ int stretch_align(const uint8_t *__restrict__ c, int lc, const uint8_t *__restrict__ x,
-                             int lx, const int8_t *__restrict__ sM, int K, int o, int e, int cb,
-                             uint16_t *__restrict__ in, uint8_t *__restrict__ oc) {
+__device__ __forceinline__ int gap_cost(int len, int o, int e) { return -(o + (len - 1) * e); }
+
+// Global affine alignment of the stretch c[0..lc) x x[0..lx) by the whole
+// warp (center residue cb + i + 1 is c[i]); writes its columns to the row and
+// returns its score (the same value in every lane).  Lanes hold center rows
+// (32 per pass) and sweep the columns as an anti-diagonal wavefront: the cell
+// above comes from the lane above by shuffle, the row above a pass from the
+// workspace.  Gotoh with W_k = o + (k - 1) e, the edges charged from the
+// stretch's corner; the codes (source 1 diagonal / 2 F / 3 E, ties in that
+// order; E and F extend only when strictly better) go to shared memory and
+// lane 0 walks them back from the end.
+__device__ int stretch_align_warp(const uint8_t *__restrict__ c, int lc, const uint8_t *__restrict__ x,
+                                  int lx, const int8_t *__restrict__ sM, int K, int o, int e, int cb,
+                                  uint16_t *__restrict__ in, uint8_t *__restrict__ oc,
+                                  uint8_t *__restrict__ work, int lane) {
   if (lc == 0 && lx == 0) return 0;
-  uint8_t codes[kBoxBytes];
-  int Hp[kBoxSide + 1], Hc[kBoxSide + 1], F[kBoxSide + 1];
-  Hp[0] = 0;
-  for (int j = 1; j <= lx; ++j) { Hp[j] = -(o + (j - 1) * e); F[j] = kNeg; }
-  for (int i = 1; i <= lc; ++i) {
-    Hc[0] = -(o + (i - 1) * e);
-    int E = kNeg;
-    const int8_t *row = sM + c[i - 1] * K;
-    for (int j = 1; j <= lx; ++j) {
-      const int eo = Hc[j - 1] - o, ee = E - e;
-      E = max(eo, ee);
-      const int fo = Hp[j] - o, fe = F[j] - e;
-      F[j] = max(fo, fe);
-      const int d = Hp[j - 1] + row[x[j - 1]];
-      const int h = max(d, max(E, F[j]));
-      Hc[j] = h;
-      const int src = h == d ? 1 : (h == F[j] ? 2 : 3);
-      const int code = src | ((ee > eo) << 2) | ((fe > fo) << 3);
-      const int at = (i - 1) * lx + (j - 1);
-      if (at & 1) codes[at >> 1] = (uint8_t)((codes[at >> 1] & 15) | (code << 4));
-      else codes[at >> 1] = (uint8_t)code;
-    }
-    for (int j = 0; j <= lx; ++j) Hp[j] = Hc[j];
+  if (lc == 0) {  // residues inserted before center residue cb + 1
+    if (lane == 0) in[cb] = (uint16_t)(in[cb] + lx);
+    return gap_cost(lx, o, e);
   }
-  const int score = Hp[lx];
-  int i = lc, j = lx, state = 0;  // 0 = H, 1 = F (center residue vs gap), 2 = E (inserted residue)
-  while (i > 0 || j > 0) {
-    if (state == 0) {
-      if (i == 0) state = 2;
-      else if (j == 0) state = 1;
-      else {
-        const int src = code_get(codes, (i - 1) * lx + (j - 1)) & 3;
-        if (src == 1) { oc[cb + i] = 1; --i; --j; continue; }
-        state = src == 2 ? 1 : 2;
+  if (lx == 0) return gap_cost(lc, o, e);  // center residues against gaps
+  uint8_t *codes = work;
+  int *rows = reinterpret_cast<int *>(work + kBoxSide * kBoxSide);
+  int hlast = 0;
+  const int npass = (lc + 31) / 32;
+  for (int p = 0; p < npass; ++p) {
+    const int i0 = 32 * p, R = min(32, lc - i0);
+    const int *rin = rows + ((p + 1) & 1) * kRowInts;  // H, F of row i0 (pass p > 0)
+    int *rout = rows + (p & 1) * kRowInts;
+    const int i = i0 + lane + 1;  // this lane's row (1-based)
+    const bool row_ok = lane < R;
+    const int8_t *srow = sM + (row_ok ? c[i - 1] : 0) * K;
+    int hs = 0, fs = kNeg, hl = 0, el = kNeg, hup_prev = 0;
+    const int steps = lx + R - 1;
+    for (int k = 0; k < steps; ++k) {
+      int hup = __shfl_up_sync(MSA_FULL_MASK, hs, 1), fup = __shfl_up_sync(MSA_FULL_MASK, fs, 1);
+      const int j = k - lane + 1;
+      if (lane == 0 && j <= lx) {
+        hup = p == 0 ? gap_cost(j, o, e) : rin[j];
+        fup = p == 0 ? kNeg : rin[kBoxSide + 1 + j];
+      }
+      if (row_ok && j >= 1 && j <= lx) {
+        int hdiag = hup_prev;
+        if (j == 1) {
+          hl = gap_cost(i, o, e);                         // H(i, 0)
+          el = kNeg;
+          hdiag = i == 1 ? 0 : gap_cost(i - 1, o, e);     // H(i - 1, 0)
+        }
+        const int eo = hl - o, ee = el - e, E = max(eo, ee);
+        const int fo = hup - o, fe = fup - e, F = max(fo, fe);
+        const int d = hdiag + srow[x[j - 1]];
+        const int h = max(d, max(E, F));
+        const int src = h == d ? 1 : (h == F ? 2 : 3);
+        codes[(i - 1) * lx + (j - 1)] = (uint8_t)(src | ((ee > eo) << 2) | ((fe > fo) << 3));
+        hs = h; fs = F; hl = h; el = E;
+        if (lane == R - 1 && p + 1 < npass) { rout[j] = h; rout[kBoxSide + 1 + j] = F; }
+        if (i == lc && j == lx) hlast = h;
+      }
+      hup_prev = hup;
+    }
+    __syncwarp();
+  }
+  const int score = __shfl_sync(MSA_FULL_MASK, hlast, (lc - 1) & 31);
+  if (lane == 0) {
+    int i = lc, j = lx, state = 0;  // 0 = H, 1 = F (center residue vs gap), 2 = E (inserted residue)
+    while (i > 0 || j > 0) {
+      if (state == 0) {
+        if (i == 0) state = 2;
+        else if (j == 0) state = 1;
+        else {
+          const int src = codes[(i - 1) * lx + (j - 1)] & 3;
+          if (src == 1) { oc[cb + i] = 1; --i; --j; continue; }
+          state = src == 2 ? 1 : 2;
+        }
+      }
+      if (state == 1) {
+        const bool ext = j == 0 ? i > 1 : ((codes[(i - 1) * lx + (j - 1)] >> 3) & 1);
+        --i;
+        state = ext ? 1 : 0;
+      } else {
+        const bool ext = i == 0 ? j > 1 : ((codes[(i - 1) * lx + (j - 1)] >> 2) & 1);
+        in[cb + i] = (uint16_t)(in[cb + i] + 1);
+        --j;
+        state = ext ? 2 : 0;
       }
     }
-    if (state == 1) {
-      const bool ext = j == 0 ? i > 1 : ((code_get(codes, (i - 1) * lx + (j - 1)) >> 3) & 1);
-      --i;
-      state = ext ? 1 : 0;
-    } else {
-      const bool ext = i == 0 ? j > 1 : ((code_get(codes, (i - 1) * lx + (j - 1)) >> 2) & 1);
-      in[cb + i] = (uint16_t)(in[cb + i] + 1);
-      --j;
-      state = ext ? 2 : 0;
-    }
   }
+  __syncwarp();
   return score;
 }
 
@@ -120,6 +160,9 @@ __global__ void __launch_bounds__(kAnchThreads) k_anchored(SeqSet ss, Scoring sc
   uint32_t *mbuf = reinterpret_cast<uint32_t *>(sid + S + (S & 1)) + (size_t)w * job.cap * 2;
   int16_t *mlen = reinterpret_cast<int16_t *>(mbuf + job.cap);
   int16_t *mpred = mlen + job.cap;
+  uint8_t *work = reinterpret_cast<uint8_t *>(reinterpret_cast<uint32_t *>(sid + S + (S & 1)) +
+                                              (size_t)kAnchWarps * job.cap * 2) +
+                  (size_t)w * kStretchBytes;
   for (int i = threadIdx.x; i < K * K; i += kAnchThreads) sM[i] = sc.M[i];
   for (int i = threadIdx.x; i < S; i += kAnchThreads) { skey[i] = job.seg_key[i]; sid[i] = job.seg_id[i]; }
   __syncthreads();
@@ -242,14 +285,14 @@ __global__ void __launch_bounds__(kAnchThreads) k_anchored(SeqSet ss, Scoring sc
         oc[ca + u + 1] = 1;
         score += sM[rc[ca + u] * K + x[xa + u]];
       }
-      if (t + 1 < T) {
-        const int cb = ca + kk, xb = xa + kk;
-        score += stretch_align(rc + cb, anchor_s(t + 1) * kk - cb, x + xb, anchor_p(t + 1) - xb,
-                               sM, K, sc.o, sc.e, cb, in, oc);
-      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) score += __shfl_xor_sync(MSA_FULL_MASK, score, off);
+    for (int t = 0; t + 1 < T; ++t) {
+      const int cb = anchor_s(t) * kk + kk, xb = anchor_p(t) + kk;
+      score += stretch_align_warp(rc + cb, anchor_s(t + 1) * kk - cb, x + xb, anchor_p(t + 1) - xb,
+                                  sM, K, sc.o, sc.e, cb, in, oc, work, lane);
+    }
     if (lane == 0) {
       const int i1 = anchor_s(0) * kk, j1 = anchor_p(0);
       const int i2 = anchor_s(T - 1) * kk + kk, j2 = anchor_p(T - 1) + kk;
@@ -268,7 +311,7 @@ __global__ void __launch_bounds__(kAnchThreads) k_anchored(SeqSet ss, Scoring sc
 }
 
 int anchored_smem(int nseg, int cap) {
-  return nseg * 12 + (nseg & 1) * 4 + kAnchWarps * cap * 8;
+  return nseg * 12 + (nseg & 1) * 4 + kAnchWarps * cap * 8 + kAnchWarps * kStretchBytes;
 }
 
 // The local path (Smith-Waterman fill with codes, traceback) for a list of
