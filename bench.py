@@ -707,6 +707,10 @@ def run_ours(args):
     clocks = sampler.stop()
     align_ms_t, align_cells_t = align_kern
     stage_ms = b.msa_stage_times(h)[0]
+    # one untimed pass first: the pinned host buffer for the rows is allocated
+    # (and reused) outside the timed steps, as the input buffer is
+    step_e2e()
+    torch.cuda.synchronize()
     e2e_ms, e2e_cells, *_ = timed(step_e2e, max(1, args.steps))
 
     def reduce_max(x):
