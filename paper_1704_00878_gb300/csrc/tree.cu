@@ -12,7 +12,7 @@
 //
 // Neighbour joining: the matrix stays on the device (int64, positions in
 // ascending slot order); every join is two launches -- the minimum of Q over
-// the active pairs (a warp per segment of a row, lanes along it, the last CTA to finish
+// the active pairs (a warp per row, lanes along it, the last CTA to finish
 // reduces the CTAs' minima) and the join itself (CTAs over the rows: branch lengths,
 // the new node's row and column, the row sums updated in place; the last
 // CTA to finish adds up the new node's row sum).  When a quarter of the
@@ -32,7 +32,6 @@ constexpr int kWords = 64;   // 32-bit words (4 columns) per staged chunk
 constexpr long long kDScale = 1LL << 20;
 constexpr long long kDLimit = 1LL << 40;  // |distance| bound of the joins
 constexpr int kArgThreads = 256;
-constexpr int kSeg = 512;  // columns of a row one warp scans for the Q minimum
 constexpr int kJoinThreads = 1024;
 
 // 0x80 in every byte of w that is nonzero
@@ -167,19 +166,13 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__re
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const long long f = m - 2;
   Pick best{LLONG_MAX, LLONG_MAX};
-  // warp tasks: (row x, segment c of kSeg columns after x); rows are long at
-  // the top of the triangle and short at the bottom, so segments balance them
-  const int nseg = (P + kSeg - 1) / kSeg;
-  const long long ntask = (long long)P * nseg;
-  for (long long task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += warps) {
-    const int x = (int)(task / nseg), c = (int)(task - (long long)x * nseg);
-    const int ybeg = x + 1 + c * kSeg;
-    if (ybeg >= P || !act[x]) continue;
-    const int yend = min(P, ybeg + kSeg);
+  for (int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < P; x += warps) {
+    if (!act[x]) continue;
     const long long rx = r[x];
     const long long *row = D + (size_t)x * P;
+    const int yend = P;
     // four independent loads per lane in flight
-    for (int y0 = ybeg + lane; y0 < yend; y0 += 128) {
+    for (int y0 = x + 1 + lane; y0 < yend; y0 += 128) {
       long long dv[4], rv[4];
       bool ok[4];
 #pragma unroll
@@ -418,9 +411,8 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
     int Pn = n, m = n, t = 0;
     while (m > 2) {
       ctx->launches += 2;
-      // a warp per task at least: small matrices take few CTAs
-      const long long tasks = (long long)Pn * ((Pn + kSeg - 1) / kSeg);
-      const int agrid = (int)std::max<long long>(1, std::min<long long>(grid, (tasks + kArgThreads / 32 - 1) / (kArgThreads / 32)));
+      // a warp per row at least: small matrices take few CTAs
+      const int agrid = std::max(1, std::min(grid, (Pn + kArgThreads / 32 - 1) / (kArgThreads / 32)));
       k_nj_argmin<<<agrid, kArgThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
                                                      P<uint8_t>(*cA), m, P<Pick>(part), ticket,
                                                      P<int>(sel));
