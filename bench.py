@@ -445,6 +445,20 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
                       "avg_sp": (sp / pairs_n if name == "learned_refined" else
                                  exact_sp / pairs_n if name == "exact" else avg_sp_of(i))}
                for name, i in picks.items()}
+    # the same training from two more seeds (network, pair sample, batches):
+    # the spread of what the learned center gives
+    seeds = [{"seed": 1, "refined_rank_pct": rank(c), "top1_rank_pct": rank(top1),
+              "sp_loss_pct": 100.0 * (sp - exact_sp) / exact_sp}]
+    for sd in (2, 3):
+        b.msa_selector_init(h, seed=sd)
+        b.msa_selector_train(h, training_pairs(n, 60000, fam, seed=8 + sd), steps=6000,
+                             batch_pairs=256, lr=3e-4, seed=3 + sd)
+        c_s, _ = b.msa_select_center_refined(h, candidates=cand, refs=refs)
+        t_s, _ = b.msa_select_center(h, b.MSA_CENTER_LEARNED)
+        seeds.append({"seed": sd, "refined_rank_pct": rank(c_s), "top1_rank_pct": rank(t_s),
+                      "sp_loss_pct": 100.0 * (avg_sp_of(c_s) * pairs_n - exact_sp) / exact_sp})
+    spread = {k: [min(x[k] for x in seeds), max(x[k] for x in seeds)]
+              for k in ("refined_rank_pct", "top1_rank_pct", "sp_loss_pct")}
     return {"exact_step_ms": exact_ms, "learned_step_ms": float(np.mean(ms)),
             "speedup": exact_ms / float(np.mean(ms)),
             "avg_sp_exact": exact_sp / pairs_n, "avg_sp_learned": sp / pairs_n,
@@ -452,6 +466,7 @@ def learned_vs_exact(b, h, dlet, offsets, fam, n, flush, stream, exact_ms, exact
             "sp_loss_top1_pct": 100.0 * (compare["learned_top1"]["avg_sp"] * pairs_n - exact_sp)
                                 / exact_sp,
             "compare": compare,
+            "seeds": seeds, "spread_over_seeds": spread,
             "random_candidates_refined_mean_rank_pct": rand_rank,
             "selector": "4-layer conv, width 128, k 9, 64-d, bf16 on tcgen05 tensor cores",
             "train": {"pairs": int(pairs.shape[0]), "steps": 6000, "batch_pairs": 256,
