@@ -102,6 +102,13 @@ TREE_MUTATIONS = {
     "distance_rounds_up": ("(DSCALE * mism) // np.maximum(comp, 1)",
                            "-((-DSCALE * mism) // np.maximum(comp, 1))"),
     "empty_pair_near": ("np.maximum(comp, 1), DSCALE)", "np.maximum(comp, 1), 0)"),
+    "cut_smallest_first": ("big = max(cuts, key=lambda v: (len(leaves[v]), -order[v]))",
+                           "big = min(cuts, key=lambda v: (len(leaves[v]), -order[v]))"),
+    "label_farthest_sample": ("k = min(range(m), key=lambda x: (int(D[i, S[x]]), S[x]))",
+                              "k = max(range(m), key=lambda x: (int(D[i, S[x]]), S[x]))"),
+    "midpoint_at_a_third": ("half = total / 2.0", "half = total / 3.0"),
+    "merged_edge_zero": ("tree[u] = [(walk_s(w), l) for w, l in kids[v]]",
+                         "tree[u] = [(walk_s(w), 0.0) for w, l in kids[v]]"),
 }
 
 
