@@ -441,6 +441,33 @@ int msa_nj(msa_ctx *ctx, const int64_t *dist, int64_t n, int32_t *joins_out, dou
  * ERANGE beyond 65,536 sequences. */
 int msa_nj_tree(msa_ctx *ctx, int32_t *joins_out, double *lengths_out);
 
+/* The tree of a large set by clusters (the paper's tree section, Figure 4:
+ * a ~10 % sample is clustered, every sequence labelled with a cluster, one
+ * tree built per cluster and the trees merged; the paper gives neither the
+ * clustering rule nor the merge).  Reading, on msa_tree_distances' distances:
+ * (1) the NJ tree of the sample rows (as msa_nj), rooted at the middle of its
+ * longest leaf-to-leaf path (from the first sample row its farthest row, then
+ * that row's farthest, ties to the smaller row; the middle measured from the
+ * second end; a middle on a node roots on that node's edge toward the second
+ * end); (2) clusters: from the root, the subtree holding the most sample rows
+ * (ties: the smaller NJ node) is replaced by its two children until none
+ * holds more than `cap` sample rows, clusters numbered in the order of their
+ * smallest sample row; (3) a sample row belongs to its own cluster, any other
+ * row to its nearest sample row's (smallest distance, ties to the smaller
+ * row); (4) per cluster the NJ tree of its rows plus an outgroup (the sample
+ * row outside the cluster nearest to the cluster's sample rows, ties to the
+ * smaller row), rooted where the outgroup joins and the outgroup removed;
+ * with a single cluster the NJ tree of all rows as msa_nj roots it; (5) every
+ * cluster's subtree of the sample tree replaced by its cluster tree, the
+ * edge above keeping its length; (6) output in post-order, each node's
+ * children ordered by their smallest row, internal nodes numbered n, n+1, ...
+ * sample: host int64[nsample] rows (duplicates ignored; at most 65,536
+ * distinct); cap >= 1; joins_out / lengths_out as msa_nj (host or device);
+ * cluster_out: nullable, host or device int32[n].  Requires msa_merge_gaps
+ * (ESTATE); ERANGE if a cluster plus its outgroup exceeds 65,536 rows. */
+int msa_nj_cluster_tree(msa_ctx *ctx, const int64_t *sample, int64_t nsample, int32_t cap,
+                        int32_t *joins_out, double *lengths_out, int32_t *cluster_out);
+
 /* Self-test of the bounded waits of the tensor-core convolution (no
  * counterpart in the paper): runs one small convolution whose loads are
  * never issued, with a short poll limit, so every mbarrier wait runs out.

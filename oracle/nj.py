@@ -219,9 +219,9 @@ def _midpoint_rooted(joins, lengths, nleaf):
     half = total / 2.0
     # walk from b toward a: the edge (v, u) where the path passes the middle
     v, walked = b, 0.0
-    while True:
+    while True:  # the last edge of the path at the latest (negative lengths)
         u, l = par[v]
-        if walked + l >= half:
+        if walked + l >= half or u == a:
             break
         walked += l
         v = u
@@ -246,8 +246,10 @@ def _midpoint_rooted(joins, lengths, nleaf):
 def cluster_tree(D, sample, cap):
     """The clustered tree of the rows of the n x n distance matrix D.
     Returns (joins int64[n-1, 2], lengths float64[n-1, 2], cluster int32[n])."""
+    import sys
     D = np.asarray(D, dtype=np.int64)
     n = D.shape[0]
+    sys.setrecursionlimit(max(sys.getrecursionlimit(), 4 * n + 1000))  # trees as deep as n
     S = sorted(set(int(s) for s in sample))
     m = len(S)
     sj, sl = nj(D[np.ix_(S, S)])

@@ -82,6 +82,9 @@ _SIGS = {
     "msa_nj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                               ctypes.c_void_p]),
     "msa_nj_tree": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "msa_nj_cluster_tree": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     "msa_probe_int_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "msa_selector_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64]),
     "msa_selector_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -392,6 +395,19 @@ def msa_nj_tree(ctx):
     lengths = np.zeros((max(n - 1, 0), 2), np.float64)
     _check(ctx, lib().msa_nj_tree(ctx, _ptr(joins), _ptr(lengths)))
     return joins, lengths
+
+
+def msa_nj_cluster_tree(ctx, sample, cap):
+    """The clustered tree of the merged MSA: (joins int32[n-1, 2], lengths
+    float64[n-1, 2], cluster int32[n])."""
+    n = msa_dims(ctx)[0]
+    smp = np.ascontiguousarray(sample, dtype=np.int64)
+    joins = np.zeros((max(n - 1, 0), 2), np.int32)
+    lengths = np.zeros((max(n - 1, 0), 2), np.float64)
+    cluster = np.zeros(n, np.int32)
+    _check(ctx, lib().msa_nj_cluster_tree(ctx, _ptr(smp), smp.size, int(cap), _ptr(joins),
+                                          _ptr(lengths), _ptr(cluster)))
+    return joins, lengths, cluster
 
 
 def msa_memory(ctx):

@@ -53,10 +53,23 @@ __device__ __forceinline__ uint32_t byte_sum(uint32_t c) {
   return (c & 0xffffu) + (c >> 16);
 }
 
-__global__ void __launch_bounds__(256) k_pdist(const uint8_t *__restrict__ msa, int n, int64_t W,
-                                               long long *__restrict__ D) {
+// Rows of a distance tile: list A x list B (row indices of the MSA; null =
+// the rows 0..nA-1 / 0..nB-1).  SYM: A and B are the same list, tiles on and
+// above the diagonal, D[a][b] and D[b][a] stored (ld = nA); NEAREST: every
+// tile of A x B, and per row of A the smallest (distance << 32 | position in
+// B) by an atomic minimum -- the nearest row of B, ties to its first position.
+struct PdistJob {
+  const int32_t *ia, *ib;
+  int nA, nB;
+  bool sym;
+  long long *D;               // SYM
+  unsigned long long *near;   // NEAREST: one key per row of A
+};
+
+__global__ void __launch_bounds__(256) k_pdist(const uint8_t *__restrict__ msa, int64_t W,
+                                               PdistJob job) {
   const int ta = blockIdx.y, tb = blockIdx.x;
-  if (tb < ta) return;
+  if (job.sym && tb < ta) return;
   __shared__ uint32_t sA[kTile][kWords + 1], sB[kTile][kWords + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int a0 = ta * kTile, b0 = tb * kTile;
@@ -65,18 +78,21 @@ __global__ void __launch_bounds__(256) k_pdist(const uint8_t *__restrict__ msa, 
   const int64_t nwords = (W + 3) / 4;
   for (int64_t w0 = 0; w0 < nwords; w0 += kWords) {
     __syncthreads();
-    // stage 64 rows x 256 columns of each side; columns past W and rows past n are gaps
+    // stage 64 rows x 256 columns of each side; columns past W and rows past
+    // the lists are gaps
     for (int idx = threadIdx.x; idx < kTile * kWords; idx += 256) {
       const int r = idx / kWords, w = idx - r * kWords;
       const int64_t c0 = (w0 + w) * 4;
       uint32_t va = kGap4, vb = kGap4;
-      const int ra = a0 + r, rb = b0 + r;
+      const int pa = a0 + r, pb = b0 + r;
+      const int ra = pa < job.nA ? (job.ia ? job.ia[pa] : pa) : -1;
+      const int rb = pb < job.nB ? (job.ib ? job.ib[pb] : pb) : -1;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t c = c0 + u;
         if (c < W) {
-          if (ra < n) va = (va & ~(0xffu << (8 * u))) | ((uint32_t)msa[(size_t)ra * W + c] << (8 * u));
-          if (rb < n) vb = (vb & ~(0xffu << (8 * u))) | ((uint32_t)msa[(size_t)rb * W + c] << (8 * u));
+          if (ra >= 0) va = (va & ~(0xffu << (8 * u))) | ((uint32_t)msa[(size_t)ra * W + c] << (8 * u));
+          if (rb >= 0) vb = (vb & ~(0xffu << (8 * u))) | ((uint32_t)msa[(size_t)rb * W + c] << (8 * u));
         }
       }
       sA[r][w] = va;
@@ -112,15 +128,25 @@ __global__ void __launch_bounds__(256) k_pdist(const uint8_t *__restrict__ msa, 
       }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty + 16 * i;
+    if (a >= job.nA) continue;
+    unsigned long long nearest = ~0ull;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
-      if (a >= n || b >= n) continue;
+      const int b = b0 + tx + 16 * j;
+      if (b >= job.nB) continue;
       const long long d = comp[i][j] ? ((long long)mism[i][j] * kDScale) / comp[i][j] : kDScale;
-      D[(size_t)a * n + b] = d;
-      if (ta != tb) D[(size_t)b * n + a] = d;
+      if (job.sym) {
+        job.D[(size_t)a * job.nA + b] = d;
+        if (ta != tb) job.D[(size_t)b * job.nA + a] = d;
+      } else {
+        const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)b;
+        nearest = key < nearest ? key : nearest;
+      }
     }
+    if (!job.sym && nearest != ~0ull) atomicMin(&job.near[a], nearest);
+  }
 }
 
 struct Pick {
@@ -365,15 +391,43 @@ __global__ void k_nj_init(long long *__restrict__ r, const long long *__restrict
   }
 }
 
+// Distances among the merged rows idx[0..m) (device list, null = rows 0..m-1)
+// into the m x m matrix D (device).
+int list_distances(msa_ctx *ctx, const int32_t *idx, int m, long long *D) {
+  const int T = (m + kTile - 1) / kTile;
+  PdistJob job{idx, idx, m, m, true, D, nullptr};
+  ++ctx->launches;
+  k_pdist<<<dim3(T, T), 256, 0, ctx->st>>>(P<uint8_t>(ctx->msa), ctx->W, job);
+  CK(cudaGetLastError());
+  return MSA_OK;
+}
+
+// Per cluster c of the sample: the smallest (d(t, s) << 32 | s) over sample
+// positions t in c and s outside it (the outgroup: the nearest sample row
+// outside, ties to the smaller row).
+__global__ void k_outgroups(const long long *__restrict__ D, int m, const int32_t *__restrict__ cl,
+                            unsigned long long *__restrict__ key) {
+  const int t = blockIdx.y;
+  const int c = cl[t];
+  unsigned long long best = ~0ull;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x)
+    if (cl[s] != c) {
+      const unsigned long long k = ((unsigned long long)D[(size_t)t * m + s] << 32) | (unsigned)s;
+      best = k < best ? k : best;
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(MSA_FULL_MASK, best, off);
+    best = o < best ? o : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&key[c], best);
+}
+
 int tree_distances(msa_ctx *ctx, DevBuf &D) {
   if (!ctx->merged) return fail(ctx, MSA_ESTATE, "merge the alignment first");
   const int n = ctx->n;
   TRY(ensure(ctx, D, sizeof(long long) * (size_t)n * n));
-  const int T = (n + kTile - 1) / kTile;
-  ++ctx->launches;
-  k_pdist<<<dim3(T, T), 256, 0, ctx->st>>>(P<uint8_t>(ctx->msa), n, ctx->W, P<long long>(D));
-  CK(cudaGetLastError());
-  return MSA_OK;
+  return list_distances(ctx, nullptr, n, P<long long>(D));
 }
 
 // Neighbour joining of the n x n matrix in D (device, int64, consumed).
@@ -459,6 +513,327 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
   return rc;
 }
 
+// ---------------------------------------------------------------- clustered tree (host side)
+// A rooted tree: kids[v] = its (child, length) pairs, none for a leaf.
+using Kids = std::vector<std::vector<std::pair<int, double>>>;
+
+// The unrooted tree of NJ joins over nleaf leaves (node nleaf + t for join t;
+// the last join's two edges become one edge, its node unused).
+static Kids unrooted(const std::vector<int32_t> &joins, const std::vector<double> &lengths, int nleaf) {
+  const int T = nleaf - 1;
+  Kids adj(2 * nleaf);
+  auto link = [&](int a, int b, double l) { adj[a].push_back({b, l}); adj[b].push_back({a, l}); };
+  for (int t = 0; t + 1 < T; ++t) {
+    link(nleaf + t, joins[2 * t], lengths[2 * t]);
+    link(nleaf + t, joins[2 * t + 1], lengths[2 * t + 1]);
+  }
+  link(joins[2 * (T - 1)], joins[2 * (T - 1) + 1], lengths[2 * (T - 1)] + lengths[2 * (T - 1) + 1]);
+  return adj;
+}
+
+// The leaf farthest from src (distances summed along the path from src,
+// ties to the smaller leaf) and each node's (parent, edge) toward src.
+static int farthest(const Kids &adj, int src, int nleaf, double &dist_out,
+                    std::vector<std::pair<int, double>> &par) {
+  std::vector<double> dist(adj.size(), 0.0);
+  std::vector<char> seen(adj.size(), 0);
+  par.assign(adj.size(), {-1, 0.0});
+  std::vector<int> stack = {src};
+  seen[src] = 1;
+  while (!stack.empty()) {
+    const int v = stack.back();
+    stack.pop_back();
+    for (auto [w, l] : adj[v])
+      if (!seen[w]) {
+        seen[w] = 1;
+        dist[w] = dist[v] + l;
+        par[w] = {v, l};
+        stack.push_back(w);
+      }
+  }
+  int best = -1;
+  for (int v = 0; v < nleaf; ++v)
+    if (best < 0 || dist[v] > dist[best]) best = v;
+  dist_out = dist[best];
+  return best;
+}
+
+// Orient the unrooted adjacency away from `root`, skipping node `drop`.
+static Kids orient(const Kids &adj, int root, int drop) {
+  Kids kids(adj.size());
+  std::vector<char> seen(adj.size(), 0);
+  seen[root] = 1;
+  if (drop >= 0) seen[drop] = 1;
+  std::vector<int> stack = {root};
+  while (!stack.empty()) {
+    const int v = stack.back();
+    stack.pop_back();
+    for (auto [w, l] : adj[v])
+      if (!seen[w]) {
+        seen[w] = 1;
+        kids[v].push_back({w, l});
+        stack.push_back(w);
+      }
+  }
+  return kids;
+}
+
+// The NJ tree rooted at the middle of its longest leaf-to-leaf path (see
+// msa_nj_cluster_tree); the new root is node 2 nleaf - 2.
+static Kids midpoint_rooted(const std::vector<int32_t> &joins, const std::vector<double> &lengths,
+                            int nleaf, int &root) {
+  Kids adj = unrooted(joins, lengths, nleaf);
+  std::vector<std::pair<int, double>> par;
+  double total = 0.0;
+  const int a = farthest(adj, 0, nleaf, total, par);
+  const int b = farthest(adj, a, nleaf, total, par);
+  const double half = total / 2.0;
+  int v = b;
+  double walked = 0.0, l = 0.0;
+  int u = -1;
+  for (;;) {  // the last edge of the path at the latest (negative lengths)
+    u = par[v].first;
+    l = par[v].second;
+    if (walked + l >= half || u == a) break;
+    walked += l;
+    v = u;
+  }
+  const double x = half - walked;
+  auto drop_edge = [&](int p, int q) {
+    auto &e = adj[p];
+    e.erase(std::find_if(e.begin(), e.end(), [&](const std::pair<int, double> &z) { return z.first == q; }));
+  };
+  drop_edge(v, u);
+  drop_edge(u, v);
+  root = 2 * nleaf - 2;
+  adj[root] = {{v, x}, {u, l - x}};
+  adj[v].push_back({root, x});
+  adj[u].push_back({root, l - x});
+  return orient(adj, root, -1);
+}
+
+// Copy a rooted tree (leaf ids mapped to rows by name[]) into the arena.
+static int graft(const Kids &kids, int root, const std::vector<int> &name, int nleaf, Kids &arena) {
+  // iterative: children are copied before their parent
+  std::vector<std::pair<int, int>> stack = {{root, 0}};
+  std::vector<int> made(kids.size(), -1);
+  while (!stack.empty()) {
+    auto &[v, state] = stack.back();
+    if (kids[v].empty()) {
+      made[v] = name[v < nleaf ? v : 0];
+      stack.pop_back();
+      continue;
+    }
+    if (state == 0) {
+      state = 1;
+      const int vv = v;
+      for (auto [w, l] : kids[vv]) stack.push_back({w, 0});
+      continue;
+    }
+    const int id = (int)arena.size();
+    arena.emplace_back();
+    for (auto [w, l] : kids[v]) arena[id].push_back({made[w], l});
+    made[v] = id;
+    stack.pop_back();
+  }
+  return made[root];
+}
+
+int cluster_tree(msa_ctx *ctx, const std::vector<int32_t> &S, int cap, int32_t *joins_out,
+                 double *lengths_out, int32_t *cluster_out) {
+  const int n = ctx->n, m = (int)S.size();
+  DevBuf dS, dS2, dlist, dnear, dcl, dkey;
+  auto cleanup = [&]() { for (DevBuf *b : {&dS, &dS2, &dlist, &dnear, &dcl, &dkey}) release(ctx, *b); };
+  int rc = [&]() -> int {
+    // 1. the sample tree, midpoint-rooted
+    TRY(ensure(ctx, dlist, sizeof(int32_t) * std::max(n, 1)));
+    CK(cudaMemcpyAsync(dlist.p, S.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->st));
+    TRY(ensure(ctx, dS, sizeof(long long) * (size_t)m * m));
+    TRY(list_distances(ctx, P<int32_t>(dlist), m, P<long long>(dS)));
+    TRY(ensure(ctx, dS2, sizeof(long long) * (size_t)m * m));
+    CK(cudaMemcpyAsync(dS2.p, dS.p, sizeof(long long) * (size_t)m * m, cudaMemcpyDeviceToDevice, ctx->st));
+    std::vector<int32_t> sj(2 * std::max(m - 1, 0));
+    std::vector<double> sl(2 * std::max(m - 1, 0));
+    if (m > 1) TRY(nj_device(ctx, dS2, m, sj.data(), sl.data()));
+    CK(cudaStreamSynchronize(ctx->st));
+    Kids skids;
+    int sroot = 0;
+    if (m > 1) skids = midpoint_rooted(sj, sl, m, sroot);
+    else skids.assign(1, {});
+    // leaves under every node (post-order)
+    const int nn = (int)skids.size();
+    std::vector<int> nleaves(nn, 0), lowleaf(nn, INT_MAX);
+    {
+      std::vector<std::pair<int, int>> stack = {{sroot, 0}};
+      while (!stack.empty()) {
+        auto &[v, st] = stack.back();
+        if (skids[v].empty()) { nleaves[v] = 1; lowleaf[v] = v; stack.pop_back(); continue; }
+        if (st == 0) { st = 1; const int vv = v; for (auto [w, l] : skids[vv]) stack.push_back({w, 0}); continue; }
+        for (auto [w, l] : skids[v]) { nleaves[v] += nleaves[w]; lowleaf[v] = std::min(lowleaf[v], lowleaf[w]); }
+        stack.pop_back();
+      }
+    }
+    // 2. the cut: split the subtree holding the most sample rows (ties: the
+    // smaller node; the root is never tied) until none holds more than cap
+    std::vector<int> cuts = {sroot};
+    for (;;) {
+      int bi = 0;
+      for (int k = 1; k < (int)cuts.size(); ++k) {
+        const int v = cuts[k], w = cuts[bi];
+        if (nleaves[v] > nleaves[w] || (nleaves[v] == nleaves[w] && v < w)) bi = k;
+      }
+      const int big = cuts[bi];
+      if (nleaves[big] <= cap) break;
+      cuts.erase(cuts.begin() + bi);
+      for (auto [w, l] : skids[big]) cuts.push_back(w);
+    }
+    std::sort(cuts.begin(), cuts.end(), [&](int x, int y) { return lowleaf[x] < lowleaf[y]; });
+    const int q = (int)cuts.size();
+    std::vector<int32_t> leaf_cl(m, 0);
+    {
+      std::vector<int> is_cut(nn, -1);
+      for (int c = 0; c < q; ++c) is_cut[cuts[c]] = c;
+      std::vector<std::pair<int, int>> stack = {{sroot, -1}};
+      while (!stack.empty()) {
+        auto [v, c] = stack.back();
+        stack.pop_back();
+        if (is_cut[v] >= 0) c = is_cut[v];
+        if (skids[v].empty()) leaf_cl[v] = c;
+        for (auto [w, l] : skids[v]) stack.push_back({w, c});
+      }
+    }
+    // 3. labels: sample rows their own cluster, others their nearest sample row's
+    std::vector<int32_t> cluster(n, -1);
+    {
+      TRY(ensure(ctx, dnear, sizeof(unsigned long long) * n));
+      CK(cudaMemsetAsync(dnear.p, 0xff, sizeof(unsigned long long) * n, ctx->st));
+      const int TA = (n + kTile - 1) / kTile, TB = (m + kTile - 1) / kTile;
+      PdistJob job{nullptr, P<int32_t>(dlist), n, m, false, nullptr, P<unsigned long long>(dnear)};
+      ++ctx->launches;
+      k_pdist<<<dim3(TB, TA), 256, 0, ctx->st>>>(P<uint8_t>(ctx->msa), ctx->W, job);
+      CK(cudaGetLastError());
+      std::vector<unsigned long long> near(n);
+      CK(cudaMemcpyAsync(near.data(), dnear.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+      for (int i = 0; i < n; ++i) cluster[i] = leaf_cl[(int)(near[i] & 0xffffffffu)];
+      for (int l = 0; l < m; ++l) cluster[S[l]] = leaf_cl[l];
+    }
+    // 4. outgroups
+    std::vector<int> outgroup(q, -1);
+    if (q > 1) {
+      TRY(ensure(ctx, dcl, sizeof(int32_t) * m));
+      TRY(ensure(ctx, dkey, sizeof(unsigned long long) * q));
+      CK(cudaMemcpyAsync(dcl.p, leaf_cl.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->st));
+      CK(cudaMemsetAsync(dkey.p, 0xff, sizeof(unsigned long long) * q, ctx->st));
+      ++ctx->launches;
+      k_outgroups<<<dim3((m + 255) / 256, m), 256, 0, ctx->st>>>(P<long long>(dS), m, P<int32_t>(dcl),
+                                                                 P<unsigned long long>(dkey));
+      CK(cudaGetLastError());
+      std::vector<unsigned long long> key(q);
+      CK(cudaMemcpyAsync(key.data(), dkey.p, sizeof(unsigned long long) * q, cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+      for (int c = 0; c < q; ++c) outgroup[c] = S[(int)(key[c] & 0xffffffffu)];
+    }
+    // 5. cluster trees into the arena (rows 0..n-1 are its leaves)
+    Kids arena(n);
+    std::vector<int> rows_of_cut(nn, -1);  // arena root of each cut's cluster tree
+    std::vector<std::vector<int>> members(q);
+    for (int i = 0; i < n; ++i) members[cluster[i]].push_back(i);
+    for (int c = 0; c < q; ++c) {
+      const std::vector<int> &R = members[c];
+      if (R.size() == 1) { rows_of_cut[cuts[c]] = R[0]; continue; }
+      std::vector<int> U = R;
+      int opos = -1;
+      if (q > 1) {
+        U.push_back(outgroup[c]);
+        std::sort(U.begin(), U.end());
+        opos = (int)(std::lower_bound(U.begin(), U.end(), outgroup[c]) - U.begin());
+      }
+      const int u = (int)U.size();
+      if (u > kMaxTreeRows) return fail(ctx, MSA_ERANGE, "a cluster of %d rows (at most %d)", u, kMaxTreeRows);
+      std::vector<int32_t> U32(U.begin(), U.end());
+      CK(cudaMemcpyAsync(dlist.p, U32.data(), sizeof(int32_t) * u, cudaMemcpyHostToDevice, ctx->st));
+      TRY(ensure(ctx, dS2, sizeof(long long) * (size_t)u * u));
+      TRY(list_distances(ctx, P<int32_t>(dlist), u, P<long long>(dS2)));
+      std::vector<int32_t> cj(2 * (u - 1));
+      std::vector<double> cl(2 * (u - 1));
+      TRY(nj_device(ctx, dS2, u, cj.data(), cl.data()));
+      CK(cudaStreamSynchronize(ctx->st));
+      Kids ck;
+      int croot;
+      if (q == 1) {  // the NJ tree as it is rooted
+        ck.assign(2 * u - 1, {});
+        for (int t = 0; t < u - 1; ++t)
+          ck[u + t] = {{cj[2 * t], cl[2 * t]}, {cj[2 * t + 1], cl[2 * t + 1]}};
+        croot = 2 * u - 2;
+      } else {  // rooted where the outgroup joins, the outgroup removed
+        const Kids adj = unrooted(cj, cl, u);
+        croot = adj[opos][0].first;
+        ck = orient(adj, croot, opos);
+      }
+      std::vector<int> name(U.begin(), U.end());
+      rows_of_cut[cuts[c]] = graft(ck, croot, name, u, arena);
+    }
+    // 6. the sample tree above the cuts, the cluster trees below
+    int root;
+    if (q == 1) {
+      root = rows_of_cut[cuts[0]];
+    } else {
+      std::vector<int> made(nn, -1);
+      std::vector<std::pair<int, int>> stack = {{sroot, 0}};
+      while (!stack.empty()) {
+        auto &[v, st] = stack.back();
+        if (rows_of_cut[v] >= 0) { made[v] = rows_of_cut[v]; stack.pop_back(); continue; }
+        if (st == 0) { st = 1; const int vv = v; for (auto [w, l] : skids[vv]) stack.push_back({w, 0}); continue; }
+        const int id = (int)arena.size();
+        arena.emplace_back();
+        for (auto [w, l] : skids[v]) arena[id].push_back({made[w], l});
+        made[v] = id;
+        stack.pop_back();
+      }
+      root = made[sroot];
+    }
+    // 7. post-order, children by their smallest row, internal nodes n, n+1, ...
+    if (n > 1) {
+      const int na = (int)arena.size();
+      std::vector<int> low(na, INT_MAX), id(na, -1);
+      for (int i = 0; i < n; ++i) low[i] = i, id[i] = i;
+      for (int v = n; v < na; ++v)  // arena children are always made before their parent
+        for (auto [w, l] : arena[v]) low[v] = std::min(low[v], low[w]);
+      for (int v = n; v < na; ++v)
+        std::sort(arena[v].begin(), arena[v].end(),
+                  [&](const std::pair<int, double> &x, const std::pair<int, double> &y) {
+                    return low[x.first] < low[y.first];
+                  });
+      int t = 0;
+      std::vector<std::pair<int, int>> stack = {{root, 0}};
+      while (!stack.empty()) {
+        auto &top = stack.back();
+        const int v = top.first;
+        if (v < n) { stack.pop_back(); continue; }
+        if (top.second == 0) {
+          top.second = 1;
+          const int c0 = arena[v][0].first, c1 = arena[v][1].first;
+          stack.push_back({c1, 0});  // the first child is finished first
+          stack.push_back({c0, 0});
+          continue;
+        }
+        id[v] = n + t;
+        joins_out[2 * t] = id[arena[v][0].first];
+        joins_out[2 * t + 1] = id[arena[v][1].first];
+        lengths_out[2 * t] = arena[v][0].second;
+        lengths_out[2 * t + 1] = arena[v][1].second;
+        ++t;
+        stack.pop_back();
+      }
+    }
+    if (cluster_out) std::copy(cluster.begin(), cluster.end(), cluster_out);
+    return MSA_OK;
+  }();
+  cleanup();
+  return rc;
+}
+
 }  // namespace
 }  // namespace msa_detail
 
@@ -518,4 +893,37 @@ int msa_nj_tree(msa_ctx *ctx, int32_t *joins_out, double *lengths_out) {
   }();
   release(ctx, D);
   return rc;
+}
+
+int msa_nj_cluster_tree(msa_ctx *ctx, const int64_t *sample, int64_t nsample, int32_t cap,
+                        int32_t *joins_out, double *lengths_out, int32_t *cluster_out) {
+  if (!ctx || !sample || nsample < 1 || cap < 1) return MSA_EINVAL;
+  if (ctx->n > 1 && (!joins_out || !lengths_out)) return MSA_EINVAL;
+  if (!ctx->merged) return fail(ctx, MSA_ESTATE, "merge the alignment first");
+  std::vector<int32_t> S;
+  S.reserve(nsample);
+  for (int64_t k = 0; k < nsample; ++k) {
+    if (sample[k] < 0 || sample[k] >= ctx->n) return fail(ctx, MSA_EINVAL, "sample row out of range");
+    S.push_back((int32_t)sample[k]);
+  }
+  std::sort(S.begin(), S.end());
+  S.erase(std::unique(S.begin(), S.end()), S.end());
+  if ((int64_t)S.size() > kMaxTreeRows) return fail(ctx, MSA_ERANGE, "a sample of more than %d rows", kMaxTreeRows);
+  TRY(set_device(ctx));
+  std::vector<int32_t> joins(2 * (size_t)std::max(ctx->n - 1, 0));
+  std::vector<double> lengths(joins.size());
+  std::vector<int32_t> cluster(ctx->n);
+  stage_begin(ctx, ST_TREE);
+  TRY(cluster_tree(ctx, S, cap, joins.data(), lengths.data(), cluster.data()));
+  stage_end(ctx, ST_TREE);
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_TREE);
+  if (!joins.empty()) {
+    CK(cudaMemcpyAsync(joins_out, joins.data(), sizeof(int32_t) * joins.size(), cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(lengths_out, lengths.data(), sizeof(double) * lengths.size(), cudaMemcpyDefault, ctx->st));
+  }
+  if (cluster_out)
+    CK(cudaMemcpyAsync(cluster_out, cluster.data(), sizeof(int32_t) * cluster.size(), cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MSA_OK;
 }

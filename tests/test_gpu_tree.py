@@ -87,3 +87,53 @@ def test_tree_of_the_msa(name, n):
         joins, lengths = b.msa_nj_tree(h)
     assert (d == od).all()
     assert (joins == oj).all() and (lengths == ol).all()
+
+
+@pytest.mark.parametrize("name,n,frac,cap", [("batched_uneven_10k", 600, 0.1, 6),
+                                             ("similar_dna_100k", 400, 0.1, 8),
+                                             ("plain_protein_200", 200, 0.2, 5),
+                                             ("plain_protein_200", 120, 0.1, 1)])
+def test_clustered_tree_of_the_msa(name, n, frac, cap):
+    """The clustered tree (sample tree cut into clusters, rows labelled, one
+    outgroup-rooted tree per cluster, grafted back): joins, branch lengths and
+    labels equal the oracle's on its own MSA."""
+    b = binding()
+    letters, offsets, w, alph, M = workload(name, n=n, seed=33)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    center = int(np.argsort(np.diff(offsets), kind="stable")[n // 2])
+    _, _, _, _, _, orows = oracle.msa(prob, center)
+    sample = np.sort(np.random.default_rng(4).choice(n, max(2, int(frac * n)), replace=False))
+    oj, ol, oc = T.cluster_tree(T.msa_distances(orows), sample, cap)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        with pytest.raises(b.MSAError):
+            b.msa_nj_cluster_tree(h, sample, cap)  # before a merge
+        b.msa_align_to_center(h, center)
+        b.msa_merge_gaps(h, want_rows=False)
+        joins, lengths, cluster = b.msa_nj_cluster_tree(h, sample, cap)
+        with pytest.raises(b.MSAError):
+            b.msa_nj_cluster_tree(h, [0, n], cap)  # a row out of range
+    assert (cluster == oc).all()
+    assert (joins == oj).all() and (lengths == ol).all()
+    print(name, "clusters", int(cluster.max()) + 1)
+
+
+def test_clustered_tree_degenerate_cuts():
+    """One sample row (a single cluster: the NJ tree of all rows) and every
+    row sampled with a cap above them (no cut): both equal the oracle's and,
+    as unrooted trees, the plain NJ tree."""
+    b = binding()
+    letters, offsets, w, alph, M = workload("plain_protein_200", n=90, seed=8)
+    prob = oracle_problem(letters, offsets, alph, M, w.gap_open, w.gap_extend)
+    _, _, _, _, _, orows = oracle.msa(prob, 5)
+    D = T.msa_distances(orows)
+    nj_splits = T.splits(*T.nj(D), 90)
+    with make_ctx(alph, M, w.gap_open, w.gap_extend) as h:
+        b.msa_load(h, letters, offsets)
+        b.msa_align_to_center(h, 5)
+        b.msa_merge_gaps(h, want_rows=False)
+        for sample, cap in (([17], 1), (np.arange(90), 90)):
+            oj, ol, oc = T.cluster_tree(D, sample, cap)
+            joins, lengths, cluster = b.msa_nj_cluster_tree(h, sample, cap)
+            assert (joins == oj).all() and (lengths == ol).all() and (cluster == oc).all()
+            assert T.splits(joins, lengths, 90) == nj_splits
