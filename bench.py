@@ -121,6 +121,12 @@ def parse():
                     help="threads per CTA of the packed alignment kernel (256 or 384)")
     ap.add_argument("--only-tree", action="store_true",
                     help="time the neighbour-joining tree of the workload's MSA only")
+    ap.add_argument("--tree-sample", type=float, default=0.0,
+                    help="with --only-tree: the clustered tree over a seeded sample of this "
+                         "fraction of the rows (else one NJ over all rows)")
+    ap.add_argument("--tree-cap", type=int, default=0,
+                    help="with --tree-sample: sample rows per cluster at most (default: a "
+                         "tenth of the sample)")
     ap.add_argument("--no-tree-record", action="store_true",
                     help="skip the neighbour-joining tree of the step's MSA")
     ap.add_argument("--no-align-record", action="store_true",
@@ -585,10 +591,27 @@ def run_ours(args):
         b.msa_set_align_threads(h, args.align_threads)
     if args.only_tree:
         lens = np.diff(offsets)
-        center = int(np.argsort(lens, kind="stable")[len(lens) // 2])
+        center = 0 if (w.center_seq or args.center == "first") else \
+            int(np.argsort(lens, kind="stable")[len(lens) // 2])
         b.msa_load(h, dlet, offsets)
         b.msa_align_to_center(h, center)
         _, Wt = b.msa_merge_gaps(h, want_rows=False)
+        if args.tree_sample > 0:
+            m = max(2, int(round(args.tree_sample * n)))
+            sample = np.sort(np.random.default_rng(12).choice(n, m, replace=False))
+            cap = args.tree_cap or max(1, m // 10)
+            for _ in range(max(1, args.warmup)):
+                t0 = time.perf_counter()
+                joins, lengths, cluster = b.msa_nj_cluster_tree(h, sample, cap)
+                wall = time.perf_counter() - t0
+            sizes = np.bincount(cluster)
+            print(json.dumps({"only_tree": True, "clustered": True, "n": n, "msa_width": Wt,
+                              "sample": m, "cap": cap, "clusters": int(sizes.size),
+                              "largest_cluster": int(sizes.max()), "seconds": wall,
+                              "tree_stage_ms": b.msa_stage_times(h)[0]["tree"],
+                              "joins": int(len(joins))}))
+            ctx.close()
+            return
         for _ in range(max(1, args.warmup)):
             rec = tree_record(b, h, n, Wt, stream, measured_peaks().get("hbm_gbs", 6800.0),
                               cpu_n=min(n, 300))
