@@ -45,6 +45,10 @@ struct msa_ctx {
   int n = 0, maxlen = 0;
   std::vector<int32_t> len_sorted, perm, inv;
   std::vector<int64_t> pstart;
+  // host scratch kept between calls (a fresh multi-megabyte vector per call
+  // pays its page faults every time)
+  std::vector<int32_t> h_lens;
+  std::vector<int64_t> h_offs;
   DevBuf res, d_pstart, d_len, d_perm, d_inv, d_srcoff, staging;
 
   // center selection

@@ -827,7 +827,8 @@ int msa_load(msa_ctx *ctx, const uint8_t *letters, const int64_t *offsets, int64
   if (n > (int64_t)INT32_MAX / 2) return fail(ctx, MSA_ERANGE, "too many sequences");
   if (offsets[0] != 0) return fail(ctx, MSA_EINVAL, "offsets[0] must be 0");
   TRY(set_device(ctx));
-  std::vector<int32_t> lens(n);
+  std::vector<int32_t> &lens = ctx->h_lens;
+  lens.resize(n);
   int maxlen = 0;
   for (int64_t t = 0; t < n; ++t) {
     const int64_t L = offsets[t + 1] - offsets[t];
@@ -839,21 +840,27 @@ int msa_load(msa_ctx *ctx, const uint8_t *letters, const int64_t *offsets, int64
   ctx->aligned = ctx->merged = ctx->have_rowsum = false;
   ctx->n = (int)n;
   ctx->maxlen = maxlen;
-  // stable sort by length: a counting sort (lengths are at most MSA_MAX_LEN)
+  // stable sort by length: a counting sort (lengths are at most MSA_MAX_LEN);
+  // the inverse permutation is written in input order during the scatter and
+  // the sorted lengths from the bucket counts, so no pass gathers at random
   ctx->perm.resize(n);
+  ctx->inv.resize(n);
+  ctx->len_sorted.resize(n);
+  ctx->pstart.resize(n);
   {
     std::vector<int64_t> first(maxlen + 2, 0);
     for (int64_t t = 0; t < n; ++t) ++first[lens[t] + 1];
     for (int L = 1; L <= maxlen + 1; ++L) first[L] += first[L - 1];
-    for (int64_t t = 0; t < n; ++t) ctx->perm[first[lens[t]]++] = (int32_t)t;
+    for (int L = 1; L <= maxlen; ++L)
+      std::fill(ctx->len_sorted.begin() + first[L], ctx->len_sorted.begin() + first[L + 1], L);
+    for (int64_t t = 0; t < n; ++t) {
+      const int64_t k = first[lens[t]]++;
+      ctx->perm[k] = (int32_t)t;
+      ctx->inv[t] = (int32_t)k;
+    }
   }
-  ctx->inv.resize(n);
-  ctx->len_sorted.resize(n);
-  ctx->pstart.resize(n);
   int64_t pos = 0;
   for (int64_t k = 0; k < n; ++k) {
-    ctx->inv[ctx->perm[k]] = (int32_t)k;
-    ctx->len_sorted[k] = lens[ctx->perm[k]];
     ctx->pstart[k] = pos;
     pos += round_up_i64(ctx->len_sorted[k], 16) + MSA_SEQ_TAIL;
   }
@@ -1103,15 +1110,28 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   CK(cudaMemsetAsync(ctx->occ.p, 0, row * n, ctx->st));
   CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
 
-  // batches of subjects (sorted order) whose codes fit the budget
-  size_t free_b = 0, total_b = 0;
-  CK(cudaMemGetInfo(&free_b, &total_b));
-  size_t budget = std::min(ctx->codes_budget, free_b / 2);
-  if (ctx->dev_limit) budget = std::min(budget, ctx->dev_limit > ctx->dev_bytes ? (ctx->dev_limit - ctx->dev_bytes) / 2 : 0);
+  // batches of subjects (sorted order) whose codes fit the budget; when all
+  // of them fit the codes buffer the context already holds (and the budget),
+  // one batch, without asking the driver for the free memory
+  size_t all_codes = 0;
+  int64_t cells = 0;
+  for (int k = 0; k < n; ++k) {
+    all_codes += code_words(ctx->len_sorted[k], Lc, G) * 8;
+    cells += (int64_t)Lc * ctx->len_sorted[k];
+  }
+  size_t budget = all_codes;
+  if (all_codes > ctx->codes.cap || all_codes > ctx->codes_budget ||
+      (ctx->dev_limit && all_codes > ctx->codes.cap)) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    budget = std::min(ctx->codes_budget, free_b / 2);
+    if (ctx->dev_limit) budget = std::min(budget, ctx->dev_limit > ctx->dev_bytes ? (ctx->dev_limit - ctx->dev_bytes) / 2 : 0);
+  }
   size_t max_one = code_words(ctx->maxlen, Lc, G) * 8;
   if (budget < max_one) budget = max_one;
   std::vector<std::pair<int, int>> batches;
-  std::vector<int64_t> offs(n);
+  std::vector<int64_t> &offs = ctx->h_offs;
+  offs.resize(n);
   size_t biggest = 0;
   {
     int b = 0;
@@ -1142,8 +1162,6 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   if (npass > 1)
     TRY(ensure(ctx, ctx->scratch, (size_t)grid * (codes_threads(packed, cta) / G) * 2 * ctx->maxlen * sizeof(int2)));
   float ms_dp = 0.f, ms_tb = 0.f;
-  int64_t cells = 0;
-  for (int k = 0; k < n; ++k) cells += (int64_t)Lc * ctx->len_sorted[k];
   // All batches as one CUDA graph (captured on the context's private stream,
   // launched on its stream, cached while the key holds): per batch the fill
   // and the traceback, with timing events, and no host round trip between
