@@ -422,7 +422,7 @@ int msa_tree_distances(msa_ctx *ctx, int64_t *dist_out);
 /* Neighbour joining (Saitou and Nei, the method the paper's tree section
  * cites) of an n x n integer distance matrix `dist` (host or device int64,
  * row-major, symmetric, zero diagonal; |entries| and every joined distance
- * within 2^40, else ERANGE).  Reading, with m nodes active: r_i = sum of
+ * within 2^30 -- the joins keep an int32 matrix -- else ERANGE).  Reading, with m nodes active: r_i = sum of
  * d(i, k) over the active k; the active pair i < j of smallest
  * Q = (m - 2) d(i, j) - r_i - r_j joins, ties to the smallest i, then the
  * smallest j, where slots are numbered as the input rows and a new node

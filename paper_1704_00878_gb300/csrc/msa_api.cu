@@ -89,7 +89,7 @@ int check_derr(msa_ctx *ctx) {
   if (h[0] & MSA_DERR_TRACE) return fail(ctx, MSA_ECUDA, "inconsistent traceback codes");
   if (h[0] & MSA_DERR_OVERFLOW) return fail(ctx, MSA_ENOMEM, "int16 overflow list full");
   if (h[0] & MSA_DERR_TIMEOUT_TC) return fail(ctx, MSA_ETIMEOUT, "tensor-core convolution timed out");
-  if (h[0] & MSA_DERR_RANGE) return fail(ctx, MSA_ERANGE, "a tree distance beyond 2^40");
+  if (h[0] & MSA_DERR_RANGE) return fail(ctx, MSA_ERANGE, "a tree distance beyond 2^30");
   return MSA_OK;
 }
 

@@ -10,7 +10,8 @@
 // counters (compared, mismatched) gather up to 64 words before they are
 // summed into 32-bit totals.
 //
-// Neighbour joining: the matrix stays on the device (int64, positions in
+// Neighbour joining: the matrix stays on the device (int32 -- every entry and
+// joined distance within 2^30, else ERANGE -- positions in
 // ascending slot order); every join is two launches -- the minimum of Q over
 // the active pairs (a warp per row, lanes along it, the last CTA to finish
 // reduces the CTAs' minima) and the join itself (CTAs over the rows: branch lengths,
@@ -30,8 +31,9 @@ namespace {
 constexpr int kTile = 64;    // rows per side of a distance tile
 constexpr int kWords = 64;   // 32-bit words (4 columns) per staged chunk
 constexpr long long kDScale = 1LL << 20;
-constexpr long long kDLimit = 1LL << 40;  // |distance| bound of the joins
+constexpr long long kDLimit = 1LL << 30;  // |distance| bound of the joins (int32 matrix)
 constexpr int kArgThreads = 256;
+constexpr int kUnroll = 8;  // loads per lane in flight in the Q minimum (16 measured slower)
 constexpr int kJoinThreads = 1024;
 
 // 0x80 in every byte of w that is nonzero
@@ -180,7 +182,7 @@ __device__ __forceinline__ Pick block_min(Pick p, Pick *sh) {
 // The active pair of smallest Q = (m - 2) d(x, y) - r_x - r_y, ties to the
 // smallest x, then y (positions ascend with the slots).  The last CTA to
 // finish reduces every CTA's minimum into sel = {x, y}.
-__global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__restrict__ D, int P,
+__global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const int *__restrict__ D, int P,
                                                            const long long *__restrict__ r,
                                                            const uint8_t *__restrict__ act, int m,
                                                            Pick *__restrict__ part,
@@ -195,21 +197,21 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__re
   for (int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < P; x += warps) {
     if (!act[x]) continue;
     const long long rx = r[x];
-    const long long *row = D + (size_t)x * P;
+    const int *row = D + (size_t)x * P;
     const int yend = P;
-    // four independent loads per lane in flight
-    for (int y0 = x + 1 + lane; y0 < yend; y0 += 128) {
-      long long dv[4], rv[4];
-      bool ok[4];
+    // kUnroll independent loads per lane in flight
+    for (int y0 = x + 1 + lane; y0 < yend; y0 += 32 * kUnroll) {
+      long long dv[kUnroll], rv[kUnroll];
+      bool ok[kUnroll];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kUnroll; ++u) {
         const int y = y0 + 32 * u;
         ok[u] = y < yend && act[y];
         dv[u] = ok[u] ? row[y] : 0;
         rv[u] = ok[u] ? r[y] : 0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kUnroll; ++u) {
         const int y = y0 + 32 * u;
         const Pick c{f * dv[u] - rx - rv[u], ((long long)x << 32) | (long long)y};
         if (ok[u] && pick_less(c, best)) best = c;
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const long long *__re
 // node n + t in position x, its distances floor((d(x,k) + d(y,k) - d(x,y)) / 2),
 // the row sums, y retired.  CTAs take ranges of k; the last CTA to finish
 // adds up their sums into r_x (every CTA has read r_x by then).
-__global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict__ D, int P,
+__global__ void __launch_bounds__(kJoinThreads) k_nj_join(int *__restrict__ D, int P,
                                                           long long *__restrict__ r,
                                                           uint8_t *__restrict__ act,
                                                           int *__restrict__ node, int m,
@@ -272,8 +274,8 @@ __global__ void __launch_bounds__(kJoinThreads) k_nj_join(long long *__restrict_
     const long long dxk = D[(size_t)x * P + k], dyk = D[(size_t)y * P + k];
     const long long dn = (dxk + dyk - dxy) >> 1;
     bad |= dn > kDLimit || dn < -kDLimit;
-    D[(size_t)x * P + k] = dn;
-    D[(size_t)k * P + x] = dn;
+    D[(size_t)x * P + k] = (int)dn;
+    D[(size_t)k * P + x] = (int)dn;
     r[k] += dn - dxk - dyk;
     sum += dn;
   }
@@ -339,9 +341,9 @@ __global__ void __launch_bounds__(1024) k_nj_index(const uint8_t *__restrict__ a
 }
 
 // The matrix, row sums and node ids packed to the m active positions.
-__global__ void k_nj_pack(const long long *__restrict__ D, int P, const long long *__restrict__ r,
+__global__ void k_nj_pack(const int *__restrict__ D, int P, const long long *__restrict__ r,
                           const int *__restrict__ node, const int *__restrict__ idx, int m,
-                          long long *__restrict__ D2, long long *__restrict__ r2,
+                          int *__restrict__ D2, long long *__restrict__ r2,
                           int *__restrict__ node2, uint8_t *__restrict__ act2) {
   const int u = blockIdx.y;
   const int su = idx[u];
@@ -355,7 +357,7 @@ __global__ void k_nj_pack(const long long *__restrict__ D, int P, const long lon
 }
 
 // The root: the two active positions joined at the middle of their edge.
-__global__ void k_nj_root(const long long *__restrict__ D, int P, const uint8_t *__restrict__ act,
+__global__ void k_nj_root(const int *__restrict__ D, int P, const uint8_t *__restrict__ act,
                           const int *__restrict__ node, int t, int *__restrict__ joins,
                           double *__restrict__ lengths) {
   if (threadIdx.x != 0) return;
@@ -373,8 +375,21 @@ __global__ void k_nj_root(const long long *__restrict__ D, int P, const uint8_t 
   lengths[2 * t + 1] = half;
 }
 
+// The int64 matrix into the int32 one the joins work on; entries beyond the
+// bound set the range error.
+__global__ void k_nj_narrow(const long long *__restrict__ D64, size_t count, int *__restrict__ D,
+                            unsigned *__restrict__ err) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const long long v = D64[i];
+    bad |= v > kDLimit || v < -kDLimit;
+    D[i] = (int)v;
+  }
+  if (bad) atomicOr(err, MSA_DERR_RANGE);
+}
+
 // Row sums (one warp per row), node ids, every position active.
-__global__ void k_nj_init(long long *__restrict__ r, const long long *__restrict__ D, int n,
+__global__ void k_nj_init(long long *__restrict__ r, const int *__restrict__ D, int n,
                           int *__restrict__ node, uint8_t *__restrict__ act) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -430,12 +445,12 @@ int tree_distances(msa_ctx *ctx, DevBuf &D) {
   return list_distances(ctx, nullptr, n, P<long long>(D));
 }
 
-// Neighbour joining of the n x n matrix in D (device, int64, consumed).
+// Neighbour joining of the n x n matrix in D (device, int64, left as it is).
 int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *lengths_out) {
   if (n < 2) return MSA_OK;
-  DevBuf D2, r, r2, node, node2, act, act2, idx, part, jpart, sel, joins, lengths;
+  DevBuf D1, D2, r, r2, node, node2, act, act2, idx, part, jpart, sel, joins, lengths;
   auto cleanup = [&]() {
-    for (DevBuf *b : {&D2, &r, &r2, &node, &node2, &act, &act2, &idx, &part, &jpart, &sel, &joins,
+    for (DevBuf *b : {&D1, &D2, &r, &r2, &node, &node2, &act, &act2, &idx, &part, &jpart, &sel, &joins,
                       &lengths})
       release(ctx, *b);
   };
@@ -456,23 +471,26 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
     unsigned *ticket = reinterpret_cast<unsigned *>(P<int>(sel) + 2);
     CK(cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned), ctx->st));
     CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
-    ++ctx->launches;
-    k_nj_init<<<grid, 256, 0, ctx->st>>>(P<long long>(r), P<long long>(D), n, P<int>(node),
+    TRY(ensure(ctx, D1, sizeof(int) * (size_t)n * n));
+    ctx->launches += 2;
+    k_nj_narrow<<<grid, 256, 0, ctx->st>>>(P<long long>(D), (size_t)n * n, P<int>(D1), ctx->derr);
+    CK(cudaGetLastError());
+    k_nj_init<<<grid, 256, 0, ctx->st>>>(P<long long>(r), P<int>(D1), n, P<int>(node),
                                          P<uint8_t>(act));
     CK(cudaGetLastError());
-    DevBuf *cD = &D, *cR = &r, *cN = &node, *cA = &act;
+    DevBuf *cD = &D1, *cR = &r, *cN = &node, *cA = &act;
     DevBuf *oD = &D2, *oR = &r2, *oN = &node2, *oA = &act2;
     int Pn = n, m = n, t = 0;
     while (m > 2) {
       ctx->launches += 2;
       // a warp per row at least: small matrices take few CTAs
       const int agrid = std::max(1, std::min(grid, (Pn + kArgThreads / 32 - 1) / (kArgThreads / 32)));
-      k_nj_argmin<<<agrid, kArgThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
+      k_nj_argmin<<<agrid, kArgThreads, 0, ctx->st>>>(P<int>(*cD), Pn, P<long long>(*cR),
                                                      P<uint8_t>(*cA), m, P<Pick>(part), ticket,
                                                      P<int>(sel));
       CK(cudaGetLastError());
       const int jgrid = std::max(1, std::min(jmax, (Pn + kJoinThreads - 1) / kJoinThreads));
-      k_nj_join<<<jgrid, kJoinThreads, 0, ctx->st>>>(P<long long>(*cD), Pn, P<long long>(*cR),
+      k_nj_join<<<jgrid, kJoinThreads, 0, ctx->st>>>(P<int>(*cD), Pn, P<long long>(*cR),
                                                      P<uint8_t>(*cA), P<int>(*cN), m, P<int>(sel), t,
                                                      n, P<int>(joins), P<double>(lengths),
                                                      P<long long>(jpart), ticket + 1, ctx->derr);
@@ -480,7 +498,7 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
       --m;
       ++t;
       if (m > 2 && Pn >= 512 && 4 * m <= 3 * Pn) {  // pack to the active positions
-        TRY(ensure(ctx, *oD, sizeof(long long) * (size_t)m * m));
+        TRY(ensure(ctx, *oD, sizeof(int) * (size_t)m * m));
         TRY(ensure(ctx, *oR, sizeof(long long) * m));
         TRY(ensure(ctx, *oN, sizeof(int) * m));
         TRY(ensure(ctx, *oA, (size_t)m));
@@ -488,7 +506,7 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
         k_nj_index<<<1, 1024, 0, ctx->st>>>(P<uint8_t>(*cA), Pn, P<int>(idx));
         CK(cudaGetLastError());
         k_nj_pack<<<dim3((m + 255) / 256, m), 256, 0, ctx->st>>>(
-            P<long long>(*cD), Pn, P<long long>(*cR), P<int>(*cN), P<int>(idx), m, P<long long>(*oD),
+            P<int>(*cD), Pn, P<long long>(*cR), P<int>(*cN), P<int>(idx), m, P<int>(*oD),
             P<long long>(*oR), P<int>(*oN), P<uint8_t>(*oA));
         CK(cudaGetLastError());
         std::swap(cD, oD);
@@ -499,7 +517,7 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
       }
     }
     ++ctx->launches;
-    k_nj_root<<<1, 32, 0, ctx->st>>>(P<long long>(*cD), Pn, P<uint8_t>(*cA), P<int>(*cN), t,
+    k_nj_root<<<1, 32, 0, ctx->st>>>(P<int>(*cD), Pn, P<uint8_t>(*cA), P<int>(*cN), t,
                                       P<int>(joins), P<double>(lengths));
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(joins_out, joins.p, sizeof(int) * 2 * (size_t)(n - 1), cudaMemcpyDefault,
@@ -650,11 +668,9 @@ int cluster_tree(msa_ctx *ctx, const std::vector<int32_t> &S, int cap, int32_t *
     CK(cudaMemcpyAsync(dlist.p, S.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->st));
     TRY(ensure(ctx, dS, sizeof(long long) * (size_t)m * m));
     TRY(list_distances(ctx, P<int32_t>(dlist), m, P<long long>(dS)));
-    TRY(ensure(ctx, dS2, sizeof(long long) * (size_t)m * m));
-    CK(cudaMemcpyAsync(dS2.p, dS.p, sizeof(long long) * (size_t)m * m, cudaMemcpyDeviceToDevice, ctx->st));
     std::vector<int32_t> sj(2 * std::max(m - 1, 0));
     std::vector<double> sl(2 * std::max(m - 1, 0));
-    if (m > 1) TRY(nj_device(ctx, dS2, m, sj.data(), sl.data()));
+    if (m > 1) TRY(nj_device(ctx, dS, m, sj.data(), sl.data()));
     CK(cudaStreamSynchronize(ctx->st));
     Kids skids;
     int sroot = 0;
