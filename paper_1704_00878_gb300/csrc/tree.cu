@@ -13,7 +13,7 @@
 // Neighbour joining: the matrix stays on the device (int32 -- every entry and
 // joined distance within 2^30, else ERANGE -- positions in
 // ascending slot order); every join is two launches -- the minimum of Q over
-// the active pairs (a warp per row, lanes along it, the last CTA to finish
+// the active pairs (warps over 512-column segments of the rows, the last CTA to finish
 // reduces the CTAs' minima) and the join itself (CTAs over the rows: branch lengths,
 // the new node's row and column, the row sums updated in place; the last
 // CTA to finish adds up the new node's row sum).  When a quarter of the
@@ -34,6 +34,7 @@ constexpr long long kDScale = 1LL << 20;
 constexpr long long kDLimit = 1LL << 30;  // |distance| bound of the joins (int32 matrix)
 constexpr int kArgThreads = 256;
 constexpr int kUnroll = 8;  // loads per lane in flight in the Q minimum (16 measured slower)
+constexpr int kSeg = 2 * 32 * kUnroll;  // columns of one warp task of the Q minimum
 constexpr int kJoinThreads = 1024;
 
 // 0x80 in every byte of w that is nonzero
@@ -185,6 +186,7 @@ __device__ __forceinline__ Pick block_min(Pick p, Pick *sh) {
 __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const int *__restrict__ D, int P,
                                                            const long long *__restrict__ r,
                                                            const uint8_t *__restrict__ act, int m,
+                                                           const int2 *__restrict__ tasks, int ntask,
                                                            Pick *__restrict__ part,
                                                            unsigned *__restrict__ ticket,
                                                            int *__restrict__ sel) {
@@ -194,13 +196,17 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const int *__restrict
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const long long f = m - 2;
   Pick best{LLONG_MAX, LLONG_MAX};
-  for (int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < P; x += warps) {
+  // warp tasks: (row x, first column) of kSeg-column segments of the upper
+  // triangle, so the long rows of the first joins spread over many warps
+  for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += warps) {
+    const int2 tk = tasks[task];
+    const int x = tk.x;
     if (!act[x]) continue;
     const long long rx = r[x];
     const int *row = D + (size_t)x * P;
-    const int yend = P;
+    const int yend = min(P, tk.y + kSeg);
     // kUnroll independent loads per lane in flight
-    for (int y0 = x + 1 + lane; y0 < yend; y0 += 32 * kUnroll) {
+    for (int y0 = tk.y + lane; y0 < yend; y0 += 32 * kUnroll) {
       long long dv[kUnroll], rv[kUnroll];
       bool ok[kUnroll];
 #pragma unroll
@@ -448,10 +454,10 @@ int tree_distances(msa_ctx *ctx, DevBuf &D) {
 // Neighbour joining of the n x n matrix in D (device, int64, left as it is).
 int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *lengths_out) {
   if (n < 2) return MSA_OK;
-  DevBuf D1, D2, r, r2, node, node2, act, act2, idx, part, jpart, sel, joins, lengths;
+  DevBuf D1, D2, r, r2, node, node2, act, act2, idx, part, jpart, sel, joins, lengths, tasks;
   auto cleanup = [&]() {
     for (DevBuf *b : {&D1, &D2, &r, &r2, &node, &node2, &act, &act2, &idx, &part, &jpart, &sel, &joins,
-                      &lengths})
+                      &lengths, &tasks})
       release(ctx, *b);
   };
   int rc = [&]() -> int {
@@ -478,16 +484,29 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
     k_nj_init<<<grid, 256, 0, ctx->st>>>(P<long long>(r), P<int>(D1), n, P<int>(node),
                                          P<uint8_t>(act));
     CK(cudaGetLastError());
+    // the Q minimum's warp tasks for a matrix of P positions
+    std::vector<int2> htasks;
+    int ntask = 0;
+    auto make_tasks = [&](int Pm) -> int {
+      htasks.clear();
+      for (int x = 0; x + 1 < Pm; ++x)
+        for (int y = x + 1; y < Pm; y += kSeg) htasks.push_back(make_int2(x, y));
+      ntask = (int)htasks.size();
+      TRY(ensure(ctx, tasks, sizeof(int2) * std::max(ntask, 1)));
+      CK(cudaMemcpyAsync(tasks.p, htasks.data(), sizeof(int2) * ntask, cudaMemcpyHostToDevice, ctx->st));
+      return MSA_OK;
+    };
+    TRY(make_tasks(n));
     DevBuf *cD = &D1, *cR = &r, *cN = &node, *cA = &act;
     DevBuf *oD = &D2, *oR = &r2, *oN = &node2, *oA = &act2;
     int Pn = n, m = n, t = 0;
     while (m > 2) {
       ctx->launches += 2;
-      // a warp per row at least: small matrices take few CTAs
-      const int agrid = std::max(1, std::min(grid, (Pn + kArgThreads / 32 - 1) / (kArgThreads / 32)));
+      // a warp per task at least: small matrices take few CTAs
+      const int agrid = std::max(1, std::min(grid, (ntask + kArgThreads / 32 - 1) / (kArgThreads / 32)));
       k_nj_argmin<<<agrid, kArgThreads, 0, ctx->st>>>(P<int>(*cD), Pn, P<long long>(*cR),
-                                                     P<uint8_t>(*cA), m, P<Pick>(part), ticket,
-                                                     P<int>(sel));
+                                                     P<uint8_t>(*cA), m, P<int2>(tasks), ntask,
+                                                     P<Pick>(part), ticket, P<int>(sel));
       CK(cudaGetLastError());
       const int jgrid = std::max(1, std::min(jmax, (Pn + kJoinThreads - 1) / kJoinThreads));
       k_nj_join<<<jgrid, kJoinThreads, 0, ctx->st>>>(P<int>(*cD), Pn, P<long long>(*cR),
@@ -514,6 +533,7 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
         std::swap(cN, oN);
         std::swap(cA, oA);
         Pn = m;
+        TRY(make_tasks(Pn));
       }
     }
     ++ctx->launches;
