@@ -785,7 +785,21 @@ def run_ours(args):
         b.msa_load(h, dlet, offsets)
         b.msa_align_to_center(h, c)
         _, Wt = b.msa_merge_gaps(h, want_rows=False)
-        tree = tree_record(b, h, n, Wt, stream, measured_peaks().get("hbm_gbs", 6800.0))
+        if n <= 20000:  # one NJ over all rows (an n x n matrix)
+            tree = tree_record(b, h, n, Wt, stream, measured_peaks().get("hbm_gbs", 6800.0))
+        elif n <= 200000:  # the clustered tree over a 10 % sample
+            m = n // 10
+            sample = np.sort(np.random.default_rng(12).choice(n, m, replace=False))
+            t0 = time.perf_counter()
+            joins, _, cluster = b.msa_nj_cluster_tree(h, sample, max(1, m // 10))
+            sizes = np.bincount(cluster)
+            tree = {"workload": "clustered NJ tree of the step's %d-row MSA (%d columns): 10 %% "
+                                "sample, at most %d sample rows per cluster" % (n, Wt, max(1, m // 10)),
+                    "seconds": time.perf_counter() - t0, "clusters": int(sizes.size),
+                    "largest_cluster": int(sizes.max()), "joins": int(len(joins))}
+        else:
+            tree = {"skipped": "%d rows: a cluster of a 10 %% sample would pass the 65,536-row "
+                               "limit of one NJ" % n}
     align = None
     if not args.no_align_record and rank == 0:
         align = align_record(flush, stream, measured_peaks().get("hbm_gbs", 6800.0),
