@@ -117,6 +117,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuners (center variants per length bucket; alignment "
                          "group width and int16x2 / int32 cells) and use the cost models")
+    ap.add_argument("--align-mode", default="full", choices=["full", "box", "both"],
+                    help="with --only-align: the full alignment (codes of every cell), the "
+                         "traceback-light one (score pass, reverse pass, codes of each box), "
+                         "or both, checked equal")
     ap.add_argument("--align-threads", type=int, default=0,
                     help="threads per CTA of the packed alignment kernel (256 or 384)")
     ap.add_argument("--only-tree", action="store_true",
@@ -285,6 +289,50 @@ def workload_text(w, n, center, length=None):
                                                 else "sampled exact (1,000 references)"))
 
 
+def time_alignment(b, h, center, mode, flush, stream, n, reps=3):
+    """msa_align_to_center in one mode (MSA_ALIGN_FULL / MSA_ALIGN_BOX), L2
+    flushed before each of `reps` timed calls: the call (CUDA events on the
+    context stream, host round trips included), the kernels' own time from the
+    library's stage events, and for the box mode its passes and the cells its
+    codes covered."""
+    import torch
+    b.msa_set_align_mode(h, mode)
+    for _ in range(2):
+        b.msa_align_to_center(h, center)
+    call, kern, tb, passes = [], [], [], {"light_score": [], "light_corner": [], "light_box": []}
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.msa_align_to_center(h, center)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        call.append(ev0.elapsed_time(ev1))
+        ms, cnt = b.msa_stage_times(h)
+        kern.append(ms["align_kernels"])
+        tb.append(ms["traceback"])
+        for k in passes:
+            passes[k].append(ms[k])
+    cells = cnt["align_cells"]
+    k = float(np.mean(kern))
+    rec = {"kernel_ms": k, "traceback_ms": float(np.mean(tb)), "call_ms": float(np.mean(call)),
+           "cells": cells, "gcups": cells / (k * 1e-3) / 1e9}
+    seg = b.msa_alignment_info(h)[0]
+    if mode == b.MSA_ALIGN_BOX:
+        boxes = b.msa_align_boxes(h, n)
+        box_cells = int(((boxes[:, 2] - boxes[:, 0]).astype(np.int64) *
+                         (boxes[:, 3] - boxes[:, 1])).sum())
+        rec.update({"pass_ms": {k2[6:]: float(np.mean(v)) for k2, v in passes.items()},
+                    "box_cells": box_cells, "box_fraction": box_cells / cells,
+                    "code_bytes": box_cells * CODES_BYTES_PER_CELL})
+    else:
+        rec["code_bytes"] = cells * CODES_BYTES_PER_CELL
+    b.msa_set_align_mode(h, b.MSA_ALIGN_FULL)
+    return rec, seg
+
+
 def align_record(flush, stream, peak_gbs, no_tune=False):
     """The alignment to the center with traceback codes (the batched DP), on
     its own: 200,000 short peptides (the 1e6-peptide workload's generator and
@@ -319,8 +367,14 @@ def align_record(flush, stream, peak_gbs, no_tune=False):
             kern_ms.append(ms["align_kernels"])
             tb_ms.append(ms["traceback"])
         cells = cnt["align_cells"]
+        full_seg = b.msa_alignment_info(h)[0]
+        light, light_seg = time_alignment(b, h, 0, b.MSA_ALIGN_BOX, flush, stream, ALIGN_N)
     k = float(np.mean(kern_ms))
     gcups = cells / (k * 1e-3) / 1e9
+    light.update(same_as_full=bool((light_seg == full_seg).all()),
+                 kernel_vs_full=light["kernel_ms"] / k,
+                 note="traceback-light: score pass to the best cell, reverse pass to the corner, "
+                      "codes of each segment's box only; gcups over the full matrices' cells")
     tuned = None
     if tune is not None:
         rates, (lanes, packed, cta) = tune
@@ -334,7 +388,7 @@ def align_record(flush, stream, peak_gbs, no_tune=False):
                         "one family at 30%% substitutions, 3%% indels) against their %d-residue "
                         "ancestor, BLOSUM62 11/1, packed int16x2 cells" % (ALIGN_N - 1, lens[0]),
             "cells": cells, "kernel_ms": k, "traceback_ms": float(np.mean(tb_ms)),
-            "call_ms": float(np.mean(call_ms)), "gcups": gcups,
+            "call_ms": float(np.mean(call_ms)), "gcups": gcups, "light": light,
             "gcups_with_traceback": cells / (float(np.mean(call_ms)) * 1e-3) / 1e9,
             "roofline": {"bound": "alu", "kernel": "k_codes2 (Gotoh fill + 4-bit traceback codes, "
                                                   "two subjects per int16x2 register)",
@@ -666,6 +720,18 @@ def run_ours(args):
                               "full_matrix_cells": int(lens[center]) * int(lens.sum()),
                               "anchored": dict(rec_a, local_path_sequences=nf),
                               "smith_waterman": rec_s}))
+            ctx.close()
+            return
+        if args.align_mode != "full":
+            rec = {"only_align": True, "n": n, "center": center, "Lc": int(lens[center])}
+            segs = {}
+            for name, mode in (("full", b.MSA_ALIGN_FULL), ("box", b.MSA_ALIGN_BOX)):
+                if args.align_mode in (name, "both"):
+                    rec[name], segs[name] = time_alignment(b, h, center, mode, flush, stream, n)
+            if len(segs) == 2:
+                rec["same"] = bool((segs["full"] == segs["box"]).all())
+                rec["box_kernel_vs_full"] = rec["box"]["kernel_ms"] / rec["full"]["kernel_ms"]
+            print(json.dumps(rec))
             ctx.close()
             return
         for _ in range(max(1, args.warmup)):

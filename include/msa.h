@@ -410,6 +410,35 @@ int msa_set_align_group(msa_ctx *ctx, int32_t lanes);
  * does not depend on it.  EINVAL for any other value. */
 int msa_set_align_threads(msa_ctx *ctx, int32_t threads);
 
+/* How msa_align_to_center finds each subject's alignment (Eq. 1-2 and the
+ * traceback of Figure 2: from the highest-scoring cell back to a cell of
+ * score zero).  Both modes give the same result, bit for bit.
+ *   MSA_ALIGN_FULL (the default): one fill of every subject's whole matrix
+ *     that stores a 4-bit traceback code for every cell.
+ *   MSA_ALIGN_BOX (traceback-light): a forward fill that keeps only each
+ *     subject's best cell (i2, j2); a fill of the two prefixes ending there,
+ *     read backwards, that finds the largest reversed row P and column Q of a
+ *     cell scoring the best score (the first residue pair of some
+ *     best-scoring alignment ending at the best cell, the traced one among
+ *     them); then codes only for the box rows (i0, i2] x columns (j0, j2]
+ *     with j0 = j2 - Q and i0 = i2 - P rounded down to a multiple of 16, a
+ *     local alignment of those slices whose walk retraces the same path.
+ *     Codes take box area x 0.5 byte instead of matrix area x 0.5 byte; the
+ *     two extra fills cost more than the codes they save unless the segments
+ *     are short against the center.  Packed int16x2 cells only: where the
+ *     center's length rules them out, the call runs the full mode.
+ * EINVAL for any other mode. */
+#define MSA_ALIGN_FULL 0
+#define MSA_ALIGN_BOX  1
+int msa_set_align_mode(msa_ctx *ctx, int32_t mode);
+
+/* The boxes of the last msa_align_to_center that ran MSA_ALIGN_BOX: per
+ * sequence in input order {i0, j0, i2, j2} (the codes covered center rows
+ * i0+1..i2 and sequence columns j0+1..j2; i2, j2 is the best cell; all 0 for
+ * a sequence with no positive cell).  box_out: host or device int32[n * 4].
+ * ESTATE when the last alignment ran the full mode, or none ran. */
+int msa_align_boxes(msa_ctx *ctx, int32_t *box_out);
+
 /* Distances between the rows of the merged MSA for the phylogenetic tree
  * (the paper's section on NJ trees, Figure 4: the tree is built from the
  * MSA; the paper names no distance).  Reading: the p-distance over the

@@ -18,9 +18,10 @@ MSA_AUTO, MSA_INT16, MSA_INT32 = 0, 1, 2
 MSA_CENTER_EXACT, MSA_CENTER_EXACT_SAMPLED, MSA_CENTER_LEARNED, MSA_CENTER_FIRST = 0, 1, 2, 3
 MSA_CENTER_LEARNED_REFINED = 4
 MSA_MAX_LEN = 8192
+MSA_ALIGN_FULL, MSA_ALIGN_BOX = 0, 1
 
 STAGES = ("encode", "center", "align_dp", "traceback", "merge", "rows", "sp", "center_kernels",
-          "align_kernels", "selector", "tree")
+          "align_kernels", "selector", "tree", "light_score", "light_corner", "light_box")
 
 
 class MSAError(RuntimeError):
@@ -79,6 +80,8 @@ _SIGS = {
     "msa_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_tree_distances": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_set_align_threads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "msa_set_align_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "msa_align_boxes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "msa_nj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                               ctypes.c_void_p]),
     "msa_nj_tree": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -427,6 +430,20 @@ def msa_set_align_group(ctx, lanes):
     rc = lib().msa_set_align_group(ctx, int(lanes))
     if rc != MSA_OK:
         raise MSAError(rc, "align group must be 0 or one of %s" % (ALIGN_LANES,))
+
+
+def msa_set_align_mode(ctx, mode):
+    """MSA_ALIGN_FULL (codes of every cell) or MSA_ALIGN_BOX (traceback-light)."""
+    rc = lib().msa_set_align_mode(ctx, int(mode))
+    if rc != MSA_OK:
+        raise MSAError(rc, "align mode must be MSA_ALIGN_FULL or MSA_ALIGN_BOX")
+
+
+def msa_align_boxes(ctx, n, out=None):
+    """int32[n, 4] {i0, j0, i2, j2} per sequence of the last MSA_ALIGN_BOX alignment."""
+    res = np.zeros((n, 4), np.int32) if out is None else out
+    _check(ctx, lib().msa_align_boxes(ctx, _ptr(res)))
+    return res
 
 
 def msa_set_codes_budget(ctx, nbytes):

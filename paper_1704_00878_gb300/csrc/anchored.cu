@@ -377,7 +377,7 @@ int align_subset_local(msa_ctx *ctx, int kc, const std::vector<int32_t> &subj, f
                                            nv - 1, sc.M, sc.K, sc.o, sc.e, Lc, G,
                                            P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ),
                                            P<int32_t>(ctx->seg), P<int32_t>(ctx->score),
-                                           ctx->derr, ctx->st));
+                                           ctx->derr, ctx->st, nullptr, nullptr, nullptr));
     CK(cudaEventRecord(e1, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     float t = 0.f;

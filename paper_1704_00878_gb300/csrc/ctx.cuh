@@ -17,7 +17,7 @@ struct DevBuf {
 
 enum Stage {
   ST_ENCODE = 0, ST_CENTER, ST_ALIGN, ST_TRACE, ST_MERGE, ST_ROWS, ST_SP, ST_CENTER_K, ST_ALIGN_K,
-  ST_SELECTOR, ST_TREE, ST_N
+  ST_SELECTOR, ST_TREE, ST_LIGHT_SCORE, ST_LIGHT_CORNER, ST_LIGHT_BOX, ST_N
 };
 
 struct Selector;  // the learned center selector (selector.cu)
@@ -95,6 +95,16 @@ struct msa_ctx {
   int align_group = 0;  // lanes per subject group of the codes kernels, 0 = modelled choice
   int align_int32 = 0;  // 1: the alignment uses int32 cells even where packed ones fit
   int align_threads = 0;  // CTA size of the packed codes kernel, 0 = kCodes2Threads
+  // traceback-light alignment (MSA_ALIGN_BOX): per position of its passes the
+  // subject, its window and the pass's best-cell keys; per sequence (input
+  // order) the box of its last light alignment
+  int align_mode = MSA_ALIGN_FULL;
+  bool light_used = false;
+  DevBuf light_order, light_win, light_keys;
+  std::vector<int32_t> h_order;
+  std::vector<int4> h_win;
+  std::vector<unsigned long long> h_keys, h_keys2;
+  std::vector<int32_t> h_boxes;
 
   msa_detail::Selector *sel = nullptr;
 

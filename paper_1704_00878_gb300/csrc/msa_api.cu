@@ -698,6 +698,241 @@ int reference_positions(msa_ctx *ctx, const int64_t *refs, int64_t nref, std::ve
   return MSA_OK;
 }
 
+// ------------------------------------------------------------ traceback-light alignment
+// The passes of MSA_ALIGN_BOX (light.cu has the reasoning): every subject's
+// best cell, then where best-scoring alignments ending there may start, then
+// codes only inside the box between and the traceback over them.  The host
+// reads the best cells and the corners back between the passes to order the
+// subjects by their windows (pass count, then columns), so the groups of a
+// warp stay in step.
+
+// positions of items sorted by (passes of GR rows, columns), both descending
+static void order_by_window(const std::vector<int4> &w, const std::vector<int32_t> &items, int GR,
+                            int max_cols, std::vector<int32_t> &pos_of) {
+  int max_np = 1;
+  for (int k : items) max_np = std::max(max_np, (w[k].y + GR - 1) / GR);
+  const size_t nb = (size_t)max_np * (max_cols + 1);
+  std::vector<int32_t> start(nb + 1, 0);
+  auto key = [&](int k) {
+    const int np = std::max(1, (w[k].y + GR - 1) / GR);
+    return (size_t)(np - 1) * (max_cols + 1) + (size_t)std::min(w[k].w, max_cols);
+  };
+  for (int k : items) ++start[key(k)];
+  int acc = 0;
+  for (size_t b = nb; b-- > 0;) {
+    const int c = start[b];
+    start[b] = acc;
+    acc += c;
+  }
+  pos_of.assign(items.size(), 0);
+  for (int k : items) pos_of[start[key(k)]++] = k;
+}
+
+static int align_light(msa_ctx *ctx, int kc, int Lc) {
+  const int n = ctx->n, R = kCodesR;
+  const SeqSet ss = seqset(ctx);
+  const Scoring sc = scoring(ctx);
+  const int G = align_group(ctx, Lc, true), GR = G * R;
+  const int npass = (Lc + GR - 1) / GR;
+  const int smem1 = light_smem_bytes(ctx->K, Lc, G, 1, npass);
+  const int smem2 = light_smem_bytes(ctx->K, Lc, G, 2, 0);
+  CK(light_allow_smem(G, 1, smem1));
+  CK(light_allow_smem(G, 2, smem2));
+  const int grid1 = light_grid(G, 1, smem1), grid2 = light_grid(G, 2, smem2);
+  if (grid1 < 1 || grid2 < 1)
+    return fail(ctx, MSA_ERANGE, "a center of %d residues leaves no shared memory for the light passes", Lc);
+  TRY(ensure(ctx, ctx->best, sizeof(unsigned long long) * n));
+  TRY(ensure(ctx, ctx->light_order, sizeof(int32_t) * n));
+  TRY(ensure(ctx, ctx->light_win, sizeof(int4) * n));
+  TRY(ensure(ctx, ctx->light_keys, sizeof(unsigned long long) * n));
+  TRY(ensure(ctx, ctx->code_off, sizeof(int64_t) * n));
+  LightJob job{};
+  job.center = kc;
+  job.counter = ctx->dcounter;
+  job.scratch_cols = ctx->maxlen;
+
+  // 1. the best cell of every subject
+  TRY(ensure(ctx, ctx->scratch, (size_t)std::max(grid1, grid2) * (kLightThreads / G) * 2 * ctx->maxlen * sizeof(int2)));
+  job.scratch = P<int2>(ctx->scratch);
+  job.sb = 0;
+  job.se = n;
+  job.npass = npass;
+  job.best = P<unsigned long long>(ctx->best);
+  CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+  stage_begin(ctx, ST_LIGHT_SCORE);
+  CK((++ctx->launches, launch_light)(G, 1, ss, sc, job, grid1, smem1, ctx->st));
+  stage_end(ctx, ST_LIGHT_SCORE);
+  std::vector<unsigned long long> &keys = ctx->h_keys, &keys2 = ctx->h_keys2;
+  keys.resize(n);
+  CK(cudaMemcpyAsync(keys.data(), ctx->best.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  stage_collect(ctx, ST_LIGHT_SCORE);
+
+  // 2. the reversed prefixes of the subjects with a positive cell: rows
+  // (i2 - p of the center, read from the reversed profile at Lc - i2, its
+  // start rounded down to 16 with the rows above masked) and columns j2 - q
+  std::vector<int4> &win = ctx->h_win;
+  std::vector<int32_t> &order = ctx->h_order;
+  win.assign(n, make_int4(0, 0, 0, 0));
+  std::vector<int32_t> items;
+  items.reserve(n);
+  for (int k = 0; k < n; ++k) {
+    if (best_key_score(keys[k]) <= 0) continue;
+    const int i2 = best_key_row(keys[k]), j2 = best_key_col(keys[k]);
+    const int top = Lc - i2;
+    win[k] = make_int4(top & ~15, (top & 15) + i2, top & 15, j2);
+    items.push_back(k);
+  }
+  const int npos = (int)items.size();
+  order_by_window(win, items, GR, ctx->maxlen, order);
+  std::vector<int4> wpos(npos);
+  for (int x = 0; x < npos; ++x) wpos[x] = win[order[x]];
+  ctx->stage_ms[ST_LIGHT_CORNER] = 0.f;
+  keys2.resize(npos);
+  if (npos > 0) {
+    CK(cudaMemcpyAsync(ctx->light_order.p, order.data(), sizeof(int32_t) * npos, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->light_win.p, wpos.data(), sizeof(int4) * npos, cudaMemcpyHostToDevice, ctx->st));
+    job.npos = npos;
+    job.order = P<int32_t>(ctx->light_order);
+    job.win = P<int4>(ctx->light_win);
+    job.best = P<unsigned long long>(ctx->light_keys);
+    CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+    stage_begin(ctx, ST_LIGHT_CORNER);
+    CK((++ctx->launches, launch_light)(G, 2, ss, sc, job, grid2, smem2, ctx->st));
+    stage_end(ctx, ST_LIGHT_CORNER);
+    CK(cudaMemcpyAsync(keys2.data(), ctx->light_keys.p, sizeof(unsigned long long) * npos, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    stage_collect(ctx, ST_LIGHT_CORNER);
+  }
+
+  // 3. boxes: rows (i0, i2] with i0 = i2 - P rounded down to 16, columns
+  // (j2 - Q, j2]; every subject takes part (no positive cell: an empty box,
+  // the traceback writes its flanks)
+  std::vector<int4> box(n, make_int4(0, 0, 0, 0));
+  double hsum = 0, wsum = 0;
+  int wmax = 0, hmax = 0;
+  for (int x = 0; x < npos; ++x) {
+    const int k = order[x];
+    const int S = best_key_score(keys[k]), i2 = best_key_row(keys[k]), j2 = best_key_col(keys[k]);
+    const int V = best_key_score(keys2[x]), Pr = best_key_row(keys2[x]), Qc = best_key_col(keys2[x]);
+    if (V != S || Pr < 1 || Pr > i2 || Qc < 1 || Qc > j2)
+      return fail(ctx, MSA_ECUDA, "light alignment: the reverse pass of sequence %d found %d at (%d, %d), "
+                  "its best score is %d", ctx->perm[k], V, Pr, Qc, S);
+    const int i0 = (i2 - Pr) & ~15;
+    box[k] = make_int4(i0, i2 - i0, j2 - Qc, Qc);
+    hsum += i2 - i0;
+    wsum += Qc;
+    hmax = std::max(hmax, i2 - i0);
+    wmax = std::max(wmax, Qc);
+  }
+  // lanes per group of the box pass: the cost model over the boxes (or the
+  // context's fixed choice)
+  const int G3 = ctx->align_group > 0 ? ctx->align_group
+                 : codes_group(npos ? (int)std::ceil(hsum / npos) : 16, true, ctx->K, std::max(npos, 1),
+                               npos ? wsum / npos : 1.0, std::max(wmax, 1));
+  const int smem3 = light_smem_bytes(ctx->K, Lc, G3, 3, 0);
+  CK(light_allow_smem(G3, 3, smem3));
+  const int grid3 = light_grid(G3, 3, smem3);
+  if (grid3 < 1)
+    return fail(ctx, MSA_ERANGE, "a center of %d residues leaves no shared memory for the light passes", Lc);
+  TRY(ensure(ctx, ctx->scratch, (size_t)grid3 * (kLightThreads / G3) * 2 * ctx->maxlen * sizeof(int2)));
+  job.scratch = P<int2>(ctx->scratch);
+  std::vector<int32_t> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  order_by_window(box, all, G3 * R, ctx->maxlen, order);
+  wpos.resize(n);
+  for (int x = 0; x < n; ++x) wpos[x] = box[order[x]];
+  auto box_bytes = [&](const int4 &b) -> size_t { return b.y > 0 ? code_words(b.w, b.y, G3) * 8 : 0; };
+  size_t all_codes = 0, max_one = 8;
+  for (int x = 0; x < n; ++x) {
+    all_codes += box_bytes(wpos[x]);
+    max_one = std::max(max_one, box_bytes(wpos[x]));
+  }
+  size_t budget = all_codes;
+  if (all_codes > ctx->codes.cap || all_codes > ctx->codes_budget) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    budget = std::min(ctx->codes_budget, free_b / 2);
+    if (ctx->dev_limit) budget = std::min(budget, ctx->dev_limit > ctx->dev_bytes ? (ctx->dev_limit - ctx->dev_bytes) / 2 : 0);
+  }
+  if (budget < max_one) budget = max_one;
+  std::vector<std::pair<int, int>> batches;
+  std::vector<int64_t> &offs = ctx->h_offs;
+  offs.resize(n);
+  size_t biggest = 8;
+  {
+    int b = 0;
+    size_t acc = 0;
+    for (int x = 0; x < n; ++x) {
+      const size_t sz = box_bytes(wpos[x]);
+      if (acc + sz > budget && x > b) {
+        batches.push_back({b, x});
+        biggest = std::max(biggest, acc);
+        b = x;
+        acc = 0;
+      }
+      offs[x] = (int64_t)acc;
+      acc += sz;
+    }
+    batches.push_back({b, n});
+    biggest = std::max(biggest, acc);
+  }
+  TRY(ensure(ctx, ctx->codes, biggest));
+  CK(cudaMemcpyAsync(ctx->light_order.p, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->light_win.p, wpos.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->code_off.p, offs.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  const int nb = (int)batches.size();
+  while ((int)ctx->align_ev.size() < 3 * nb) {
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreate(&ev));
+    ctx->align_ev.push_back(ev);
+  }
+  for (int bi = 0; bi < nb; ++bi) {
+    const int pb = batches[bi].first, pe = batches[bi].second;
+    job.npos = pe - pb;
+    job.order = P<int32_t>(ctx->light_order) + pb;
+    job.win = P<int4>(ctx->light_win) + pb;
+    job.code_off = P<int64_t>(ctx->code_off) + pb;
+    job.codes = P<uint8_t>(ctx->codes);
+    job.best = P<unsigned long long>(ctx->light_keys) + pb;
+    CK(cudaEventRecord(ctx->align_ev[3 * bi], ctx->st));
+    CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
+    CK((++ctx->launches, launch_light)(G3, 3, ss, sc, job, grid3, smem3, ctx->st));
+    CK(cudaEventRecord(ctx->align_ev[3 * bi + 1], ctx->st));
+    CK((++ctx->launches, launch_traceback)(
+        P<uint8_t>(ctx->codes), P<int64_t>(ctx->code_off) + pb, P<unsigned long long>(ctx->best), 0,
+        pe - pb, P<int32_t>(ctx->d_len), P<int32_t>(ctx->d_perm), ss.res, ss.pstart, kc, sc.M, sc.K,
+        sc.o, sc.e, Lc, G3, P<uint16_t>(ctx->ins), P<uint8_t>(ctx->occ), P<int32_t>(ctx->seg),
+        P<int32_t>(ctx->score), ctx->derr, ctx->st, P<int32_t>(ctx->light_order) + pb,
+        P<int4>(ctx->light_win) + pb, P<unsigned long long>(ctx->light_keys) + pb));
+    CK(cudaEventRecord(ctx->align_ev[3 * bi + 2], ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  float ms_box = 0.f, ms_tb = 0.f;
+  for (int bi = 0; bi < nb; ++bi) {
+    float a = 0.f, t = 0.f;
+    CK(cudaEventElapsedTime(&a, ctx->align_ev[3 * bi], ctx->align_ev[3 * bi + 1]));
+    CK(cudaEventElapsedTime(&t, ctx->align_ev[3 * bi + 1], ctx->align_ev[3 * bi + 2]));
+    ms_box += a;
+    ms_tb += t;
+  }
+  ctx->stage_ms[ST_LIGHT_BOX] = ms_box;
+  ctx->stage_ms[ST_TRACE] = ms_tb;
+  ctx->stage_ms[ST_ALIGN_K] = ctx->stage_ms[ST_LIGHT_SCORE] + ctx->stage_ms[ST_LIGHT_CORNER] + ms_box;
+  ctx->stage_ms[ST_ALIGN] = ctx->stage_ms[ST_ALIGN_K];
+  std::vector<int32_t> &hb = ctx->h_boxes;
+  hb.assign((size_t)4 * n, 0);
+  for (int k = 0; k < n; ++k) {
+    if (box[k].y <= 0) continue;
+    int32_t *b = &hb[(size_t)4 * ctx->perm[k]];
+    b[0] = box[k].x;
+    b[1] = box[k].z;
+    b[2] = box[k].x + box[k].y;
+    b[3] = box[k].z + box[k].w;
+  }
+  return MSA_OK;
+}
+
 }  // namespace msa_detail
 
 using namespace msa_detail;
@@ -1109,6 +1344,21 @@ int msa_align_to_center(msa_ctx *ctx, int64_t center, int32_t *scores_out) {
   CK(cudaMemsetAsync(ctx->ins.p, 0, sizeof(uint16_t) * row * n, ctx->st));
   CK(cudaMemsetAsync(ctx->occ.p, 0, row * n, ctx->st));
   CK(cudaMemsetAsync(ctx->derr, 0, 2 * sizeof(unsigned), ctx->st));
+  ctx->light_used = false;
+  if (ctx->align_mode == MSA_ALIGN_BOX && packed) {
+    int64_t matrix_cells = 0;
+    for (int k = 0; k < n; ++k) matrix_cells += (int64_t)Lc * ctx->len_sorted[k];
+    TRY(align_light(ctx, kc, Lc));
+    ctx->cells[1] = matrix_cells;
+    TRY(check_derr(ctx));
+    if (scores_out) {
+      CK(cudaMemcpyAsync(scores_out, ctx->score.p, sizeof(int32_t) * n, cudaMemcpyDefault, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+    }
+    ctx->light_used = true;
+    ctx->aligned = true;
+    return MSA_OK;
+  }
 
   // batches of subjects (sorted order) whose codes fit the budget; when all
   // of them fit the codes buffer the context already holds (and the budget),
@@ -1541,6 +1791,21 @@ int msa_set_align_threads(msa_ctx *ctx, int32_t threads) {
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes) {
   if (!ctx || lanes < 0 || lanes > 32 || (lanes & (lanes - 1)) != 0) return MSA_EINVAL;
   ctx->align_group = lanes;
+  return MSA_OK;
+}
+
+int msa_set_align_mode(msa_ctx *ctx, int32_t mode) {
+  if (!ctx || (mode != MSA_ALIGN_FULL && mode != MSA_ALIGN_BOX)) return MSA_EINVAL;
+  ctx->align_mode = mode;
+  return MSA_OK;
+}
+
+int msa_align_boxes(msa_ctx *ctx, int32_t *box_out) {
+  if (!ctx || !box_out) return MSA_EINVAL;
+  if (!ctx->aligned || !ctx->light_used) return fail(ctx, MSA_ESTATE, "no alignment in MSA_ALIGN_BOX mode");
+  TRY(set_device(ctx));
+  CK(cudaMemcpyAsync(box_out, ctx->h_boxes.data(), sizeof(int32_t) * ctx->h_boxes.size(), cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   return MSA_OK;
 }
 

@@ -63,24 +63,37 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
                             int center, const int8_t *__restrict__ M, int K, int o, int e,
                             int Lc, int G, uint16_t *__restrict__ ins, uint8_t *__restrict__ occ,
                             int32_t *__restrict__ seg, int32_t *__restrict__ score,
-                            unsigned *err) {
+                            unsigned *err, const int32_t *__restrict__ list,
+                            const int4 *__restrict__ box,
+                            const unsigned long long *__restrict__ box_best) {
   __shared__ int8_t sM[MSA_MAX_ALPHABET * MSA_MAX_ALPHABET];
   for (int i = threadIdx.x; i < K * K; i += blockDim.x) sM[i] = M[i];
   __syncthreads();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= se - sb) return;
-  const int k = sb + x;
+  // the subject: the x-th of [sb, se), or the x-th of a list (codes and boxes
+  // by list position, best cells by sorted index)
+  const int k = list ? list[x] : sb + x;
   const int orig = perm[k];
   const int Ls = len[k];
   const uint8_t *c = codes + code_off[x];
   const uint8_t *rc = res + pstart[center], *rs = res + pstart[k];
   uint16_t *in = ins + (size_t)orig * (Lc + 1);
   uint8_t *oc = occ + (size_t)orig * (Lc + 1);
-  const unsigned long long key = best[x];
+  const unsigned long long key = list ? best[k] : best[x];
   const int bv = best_key_score(key);
   int i2 = best_key_row(key), j2 = best_key_col(key);
   int i1 = 0, j1 = 0;
   if (bv > 0 && (i2 < 1 || i2 > Lc || j2 < 1 || j2 > Ls)) {  // a best cell outside the matrix
+    atomicOr(err, MSA_DERR_TRACE);
+    return;
+  }
+  // codes of the box rows (i0, i2] x columns (j0, j0 + cw], or of the whole
+  // matrix; the box's own best cell must be the matrix's
+  const int4 bx = box ? box[x] : make_int4(0, Lc, 0, Ls);
+  const int i0 = bx.x, j0 = bx.z, cw = bx.w;
+  if (box && bv > 0 &&
+      (i0 < 0 || j0 < 0 || i0 + bx.y != i2 || j0 + cw != j2 || box_best[x] != best_key(bv, i2 - i0, j2 - j0))) {
     atomicOr(err, MSA_DERR_TRACE);
     return;
   }
@@ -92,11 +105,11 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
     const int limit = 2 * (i2 + j2) + 4;
     bool ok = false;
     for (int step = 0; step < limit; ++step) {
-      if (i <= 0 || j <= 0) { ok = state == 0 && v == 0; break; }
+      if (i <= i0 || j <= j0) { ok = state == 0 && v == 0; break; }
       if (state == 0) {
         if (v == 0) { ok = true; break; }
         if (v < 0) break;
-        const uint32_t src = code_at(c, Ls, G, i, j) & 3u;
+        const uint32_t src = code_at(c, cw, G, i - i0, j - j0) & 3u;
         if (src == 1) {
           v -= sM[rc[i - 1] * K + rs[j - 1]];
           oc[i] = 1; --i; --j;
@@ -106,12 +119,12 @@ __global__ void k_traceback(const uint8_t *__restrict__ codes, const int64_t *__
           state = src == 2 ? 1 : 2;
         }
       } else if (state == 1) {
-        const bool ext = (code_at(c, Ls, G, i, j) >> 3) & 1u;
+        const bool ext = (code_at(c, cw, G, i - i0, j - j0) >> 3) & 1u;
         v += ext ? e : o;
         state = ext ? 1 : 0;
         --i;
       } else {
-        const bool ext = (code_at(c, Ls, G, i, j) >> 2) & 1u;
+        const bool ext = (code_at(c, cw, G, i - i0, j - j0) >> 2) & 1u;
         in[i] = (uint16_t)(in[i] + 1);
         v += ext ? e : o;
         state = ext ? 2 : 0;
@@ -431,13 +444,15 @@ cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
                              const uint8_t *res, const int64_t *pstart, int center,
                              const int8_t *M, int K, int o, int e, int Lc, int G,
                              uint16_t *ins, uint8_t *occ, int32_t *seg, int32_t *score,
-                             unsigned *err, cudaStream_t st) {
+                             unsigned *err, cudaStream_t st, const int32_t *list, const int4 *box,
+                             const unsigned long long *box_best) {
   const int cnt = se - sb;
   if (cnt <= 0) return cudaSuccess;
   const int threads = 128;
   k_traceback<<<(cnt + threads - 1) / threads, threads, 0, st>>>(codes, code_off, best, sb, se, len,
                                                                  perm, res, pstart, center, M, K, o,
-                                                                 e, Lc, G, ins, occ, seg, score, err);
+                                                                 e, Lc, G, ins, occ, seg, score, err,
+                                                                 list, box, box_best);
   return cudaGetLastError();
 }
 

@@ -8,13 +8,19 @@ cudaError_t launch_encode(const uint8_t *letters, const int64_t *src_off, const 
 
 // res/pstart/center/M/K/o/e: the walk recomputes the score of each cell on
 // its path (the codes hold a source only where H > 0).
+// list: subjects by sorted index (else [sb, se)), their best cells then read
+// at best[k]; box (with list): per list position {first row, rows, first
+// column, columns} of the box its codes cover, box_best the box's own best
+// cell (it must be the matrix's best cell in box coordinates).
 cudaError_t launch_traceback(const uint8_t *codes, const int64_t *code_off,
                              const unsigned long long *best,
                              int sb, int se, const int32_t *len, const int32_t *perm,
                              const uint8_t *res, const int64_t *pstart, int center,
                              const int8_t *M, int K, int o, int e, int Lc, int G,
                              uint16_t *ins, uint8_t *occ, int32_t *seg, int32_t *score,
-                             unsigned *err, cudaStream_t st);
+                             unsigned *err, cudaStream_t st, const int32_t *list = nullptr,
+                             const int4 *box = nullptr,
+                             const unsigned long long *box_best = nullptr);
 
 cudaError_t launch_colmax(const uint16_t *ins, int n, int Lc, int32_t *G, cudaStream_t st);
 cudaError_t launch_scan(const int32_t *G, int Lc, int32_t *off, int64_t *width, cudaStream_t st);

@@ -108,3 +108,33 @@ constexpr int kCodes2Threads = 256;      // codes kernel threads per CTA
 constexpr int kCodes2WideThreads = 384;  // the packed kernel's wider CTA
 constexpr int kPairsR = 16;
 constexpr int kCenterThreads = 256;
+
+// The traceback-light alignment to the center, packed cells only: a forward
+// score pass to each subject's best cell (mode 1), a pass over the reversed
+// prefixes up to that cell to where best-scoring alignments may start
+// (mode 2), and the codes of the box between (mode 3).
+struct LightJob {
+  int center;                     // sorted index
+  int sb, se, npass;              // mode 1: subjects [sb, se) in sorted order, passes over the center
+  int npos;                       // modes 2, 3: positions; group x takes positions 2x and 2x+1
+  const int32_t *order;           // modes 2, 3: sorted subject index of each position
+  const int4 *win;                // modes 2, 3: per position {first profile row (a multiple of
+                                  // 16), rows, mode 2: masked top rows / mode 3: first column,
+                                  // columns}
+  const int64_t *code_off;        // mode 3: byte offset of each position's codes
+  uint8_t *codes;
+  unsigned long long *best;       // mode 1: per subject (k - sb); modes 2, 3: per position
+  unsigned long long *counter;
+  int2 *scratch; int scratch_cols;
+};
+// profile rows of a light pass (modes 2 and 3 hold the whole center, and the
+// center reversed for mode 2, plus two passes of padding rows)
+__host__ __device__ inline int light_prof_rows(int Lc, int G, int mode, int npass) {
+  return mode == 1 ? npass * G * 16 : ((Lc + 15) & ~15) + 2 * G * 16;
+}
+int light_smem_bytes(int K, int Lc, int G, int mode, int npass);
+cudaError_t light_allow_smem(int G, int mode, int smem);
+int light_grid(int G, int mode, int smem);
+cudaError_t launch_light(int G, int mode, const SeqSet &ss, const Scoring &sc, const LightJob &job,
+                         int grid, int smem, cudaStream_t st);
+constexpr int kLightThreads = 256;
