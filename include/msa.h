@@ -355,9 +355,11 @@ int msa_dims(msa_ctx *ctx, int64_t *dims_out);
  * context stream: [0] encode, [1] center selection, [2] align DP, [3]
  * traceback, [4] merge, [5] rows, [6] SP, [7] center DP kernels alone, [8]
  * align DP kernels alone, [9] selector (embedding or training), [10] tree
- * (distances and neighbour joining).  counters_out (nullable, int64[3]): DP cells of the
- * last center selection, DP cells of the last alignment, kernels launched by
- * this context since msa_create. */
+ * (distances and neighbour joining), and the passes of the last MSA_ALIGN_BOX
+ * alignment: [11] score pass, [12] reverse pass, [13] box codes (their sum is
+ * [8] then).  counters_out (nullable, int64[3]): DP cells of the last center
+ * selection, DP cells of the last alignment (the whole matrices', in either
+ * mode), kernels launched by this context since msa_create. */
 int msa_stage_times(msa_ctx *ctx, float *ms_out, int32_t n, int64_t *counters_out);
 
 /* Device memory the context holds for its working buffers (the paper has no
@@ -390,6 +392,7 @@ int msa_set_codes_budget(msa_ctx *ctx, int64_t bytes);
  * cells, the packed kernel also in 384-thread CTAs (8 to 32 lanes), and keeps
  * the fastest shape, precision and CTA size for later alignments on this
  * context (msa_set_align_group and msa_set_align_threads override them).
+ * It times the full mode (MSA_ALIGN_FULL) whatever the context's mode.
  * rates_out (nullable, host double[3][6]): cells per second (fill and
  * traceback), rows [packed, int32, packed in 384-thread CTAs] x
  * [1, 2, 4, 8, 16, 32] lanes, 0 where not timed; choice_out
@@ -401,8 +404,11 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
 /* Lanes per subject group of the alignment kernels (1, 2, 4, 8, 16 or 32;
  * each lane holds 16 center rows, so a pass covers 16 x lanes rows; with 1
  * lane every lane aligns its own subjects, pass after pass), or 0 for the
- * choice of the library's cost model among 8, 16 and 32 (the default).  A tuning knob: the
- * result does not depend on it.  EINVAL for any other value. */
+ * choice of the library's cost model among 8, 16 and 32 (the default).  Under
+ * MSA_ALIGN_BOX a width set here holds for all three passes; otherwise the
+ * score and reverse passes take the full pass's width and the box pass the
+ * cost model's pick for the boxes' mean size.  A tuning knob: the result does
+ * not depend on it.  EINVAL for any other value. */
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes);
 
 /* Threads per CTA of the packed alignment kernel with groups of 8 lanes or

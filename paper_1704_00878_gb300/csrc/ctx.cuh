@@ -93,6 +93,7 @@ struct msa_ctx {
   // times over, and the traceback of each batch waits for its fill
   size_t codes_budget = (size_t)32 << 30;
   int align_group = 0;  // lanes per subject group of the codes kernels, 0 = modelled choice
+  bool align_group_fixed = false;  // set by msa_set_align_group: every light pass uses it too
   int align_int32 = 0;  // 1: the alignment uses int32 cells even where packed ones fit
   int align_threads = 0;  // CTA size of the packed codes kernel, 0 = kCodes2Threads
   // traceback-light alignment (MSA_ALIGN_BOX): per position of its passes the
@@ -101,10 +102,10 @@ struct msa_ctx {
   int align_mode = MSA_ALIGN_FULL;
   bool light_used = false;
   DevBuf light_order, light_win, light_keys;
-  std::vector<int32_t> h_order;
-  std::vector<int4> h_win;
-  std::vector<unsigned long long> h_keys, h_keys2;
-  std::vector<int32_t> h_boxes;
+  void *pinned = nullptr;  // pinned host staging of the light passes' round trips
+  size_t pinned_cap = 0;
+  std::vector<int4> h_win, h_box;
+  std::vector<int32_t> h_boxes, h_items, h_all;
 
   msa_detail::Selector *sel = nullptr;
 

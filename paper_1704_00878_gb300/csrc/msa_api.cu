@@ -2,6 +2,7 @@
 // length sorting, work-item classes for the center kernels, batching of the
 // traceback codes, and the stage timers.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -708,7 +709,7 @@ int reference_positions(msa_ctx *ctx, const int64_t *refs, int64_t nref, std::ve
 
 // positions of items sorted by (passes of GR rows, columns), both descending
 static void order_by_window(const std::vector<int4> &w, const std::vector<int32_t> &items, int GR,
-                            int max_cols, std::vector<int32_t> &pos_of) {
+                            int max_cols, int32_t *pos_of) {
   int max_np = 1;
   for (int k : items) max_np = std::max(max_np, (w[k].y + GR - 1) / GR);
   const size_t nb = (size_t)max_np * (max_cols + 1);
@@ -724,8 +725,55 @@ static void order_by_window(const std::vector<int4> &w, const std::vector<int32_
     start[b] = acc;
     acc += c;
   }
-  pos_of.assign(items.size(), 0);
   for (int k : items) pos_of[start[key(k)]++] = k;
+}
+
+// Pinned host staging of the light passes' round trips, per subject: its
+// window (16 bytes), best-cell key, corner key, codes offset (8 bytes each)
+// and position order (4 bytes).
+struct LightStage {
+  int4 *wpos;
+  unsigned long long *keys, *keys2;
+  int64_t *offs;
+  int32_t *order;
+};
+static int light_staging(msa_ctx *ctx, int n, LightStage *ls) {
+  const size_t need = (size_t)n * 44 + 64;
+  if (need > ctx->pinned_cap) {
+    if (ctx->pinned) {
+      CK(cudaStreamSynchronize(ctx->st));
+      CK(cudaFreeHost(ctx->pinned));
+      ctx->pinned = nullptr;
+      ctx->pinned_cap = 0;
+    }
+    CK(cudaHostAlloc(&ctx->pinned, need, cudaHostAllocDefault));
+    ctx->pinned_cap = need;
+  }
+  char *p = static_cast<char *>(ctx->pinned);
+  ls->wpos = reinterpret_cast<int4 *>(p);
+  ls->keys = reinterpret_cast<unsigned long long *>(p + (size_t)16 * n);
+  ls->keys2 = reinterpret_cast<unsigned long long *>(p + (size_t)24 * n);
+  ls->offs = reinterpret_cast<int64_t *>(p + (size_t)32 * n);
+  ls->order = reinterpret_cast<int32_t *>(p + (size_t)40 * n);
+  return MSA_OK;
+}
+
+// Lanes per group of the box pass: the codes kernel's cost model with the
+// boxes' mean height as the center length and their mean and largest widths
+// as the subject lengths.  (On the 200,000 peptides and the 10k proteins it
+// measured faster than a rule that fits 90% of the boxes into one pass.)
+static int box_group(msa_ctx *ctx, const std::vector<int4> &box, int n) {
+  double hs = 0.0, ws = 0.0;
+  int wmax = 1, cnt = 0;
+  for (int k = 0; k < n; ++k) {
+    if (box[k].y <= 0) continue;
+    hs += box[k].y;
+    ws += box[k].w;
+    wmax = std::max(wmax, box[k].w);
+    ++cnt;
+  }
+  if (cnt == 0) return 32;
+  return codes_group((int)std::ceil(hs / cnt), true, ctx->K, cnt, ws / cnt, wmax);
 }
 
 static int align_light(msa_ctx *ctx, int kc, int Lc) {
@@ -735,11 +783,9 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   const int G = align_group(ctx, Lc, true), GR = G * R;
   const int npass = (Lc + GR - 1) / GR;
   const int smem1 = light_smem_bytes(ctx->K, Lc, G, 1, npass);
-  const int smem2 = light_smem_bytes(ctx->K, Lc, G, 2, 0);
   CK(light_allow_smem(G, 1, smem1));
-  CK(light_allow_smem(G, 2, smem2));
-  const int grid1 = light_grid(G, 1, smem1), grid2 = light_grid(G, 2, smem2);
-  if (grid1 < 1 || grid2 < 1)
+  const int grid1 = light_grid(G, 1, smem1);
+  if (grid1 < 1)
     return fail(ctx, MSA_ERANGE, "a center of %d residues leaves no shared memory for the light passes", Lc);
   TRY(ensure(ctx, ctx->best, sizeof(unsigned long long) * n));
   TRY(ensure(ctx, ctx->light_order, sizeof(int32_t) * n));
@@ -752,7 +798,7 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   job.scratch_cols = ctx->maxlen;
 
   // 1. the best cell of every subject
-  TRY(ensure(ctx, ctx->scratch, (size_t)std::max(grid1, grid2) * (kLightThreads / G) * 2 * ctx->maxlen * sizeof(int2)));
+  TRY(ensure(ctx, ctx->scratch, (size_t)grid1 * (kLightThreads / G) * 2 * ctx->maxlen * sizeof(int2)));
   job.scratch = P<int2>(ctx->scratch);
   job.sb = 0;
   job.se = n;
@@ -762,9 +808,12 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   stage_begin(ctx, ST_LIGHT_SCORE);
   CK((++ctx->launches, launch_light)(G, 1, ss, sc, job, grid1, smem1, ctx->st));
   stage_end(ctx, ST_LIGHT_SCORE);
-  std::vector<unsigned long long> &keys = ctx->h_keys, &keys2 = ctx->h_keys2;
-  keys.resize(n);
-  CK(cudaMemcpyAsync(keys.data(), ctx->best.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
+  LightStage ls;
+  TRY(light_staging(ctx, n, &ls));
+  unsigned long long *keys = ls.keys, *keys2 = ls.keys2;
+  int32_t *order = ls.order;
+  int4 *wpos = ls.wpos;
+  CK(cudaMemcpyAsync(keys, ctx->best.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   stage_collect(ctx, ST_LIGHT_SCORE);
 
@@ -772,10 +821,9 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   // (i2 - p of the center, read from the reversed profile at Lc - i2, its
   // start rounded down to 16 with the rows above masked) and columns j2 - q
   std::vector<int4> &win = ctx->h_win;
-  std::vector<int32_t> &order = ctx->h_order;
   win.assign(n, make_int4(0, 0, 0, 0));
-  std::vector<int32_t> items;
-  items.reserve(n);
+  std::vector<int32_t> &items = ctx->h_items;
+  items.clear();
   for (int k = 0; k < n; ++k) {
     if (best_key_score(keys[k]) <= 0) continue;
     const int i2 = best_key_row(keys[k]), j2 = best_key_col(keys[k]);
@@ -785,22 +833,29 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   }
   const int npos = (int)items.size();
   order_by_window(win, items, GR, ctx->maxlen, order);
-  std::vector<int4> wpos(npos);
+  // the reversed windows span up to the whole center: the full pass's lanes
+  const int G2 = G;
+  const int smem2 = light_smem_bytes(ctx->K, Lc, G2, 2, 0);
+  CK(light_allow_smem(G2, 2, smem2));
+  const int grid2 = light_grid(G2, 2, smem2);
+  if (grid2 < 1)
+    return fail(ctx, MSA_ERANGE, "a center of %d residues leaves no shared memory for the light passes", Lc);
+  TRY(ensure(ctx, ctx->scratch, (size_t)grid2 * (kLightThreads / G2) * 2 * ctx->maxlen * sizeof(int2)));
+  job.scratch = P<int2>(ctx->scratch);
   for (int x = 0; x < npos; ++x) wpos[x] = win[order[x]];
   ctx->stage_ms[ST_LIGHT_CORNER] = 0.f;
-  keys2.resize(npos);
   if (npos > 0) {
-    CK(cudaMemcpyAsync(ctx->light_order.p, order.data(), sizeof(int32_t) * npos, cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(ctx->light_win.p, wpos.data(), sizeof(int4) * npos, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->light_order.p, order, sizeof(int32_t) * npos, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->light_win.p, wpos, sizeof(int4) * npos, cudaMemcpyHostToDevice, ctx->st));
     job.npos = npos;
     job.order = P<int32_t>(ctx->light_order);
     job.win = P<int4>(ctx->light_win);
     job.best = P<unsigned long long>(ctx->light_keys);
     CK(cudaMemsetAsync(ctx->dcounter, 0, sizeof(unsigned long long), ctx->st));
     stage_begin(ctx, ST_LIGHT_CORNER);
-    CK((++ctx->launches, launch_light)(G, 2, ss, sc, job, grid2, smem2, ctx->st));
+    CK((++ctx->launches, launch_light)(G2, 2, ss, sc, job, grid2, smem2, ctx->st));
     stage_end(ctx, ST_LIGHT_CORNER);
-    CK(cudaMemcpyAsync(keys2.data(), ctx->light_keys.p, sizeof(unsigned long long) * npos, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(keys2, ctx->light_keys.p, sizeof(unsigned long long) * npos, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     stage_collect(ctx, ST_LIGHT_CORNER);
   }
@@ -808,9 +863,8 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   // 3. boxes: rows (i0, i2] with i0 = i2 - P rounded down to 16, columns
   // (j2 - Q, j2]; every subject takes part (no positive cell: an empty box,
   // the traceback writes its flanks)
-  std::vector<int4> box(n, make_int4(0, 0, 0, 0));
-  double hsum = 0, wsum = 0;
-  int wmax = 0, hmax = 0;
+  std::vector<int4> &box = ctx->h_box;
+  box.assign(n, make_int4(0, 0, 0, 0));
   for (int x = 0; x < npos; ++x) {
     const int k = order[x];
     const int S = best_key_score(keys[k]), i2 = best_key_row(keys[k]), j2 = best_key_col(keys[k]);
@@ -820,16 +874,14 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
                   "its best score is %d", ctx->perm[k], V, Pr, Qc, S);
     const int i0 = (i2 - Pr) & ~15;
     box[k] = make_int4(i0, i2 - i0, j2 - Qc, Qc);
-    hsum += i2 - i0;
-    wsum += Qc;
-    hmax = std::max(hmax, i2 - i0);
-    wmax = std::max(wmax, Qc);
   }
-  // lanes per group of the box pass: the cost model over the boxes (or the
-  // context's fixed choice)
-  const int G3 = ctx->align_group > 0 ? ctx->align_group
-                 : codes_group(npos ? (int)std::ceil(hsum / npos) : 16, true, ctx->K, std::max(npos, 1),
-                               npos ? wsum / npos : 1.0, std::max(wmax, 1));
+  // lanes per group of the box pass (or the context's fixed choice)
+  std::vector<int32_t> &all = ctx->h_all;
+  if ((int)all.size() != n) {
+    all.resize(n);
+    std::iota(all.begin(), all.end(), 0);
+  }
+  const int G3 = ctx->align_group_fixed ? ctx->align_group : box_group(ctx, box, n);
   const int smem3 = light_smem_bytes(ctx->K, Lc, G3, 3, 0);
   CK(light_allow_smem(G3, 3, smem3));
   const int grid3 = light_grid(G3, 3, smem3);
@@ -837,10 +889,7 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
     return fail(ctx, MSA_ERANGE, "a center of %d residues leaves no shared memory for the light passes", Lc);
   TRY(ensure(ctx, ctx->scratch, (size_t)grid3 * (kLightThreads / G3) * 2 * ctx->maxlen * sizeof(int2)));
   job.scratch = P<int2>(ctx->scratch);
-  std::vector<int32_t> all(n);
-  std::iota(all.begin(), all.end(), 0);
   order_by_window(box, all, G3 * R, ctx->maxlen, order);
-  wpos.resize(n);
   for (int x = 0; x < n; ++x) wpos[x] = box[order[x]];
   auto box_bytes = [&](const int4 &b) -> size_t { return b.y > 0 ? code_words(b.w, b.y, G3) * 8 : 0; };
   size_t all_codes = 0, max_one = 8;
@@ -857,8 +906,7 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
   }
   if (budget < max_one) budget = max_one;
   std::vector<std::pair<int, int>> batches;
-  std::vector<int64_t> &offs = ctx->h_offs;
-  offs.resize(n);
+  int64_t *offs = ls.offs;
   size_t biggest = 8;
   {
     int b = 0;
@@ -878,9 +926,9 @@ static int align_light(msa_ctx *ctx, int kc, int Lc) {
     biggest = std::max(biggest, acc);
   }
   TRY(ensure(ctx, ctx->codes, biggest));
-  CK(cudaMemcpyAsync(ctx->light_order.p, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->light_win.p, wpos.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->code_off.p, offs.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->light_order.p, order, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->light_win.p, wpos, sizeof(int4) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->code_off.p, offs, sizeof(int64_t) * n, cudaMemcpyHostToDevice, ctx->st));
   const int nb = (int)batches.size();
   while ((int)ctx->align_ev.size() < 3 * nb) {
     cudaEvent_t ev = nullptr;
@@ -1032,7 +1080,8 @@ void msa_destroy(msa_ctx *ctx) {
                     &ctx->part_val, &ctx->part_idx, &ctx->pairs, &ctx->pair_dst,
                     &ctx->pair_out, &ctx->ins, &ctx->occ, &ctx->seg, &ctx->score,
                     &ctx->codes, &ctx->code_off, &ctx->best, &ctx->G, &ctx->off, &ctx->msa,
-                    &ctx->counts, &ctx->scratch, &ctx->counters, &ctx->streams};
+                    &ctx->counts, &ctx->scratch, &ctx->counters, &ctx->streams,
+                    &ctx->light_order, &ctx->light_win, &ctx->light_keys};
   for (DevBuf *b : bufs)
     if (b->p) cudaFree(b->p);
   cudaFree(ctx->dM);
@@ -1049,6 +1098,7 @@ void msa_destroy(msa_ctx *ctx) {
   if (ctx->cap_join) cudaEventDestroy(ctx->cap_join);
   cudaFree(ctx->derr);
   cudaFree(ctx->dsmall);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto &ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
   delete ctx;
@@ -1744,6 +1794,13 @@ int msa_align_autotune(msa_ctx *ctx, int64_t center, double *rates_out, int32_t 
   const int Lc = ctx->len_sorted[ctx->inv[center]];
   ctx->align_int32 = 0;
   const bool can_pack = codes_packed(ctx, Lc);
+  // the shapes are those of the full alignment
+  struct ModeGuard {
+    msa_ctx *c;
+    int saved;
+    ~ModeGuard() { c->align_mode = saved; }
+  } guard{ctx, ctx->align_mode};
+  ctx->align_mode = MSA_ALIGN_FULL;
   // rows: packed cells in 256-thread CTAs, int32 cells, packed cells in
   // 384-thread CTAs (groups of 8 lanes and more)
   double rates[3][kAlignWidths] = {};
@@ -1791,6 +1848,7 @@ int msa_set_align_threads(msa_ctx *ctx, int32_t threads) {
 int msa_set_align_group(msa_ctx *ctx, int32_t lanes) {
   if (!ctx || lanes < 0 || lanes > 32 || (lanes & (lanes - 1)) != 0) return MSA_EINVAL;
   ctx->align_group = lanes;
+  ctx->align_group_fixed = lanes > 0;
   return MSA_OK;
 }
 

@@ -54,3 +54,49 @@ def test_box_recompute_reproduces_the_traced_path(seed):
             assert inner(bins, bocc, ki1, ki2) == inner(ins, occ, i1, i2)
             checked += 1
     assert checked > 200
+
+
+def reversed_local_h(c, s, M, o, e):
+    """H of the local alignment (Eq. 1-2, a gap of k costing o + (k-1) e) of
+    the two sequences as given, written out cell by cell: (len(c)+1) x
+    (len(s)+1), row and column 0 zero."""
+    NEG = -(1 << 40)
+    H = np.zeros((len(c) + 1, len(s) + 1), np.int64)
+    F = np.full(len(s) + 1, NEG, np.int64)
+    for i in range(1, len(c) + 1):
+        E = NEG
+        for j in range(1, len(s) + 1):
+            E = max(H[i, j - 1] - o, E - e)
+            F[j] = max(H[i - 1, j] - o, F[j] - e)
+            H[i, j] = max(0, H[i - 1, j - 1] + int(M[c[i - 1], s[j - 1]]), E, F[j])
+    return H
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_reverse_pass_corner_holds_the_traced_start(seed):
+    """The reverse pass of the traceback-light alignment: on the two prefixes
+    ending at the best cell, both read backwards, no cell scores above the
+    best score S, and the largest reversed row P and column Q of cells scoring
+    S give a corner (i2 - P, j2 - Q) above and left of the traced segment's
+    start (i1, j1) -- so the box from that corner holds the traced path."""
+    rng = np.random.default_rng(2000 + seed)
+    checked = 0
+    for _ in range(150):
+        c, s, M, o, e = random_case(rng)
+        best, codes, end = oracle.sw(c, s, M, o, e, codes=True)
+        if best <= 0:
+            continue
+        ins, occ, (i1, j1, i2, j2) = oracle.traceback(codes, best, end)
+        H = reversed_local_h(c[:i2][::-1], s[:j2][::-1], M, o, e)
+        assert H.max() == best
+        ps, qs = np.nonzero(H == best)
+        assert i2 - ps.max() <= i1 and j2 - qs.max() <= j1
+        # and the box from that corner, its row rounded down to 16, gives back
+        # the traced path (the box-recompute property above)
+        bi, bj = (i2 - ps.max()) & ~15, j2 - qs.max()
+        bb, bcodes, bend = oracle.sw(c[bi:i2], s[bj:j2], M, o, e, codes=True)
+        assert bb == best and bend == (i2 - bi, j2 - bj)
+        _, _, seg = oracle.traceback(bcodes, bb, bend)
+        assert (seg[0] + bi, seg[1] + bj) == (i1, j1)
+        checked += 1
+    assert checked > 100
