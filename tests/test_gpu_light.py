@@ -180,3 +180,34 @@ def test_light_mode_switches_and_errors():
         check_against_oracle(prob, 2, *out)
         with pytest.raises(b.MSAError):
             b.msa_align_boxes(h, 30)
+
+
+@pytest.mark.parametrize("kind", ["dna", "protein"])
+def test_light_at_the_longest_packed_centers(kind):
+    """The longest centers the packed cells take: MSA_MAX_LEN residues of DNA
+    (reverse windows of up to 16 passes of 512 rows) and 2,900 residues of
+    protein under BLOSUM62 (the int16 bound), with subjects from full length
+    down to short reads cut from anywhere in the center."""
+    from tests.test_gpu_limits import mutants
+    from seqgen import blosum62, STANDARD_AA
+    b = binding()
+    rng = np.random.default_rng(31 if kind == "dna" else 37)
+    if kind == "dna":
+        alph, M = dna_matrix(2, -3)
+        pool = np.frombuffer(b"ACGT", np.uint8)
+        L, o, e, rate = b.MSA_MAX_LEN, 5, 2, 0.02
+        lengths = [L, L - 100, 3000, 200, 40, 17]
+    else:
+        alph, M = blosum62()
+        pool = np.frombuffer(STANDARD_AA.encode(), np.uint8)
+        L, o, e, rate = 2900, 11, 1, 0.3
+        lengths = [L, 2000, 300, 60, 25]
+    ancestor = pool[rng.integers(0, pool.size, L)]
+    seqs = [ancestor.copy()] + mutants(rng, ancestor, pool, lengths, rate)
+    letters, offsets = pack_sequences(seqs)
+    prob = oracle_problem(letters, offsets, alph, M, o, e)
+    with make_ctx(alph, M, o, e) as h:
+        b.msa_load(h, letters, offsets)
+        out, boxes = light_pipeline(b, h, letters, offsets, 0)
+    check_against_oracle(prob, 0, *out)
+    check_boxes(prob, 0, boxes)
