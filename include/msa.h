@@ -429,9 +429,10 @@ int msa_set_align_threads(msa_ctx *ctx, int32_t threads);
  *     them); then codes only for the box rows (i0, i2] x columns (j0, j2]
  *     with j0 = j2 - Q and i0 = i2 - P rounded down to a multiple of 16, a
  *     local alignment of those slices whose walk retraces the same path.
- *     Codes take box area x 0.5 byte instead of matrix area x 0.5 byte; the
- *     two extra fills cost more than the codes they save unless the segments
- *     are short against the center.  Packed int16x2 cells only: where the
+ *     Codes take box area x 0.5 byte instead of matrix area x 0.5 byte, so
+ *     far more subjects fit one code batch; the two extra fills take longer
+ *     than writing the codes they save (the full fill is bound by integer
+ *     issue, not by its code stores).  Packed int16x2 cells only: where the
  *     center's length rules them out, the call runs the full mode.
  * EINVAL for any other mode. */
 #define MSA_ALIGN_FULL 0
