@@ -13,8 +13,8 @@
 // Neighbour joining: the matrix stays on the device (int32 -- every entry and
 // joined distance within 2^30, else ERANGE -- positions in
 // ascending slot order); every join is two launches -- the minimum of Q over
-// the active pairs (warps over 512-column segments of the rows, the last CTA to finish
-// reduces the CTAs' minima) and the join itself (CTAs over the rows: branch lengths,
+// the active pairs (warps over tiles of 8 rows x 256 columns, the last CTA to
+// finish reduces the CTAs' minima) and the join itself (CTAs over the rows: branch lengths,
 // the new node's row and column, the row sums updated in place; the last
 // CTA to finish adds up the new node's row sum).  When a quarter of the
 // positions are inactive the matrix is packed to the active ones, which keeps
@@ -33,8 +33,8 @@ constexpr int kWords = 64;   // 32-bit words (4 columns) per staged chunk
 constexpr long long kDScale = 1LL << 20;
 constexpr long long kDLimit = 1LL << 30;  // |distance| bound of the joins (int32 matrix)
 constexpr int kArgThreads = 256;
-constexpr int kUnroll = 8;  // loads per lane in flight in the Q minimum (16 measured slower)
-constexpr int kSeg = 2 * 32 * kUnroll;  // columns of one warp task of the Q minimum
+constexpr int kRowBlk = 8;    // rows of one warp task (tile) of the Q minimum
+constexpr int kColSeg = 256;  // columns of a tile: 8 per lane
 constexpr int kJoinThreads = 1024;
 
 // 0x80 in every byte of w that is nonzero
@@ -181,8 +181,14 @@ __device__ __forceinline__ Pick block_min(Pick p, Pick *sh) {
 }
 
 // The active pair of smallest Q = (m - 2) d(x, y) - r_x - r_y, ties to the
-// smallest x, then y (positions ascend with the slots).  The last CTA to
-// finish reduces every CTA's minimum into sel = {x, y}.
+// smallest x, then y (positions ascend with the slots).  Warp tasks are tiles
+// of kRowBlk rows x kColSeg columns of the upper triangle: a lane loads -r_y
+// and the active flags of its kColSeg / 32 columns once per tile, then per
+// row one int32 distance per column and one 64-bit multiply-add
+// (m - 2) d - r_y, compared with the tile's best so far plus r_x.  Inside a
+// tile a lane meets its cells in ascending (x, y), so a strict comparison
+// keeps the first of equal values; tiles, lanes and CTAs then merge on
+// (Q, x, y).  The last CTA to finish reduces every CTA's minimum into sel.
 __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const int *__restrict__ D, int P,
                                                            const long long *__restrict__ r,
                                                            const uint8_t *__restrict__ act, int m,
@@ -190,38 +196,56 @@ __global__ void __launch_bounds__(kArgThreads) k_nj_argmin(const int *__restrict
                                                            Pick *__restrict__ part,
                                                            unsigned *__restrict__ ticket,
                                                            int *__restrict__ sel) {
+  constexpr int U = kColSeg / 32;
   __shared__ Pick sh[32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  const long long f = m - 2;
+  const int f = m - 2;
   Pick best{LLONG_MAX, LLONG_MAX};
-  // warp tasks: (row x, first column) of kSeg-column segments of the upper
-  // triangle, so the long rows of the first joins spread over many warps
   for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += warps) {
     const int2 tk = tasks[task];
-    const int x = tk.x;
-    if (!act[x]) continue;
-    const long long rx = r[x];
-    const int *row = D + (size_t)x * P;
-    const int yend = min(P, tk.y + kSeg);
-    // kUnroll independent loads per lane in flight
-    for (int y0 = tk.y + lane; y0 < yend; y0 += 32 * kUnroll) {
-      long long dv[kUnroll], rv[kUnroll];
-      bool ok[kUnroll];
+    const int yb = tk.y + lane;
+    long long nry[U];
+    unsigned okm = 0;
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int y = y0 + 32 * u;
-        ok[u] = y < yend && act[y];
-        dv[u] = ok[u] ? row[y] : 0;
-        rv[u] = ok[u] ? r[y] : 0;
-      }
+    for (int u = 0; u < U; ++u) {
+      const int y = yb + 32 * u;
+      const bool ok = y < P && act[y];
+      okm |= (ok ? 1u : 0u) << u;
+      nry[u] = ok ? -r[y] : 0;
+    }
+    long long tq = LLONG_MAX;  // the tile's best Q for this lane, at (tx, ty)
+    int tx = 0, ty = 0;
+    const int xend = min(tk.x + kRowBlk, P);
+    for (int x = tk.x; x < xend; ++x) {
+      if (!act[x]) continue;  // the same x on every lane
+      const long long rx = r[x];
+      // columns y > x only: u from ceil((x + 1 - yb) / 32) on
+      const int lim = x + 1 - yb;
+      const int umin = lim <= 0 ? 0 : (lim + 31) >> 5;
+      const unsigned rm = umin >= U ? 0u : okm & (0xffffffffu << umin);
+      if (rm == 0) continue;
+      const int *row = D + (size_t)x * P;
+      int dv[U];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int y = y0 + 32 * u;
-        const Pick c{f * dv[u] - rx - rv[u], ((long long)x << 32) | (long long)y};
-        if (ok[u] && pick_less(c, best)) best = c;
+      for (int u = 0; u < U; ++u) dv[u] = (rm >> u) & 1u ? row[yb + 32 * u] : 0;
+      // q < tq  <=>  f d - r_y < tq + r_x (no overflow: |Q| < 2^63 by far)
+      long long thr = tq == LLONG_MAX ? LLONG_MAX : tq + rx;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long v = (long long)f * dv[u] + nry[u];
+        if (((rm >> u) & 1u) && v < thr) {
+          thr = v;
+          tq = v - rx;
+          tx = x;
+          ty = yb + 32 * u;
+        }
       }
+    }
+    if (tq != LLONG_MAX) {
+      const Pick c{tq, ((long long)tx << 32) | (long long)ty};
+      if (pick_less(c, best)) best = c;
     }
   }
   best = block_min(best, sh);
@@ -484,13 +508,14 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
     k_nj_init<<<grid, 256, 0, ctx->st>>>(P<long long>(r), P<int>(D1), n, P<int>(node),
                                          P<uint8_t>(act));
     CK(cudaGetLastError());
-    // the Q minimum's warp tasks for a matrix of P positions
+    // the Q minimum's warp tasks for a matrix of P positions: tiles of
+    // kRowBlk rows from x0, kColSeg columns from y0 > x0
     std::vector<int2> htasks;
     int ntask = 0;
     auto make_tasks = [&](int Pm) -> int {
       htasks.clear();
-      for (int x = 0; x + 1 < Pm; ++x)
-        for (int y = x + 1; y < Pm; y += kSeg) htasks.push_back(make_int2(x, y));
+      for (int x0 = 0; x0 + 1 < Pm; x0 += kRowBlk)
+        for (int y0 = x0 + 1; y0 < Pm; y0 += kColSeg) htasks.push_back(make_int2(x0, y0));
       ntask = (int)htasks.size();
       TRY(ensure(ctx, tasks, sizeof(int2) * std::max(ntask, 1)));
       CK(cudaMemcpyAsync(tasks.p, htasks.data(), sizeof(int2) * ntask, cudaMemcpyHostToDevice, ctx->st));
@@ -500,10 +525,14 @@ int nj_device(msa_ctx *ctx, DevBuf &D, int n, int32_t *joins_out, double *length
     DevBuf *cD = &D1, *cR = &r, *cN = &node, *cA = &act;
     DevBuf *oD = &D2, *oR = &r2, *oN = &node2, *oA = &act2;
     int Pn = n, m = n, t = 0;
+    // the Q minimum runs as many CTAs as stay resident (its warps loop over the tiles)
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nj_argmin, kArgThreads, 0);
+    const int aresident = std::min(grid, std::max(1, sms) * std::max(1, per_sm));
     while (m > 2) {
       ctx->launches += 2;
       // a warp per task at least: small matrices take few CTAs
-      const int agrid = std::max(1, std::min(grid, (ntask + kArgThreads / 32 - 1) / (kArgThreads / 32)));
+      const int agrid = std::max(1, std::min(aresident, (ntask + kArgThreads / 32 - 1) / (kArgThreads / 32)));
       k_nj_argmin<<<agrid, kArgThreads, 0, ctx->st>>>(P<int>(*cD), Pn, P<long long>(*cR),
                                                      P<uint8_t>(*cA), m, P<int2>(tasks), ntask,
                                                      P<Pick>(part), ticket, P<int>(sel));
