@@ -894,6 +894,10 @@ def run_ours(args):
         "roofline": ({"bound": "alu", "kernel": "k_center (exact-center DP, packed int16x2)",
                       "achieved": achieved, "peak": ALU_PEAK_GCUPS, "unit": UNIT,
                       "frac": achieved / ALU_PEAK_GCUPS if achieved else None, "traffic": None,
+                      "traffic_note": "not scaled: the center kernels' DRAM traffic is the "
+                                      "residues and profiles, which does not grow with the "
+                                      "cells (0.28 MB for one 1.57 ms launch on 2,000 "
+                                      "proteins, profiles/k_center2_batched_uneven_10k.md)",
                       "peak_source": "152 SMs x 64 DPX lanes/clk x 2.07 GHz / 3 DPX ops per cell",
                       "peak_measured": rate / OPS_PER_CELL / 1e9,
                       "dpx_ops_per_clk_sm_measured": per_clk}
